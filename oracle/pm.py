@@ -1,0 +1,356 @@
+"""Particle-mesh force, KDK integration and its discrete adjoint, FP64
+(test infrastructure only).
+
+Paper: pmwd is a cosmological particle-mesh (PM) simulation (Summary) whose
+gradients come from the adjoint method with reverse time integration
+(Summary; Statement of Need) and follow the same discrete trajectory as the
+forward integrator (Statement of Need, "discretize-then-optimize").  The
+paper prints no equations; the readings below are the standard comoving PM
+ones.                                                             [reading]
+
+Geometry: box L, n_m^3 mesh with nodes at c h, h = L / n_m, periodic;
+n_p^3 particles on the lattice q = i L / n_p + h / 2, i.e. half a mesh cell
+off the nodes [reading]: the unperturbed lattice then paints an exactly
+uniform mesh and small displacements sit away from the CIC kinks, so the
+linear response is symmetric.  Particle state:
+displacement s = x - q and momentum p = a^3 E dx/da.
+
+  CIC weights   W(x - c) = prod_d w(u_d - c_d), u = x / h, i0 = floor(u),
+                f = u - i0, w = 1 - f at i0 and f at i0 + 1.
+  density       rho(c) = alpha sum_i W(x_i - c) - 1, alpha = (n_m / n_p)^3
+  force         F_j(k) = i k_j (3/2) Om rho(k) / k^2, zero at k = 0 and where
+                n_j is the Nyquist index; F_j(c) = IDFT; F_i = sum_c W F(c)
+  step n        p <- p + K_a F(s);  s <- s + Dr p;  p <- p + K_b F(s)
+
+Every routine below is written as the definition it implements; FFTs are
+library calls (scipy.fft), everything else is plain numpy.
+"""
+
+import itertools
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.fft as sfft
+
+from .cosmology import Cosmology, kdk_coefficients, kdk_coefficients_domega
+
+_WORKERS = -1   # scipy.fft threads: all host cores
+
+
+@dataclass(frozen=True)
+class Setup:
+    n_p: int
+    n_m: int
+    box: float
+    cosmo: Cosmology = field(default_factory=Cosmology)
+    a_init: float = 1.0 / 64
+    a_final: float = 1.0
+    n_steps: int = 10
+
+    @property
+    def cell(self):
+        return self.box / self.n_m
+
+    @property
+    def spacing(self):
+        return self.box / self.n_p
+
+    @property
+    def alpha(self):
+        return (self.n_m / self.n_p) ** 3
+
+
+# ------------------------------------------------------------ geometry ----
+
+def lattice(n_p, box, n_m):
+    """Lagrangian positions q = i L / n_p + h / 2, lattice order (x slowest,
+    z fastest)."""
+    g = np.arange(n_p, dtype=np.float64) * (box / n_p) + 0.5 * box / n_m
+    qx, qy, qz = np.meshgrid(g, g, g, indexing="ij")
+    return np.stack([qx.ravel(), qy.ravel(), qz.ravel()], axis=1)
+
+
+def positions(s, setup):
+    return lattice(setup.n_p, setup.box, setup.n_m) + s
+
+
+def rfft_wavenumbers(n, box):
+    """k_x, k_y, k_z broadcastable over an (n, n, n//2+1) rfft grid and the
+    Nyquist masks of each axis (index n//2 on every axis)."""
+    kf = 2.0 * np.pi / box
+    full = np.fft.fftfreq(n, 1.0 / n)
+    half = np.arange(n // 2 + 1, dtype=np.float64)
+    kx = (kf * full)[:, None, None]
+    ky = (kf * full)[None, :, None]
+    kz = (kf * half)[None, None, :]
+    ix = np.arange(n)
+    iz = np.arange(n // 2 + 1)
+    nyq = ((ix == n // 2)[:, None, None], (ix == n // 2)[None, :, None],
+           (iz == n // 2)[None, None, :])
+    return (kx, ky, kz), nyq
+
+
+def rfftn(a):
+    return sfft.rfftn(a, workers=_WORKERS)
+
+
+def irfftn(a, n):
+    return sfft.irfftn(a, s=(n, n, n), workers=_WORKERS)
+
+
+# ---------------------------------------------------------------- CIC ----
+
+def cic_corners(x, n_m, cell):
+    """For each of the 8 corners: flat mesh index, weight W and dW/dx (N,3).
+    dW/dx uses the one-sided slopes -1/h, +1/h of the floor convention."""
+    u = x / cell
+    base = np.floor(u)
+    f = u - base
+    base = base.astype(np.int64)
+    out = []
+    for off in itertools.product((0, 1), repeat=3):
+        off = np.array(off)
+        idx = (base + off) % n_m
+        flat = (idx[:, 0] * n_m + idx[:, 1]) * n_m + idx[:, 2]
+        w1 = np.where(off == 1, f, 1.0 - f)
+        dw1 = np.where(off == 1, 1.0, -1.0) / cell
+        w = w1[:, 0] * w1[:, 1] * w1[:, 2]
+        grad = np.stack([dw1[0] * w1[:, 1] * w1[:, 2],
+                         w1[:, 0] * dw1[1] * w1[:, 2],
+                         w1[:, 0] * w1[:, 1] * dw1[2]], axis=1)
+        out.append((flat, w, grad))
+    return out
+
+
+def cic_paint(x, n_m, cell, weights=None):
+    """sum_i weights_i W(x_i - c) on the n_m^3 mesh."""
+    mesh = np.zeros(n_m ** 3)
+    wts = np.ones(len(x)) if weights is None else weights
+    for flat, w, _ in cic_corners(x, n_m, cell):
+        mesh += np.bincount(flat, weights=w * wts, minlength=n_m ** 3)
+    return mesh.reshape(n_m, n_m, n_m)
+
+
+def cic_read(x, mesh, cell):
+    """sum_c W(x_i - c) mesh(c) per particle."""
+    n_m = mesh.shape[0]
+    flatmesh = mesh.ravel()
+    val = np.zeros(len(x))
+    for flat, w, _ in cic_corners(x, n_m, cell):
+        val += w * flatmesh[flat]
+    return val
+
+
+def cic_read_grad(x, mesh, cell):
+    """sum_c dW(x_i - c)/dx_i mesh(c) per particle, (N, 3)."""
+    n_m = mesh.shape[0]
+    flatmesh = mesh.ravel()
+    val = np.zeros((len(x), 3))
+    for flat, _, grad in cic_corners(x, n_m, cell):
+        val += grad * flatmesh[flat][:, None]
+    return val
+
+
+def density(s, setup):
+    """CIC density contrast alpha sum W - 1 of the particles at s."""
+    return setup.alpha * cic_paint(positions(s, setup), setup.n_m, setup.cell) - 1.0
+
+
+# -------------------------------------------------------------- force ----
+
+def gradient_green_multipliers(n, box, omega_m):
+    """i k_j (3/2) Om / k^2 on the rfft grid, zero at k = 0 and where n_j is
+    the Nyquist index (so each inverse transform is exactly real) [reading]."""
+    (kx, ky, kz), nyq = rfft_wavenumbers(n, box)
+    k2 = kx ** 2 + ky ** 2 + kz ** 2
+    k2s = np.where(k2 > 0, k2, 1.0)
+    out = []
+    for kj, mj in zip((kx, ky, kz), nyq):
+        m = 1j * kj * (1.5 * omega_m) / k2s
+        m = np.where((k2 > 0) & ~mj, m, 0.0)
+        out.append(m)
+    return out
+
+
+def force_meshes(x, setup):
+    rho = setup.alpha * cic_paint(x, setup.n_m, setup.cell) - 1.0
+    rho_k = rfftn(rho)
+    mult = gradient_green_multipliers(setup.n_m, setup.box, setup.cosmo.omega_m)
+    return [irfftn(m * rho_k, setup.n_m) for m in mult]
+
+
+def force(s, setup):
+    """PM force per particle, (N, 3), in lattice order."""
+    x = positions(s, setup)
+    meshes = force_meshes(x, setup)
+    return np.stack([cic_read(x, m, setup.cell) for m in meshes], axis=1)
+
+
+def force_vjp(s, v, setup):
+    """J(s)^T v for F(s) above (exact vector-Jacobian product):
+    term A differentiates the interpolation weights, term B the painted
+    density through the (real, odd) Green-gradient convolution whose adjoint
+    multiplies by the conjugate multiplier."""
+    x = positions(s, setup)
+    meshes = force_meshes(x, setup)
+    term_a = np.zeros((len(x), 3))
+    for j in range(3):
+        term_a += cic_read_grad(x, meshes[j], setup.cell) * v[:, j:j + 1]
+    mult = gradient_green_multipliers(setup.n_m, setup.box, setup.cosmo.omega_m)
+    psi_k = 0.0
+    for j in range(3):
+        u_j = cic_paint(x, setup.n_m, setup.cell, v[:, j])
+        psi_k = psi_k + np.conj(mult[j]) * rfftn(u_j)
+    psi = irfftn(psi_k, setup.n_m)
+    term_b = setup.alpha * cic_read_grad(x, psi, setup.cell)
+    return term_a + term_b
+
+
+# ---------------------------------------------------------------- KDK ----
+
+def coefficients(setup):
+    return kdk_coefficients(setup.cosmo, setup.a_init, setup.a_final, setup.n_steps)
+
+
+def integrate(s, p, setup, force_fn=None, steps=None):
+    """Forward KDK from a_init; returns (s, p, F(s)) after ``steps`` steps
+    (default: all).  ``force_fn`` defaults to the PM force."""
+    fn = force_fn or (lambda y: force(y, setup))
+    c = coefficients(setup)
+    s, p = s.copy(), p.copy()
+    f = fn(s)
+    for n in range(setup.n_steps if steps is None else steps):
+        p = p + c["K_a"][n] * f
+        s = s + c["Dr"][n] * p
+        f = fn(s)
+        p = p + c["K_b"][n] * f
+    return s, p, f
+
+
+def reverse_integrate(s, p, f, setup, steps=None):
+    """Reverse time integration: undo the KDK steps from the last one back,
+    recomputing forces instead of reading a stored history."""
+    c = coefficients(setup)
+    s, p = s.copy(), p.copy()
+    n_steps = setup.n_steps if steps is None else steps
+    for n in reversed(range(n_steps)):
+        p = p - c["K_b"][n] * f
+        s = s - c["Dr"][n] * p
+        f = force(s, setup)
+        p = p - c["K_a"][n] * f
+    return s, p, f
+
+
+def adjoint_integrate(s, p, f, lam, mu, setup):
+    """Discrete adjoint of ``integrate`` run backward in time along the
+    reconstructed trajectory.  (s, p, f) is the final state and F(s);
+    (lam, mu) the cotangents of the final s and p.  Returns the initial state,
+    the cotangents of the initial s and p, and the cotangents of the
+    coefficients (K_a, Dr, K_b per step) and of Om through the force
+    prefactor."""
+    c = coefficients(setup)
+    om = setup.cosmo.omega_m
+    n_steps = setup.n_steps
+    g_ka, g_dr, g_kb = np.zeros(n_steps), np.zeros(n_steps), np.zeros(n_steps)
+    g_om_direct = 0.0
+    s, p, lam, mu = s.copy(), p.copy(), lam.copy(), mu.copy()
+    for n in reversed(range(n_steps)):
+        # p_{n+1} = p_half + K_b F(s_{n+1})
+        g_kb[n] = np.sum(mu * f)
+        g_om_direct += c["K_b"][n] * g_kb[n] / om
+        lam = lam + c["K_b"][n] * force_vjp(s, mu, setup)
+        p_half = p - c["K_b"][n] * f
+        # s_{n+1} = s_n + Dr p_half
+        g_dr[n] = np.sum(lam * p_half)
+        mu = mu + c["Dr"][n] * lam
+        s = s - c["Dr"][n] * p_half
+        f = force(s, setup)
+        # p_half = p_n + K_a F(s_n)
+        g_ka[n] = np.sum(mu * f)
+        g_om_direct += c["K_a"][n] * g_ka[n] / om
+        lam = lam + c["K_a"][n] * force_vjp(s, mu, setup)
+        p = p_half - c["K_a"][n] * f
+    grads = {"K_a": g_ka, "Dr": g_dr, "K_b": g_kb, "omega_m_direct": g_om_direct}
+    return s, p, lam, mu, grads
+
+
+def dynamics_domega(grads, setup):
+    """Total d/dOm of the dynamics part: chain through the coefficient tables
+    plus the direct force prefactor."""
+    d = kdk_coefficients_domega(setup.cosmo, setup.a_init, setup.a_final, setup.n_steps)
+    return (np.dot(grads["K_a"], d["K_a"]) + np.dot(grads["Dr"], d["Dr"])
+            + np.dot(grads["K_b"], d["K_b"]) + grads["omega_m_direct"])
+
+
+# --------------------------------------------------------------- loss ----
+
+def mse_loss(s, target, setup):
+    """L = n_m^-3 sum_c (delta(c) - target(c))^2 of the final CIC density."""
+    d = density(s, setup) - target
+    return float(np.mean(d * d))
+
+
+def mse_loss_grad(s, target, setup):
+    """dL/ds: the CIC-weight-gradient read of 2 (delta - target) / n_m^3."""
+    x = positions(s, setup)
+    g_mesh = 2.0 * (density(s, setup) - target) / setup.n_m ** 3
+    return setup.alpha * cic_read_grad(x, g_mesh, setup.cell)
+
+
+def density_vjp(s, g_mesh, setup):
+    """Cotangent of s for a cotangent g_mesh of ``density(s)``."""
+    return setup.alpha * cic_read_grad(positions(s, setup), g_mesh, setup.cell)
+
+
+# ----------------------------------------------------- power spectrum ----
+
+def power_of_mesh(delta, box):
+    """Binned power of a real n^3 mesh: bins b = 0 .. n/2-1 with edges
+    (b + 1/2) k_F .. (b + 3/2) k_F over the full k space (rfft entries with
+    0 < n_z < n/2 count twice), k = 0 excluded, no shot-noise or window
+    correction [reading].  P_b = V / n^6 <|delta_k|^2>.  Returns
+    (k_mean, P, n_modes)."""
+    n = delta.shape[0]
+    dk = rfftn(delta)
+    (kx, ky, kz), _ = rfft_wavenumbers(n, box)
+    kmag = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    kf = 2.0 * np.pi / box
+    iz = np.arange(n // 2 + 1)
+    wz = np.where((iz == 0) | (iz == n // 2), 1.0, 2.0)[None, None, :]
+    w = np.broadcast_to(wz, dk.shape).ravel()
+    kk = np.broadcast_to(kmag, dk.shape).ravel()
+    pw = (np.abs(dk) ** 2).ravel()
+    nb = n // 2
+    b = np.floor(kk / kf - 0.5).astype(np.int64)
+    ok = (kk > 0) & (b >= 0) & (b < nb)
+    n_modes = np.bincount(b[ok], weights=w[ok], minlength=nb)
+    ksum = np.bincount(b[ok], weights=(w * kk)[ok], minlength=nb)
+    psum = np.bincount(b[ok], weights=(w * pw)[ok], minlength=nb)
+    vol = box ** 3
+    safe = np.where(n_modes > 0, n_modes, 1.0)
+    return ksum / safe, vol / n ** 6 * psum / safe, n_modes
+
+
+def power_spectrum(s, setup):
+    return power_of_mesh(density(s, setup), setup.box)
+
+
+# ------------------------------------------------------------ pipeline ----
+
+def simulate(noise, setup):
+    """White noise -> 2LPT at a_init -> KDK to a_final: (s, p, F)."""
+    from .lpt import initial_conditions
+    s0, p0 = initial_conditions(noise, setup)
+    return integrate(s0, p0, setup)
+
+
+def loss_and_grad(noise, target, setup):
+    """MSE of the final density against ``target`` and its gradient with
+    respect to the white noise, Om and sigma8, by the adjoint method."""
+    from .lpt import initial_conditions_vjp
+    s, p, f = simulate(noise, setup)
+    loss = mse_loss(s, target, setup)
+    lam = mse_loss_grad(s, target, setup)
+    _, _, lam0, mu0, grads = adjoint_integrate(s, p, f, lam, np.zeros_like(p), setup)
+    g_noise, g_om_ic, g_s8 = initial_conditions_vjp(noise, lam0, mu0, setup)
+    return loss, g_noise, g_om_ic + dynamics_domega(grads, setup), g_s8

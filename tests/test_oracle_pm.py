@@ -1,0 +1,193 @@
+"""Pins of the oracle's CIC assignment/interpolation, spectral Poisson force,
+its vector-Jacobian product and the power-spectrum estimator."""
+
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import pm
+from oracle.pm import Setup
+
+
+def _tent_mesh(x, n, cell):
+    # Brute force: W is the product of periodic tent functions max(0, 1 - |d|/h).
+    c = np.arange(n) * cell
+    box = n * cell
+    mesh = np.zeros((n, n, n))
+    for xi in x:
+        w = []
+        for d in range(3):
+            dist = (xi[d] - c + 0.5 * box) % box - 0.5 * box
+            w.append(np.maximum(0.0, 1.0 - np.abs(dist) / cell))
+        mesh += w[0][:, None, None] * w[1][None, :, None] * w[2][None, None, :]
+    return mesh
+
+
+def _special_positions(rng, n, cell, count):
+    x = rng.uniform(-2 * n * cell, 3 * n * cell, (count, 3))     # outside the box too
+    x[0] = [0.0, 0.0, 0.0]                                       # on a node
+    x[1] = [0.5 * cell, 0.5 * cell, 0.5 * cell]                  # cell centre
+    x[2] = [n * cell, 3 * cell, -cell]                           # nodes at the wrap
+    x[3] = [2.0 * cell, 2.5 * cell, (n - 0.25) * cell]           # on a face
+    return x
+
+
+def test_cic_paint_equals_tent_definition():
+    rng = np.random.default_rng(0)
+    n, cell = 6, 1.7
+    x = _special_positions(rng, n, cell, 40)
+    np.testing.assert_allclose(pm.cic_paint(x, n, cell), _tent_mesh(x, n, cell), atol=1e-12)
+
+
+def test_cic_node_and_centre():
+    n, cell = 8, 1.0
+    m = pm.cic_paint(np.array([[3.0, 4.0, 5.0]]), n, cell)
+    assert m[3, 4, 5] == 1.0 and m.sum() == 1.0
+    m = pm.cic_paint(np.array([[3.5, 4.5, 7.5]]), n, cell)
+    np.testing.assert_allclose(m[3:5, 4:6, [7, 0]], np.full((2, 2, 2), 0.125), atol=1e-15)
+
+
+def test_cic_mass_conservation():
+    rng = np.random.default_rng(1)
+    st = Setup(16, 32, 100.0)
+    s = rng.normal(0, 5.0, (16 ** 3, 3))
+    rho = pm.density(s, st)
+    assert abs(np.sum(rho + 1.0) - 32 ** 3) < 1e-8
+
+
+def test_cic_read_equals_tent_definition():
+    rng = np.random.default_rng(2)
+    n, cell = 6, 0.9
+    mesh = rng.standard_normal((n, n, n))
+    x = _special_positions(rng, n, cell, 30)
+    ref = np.array([np.sum(_tent_mesh(xi[None], n, cell) * mesh) for xi in x])
+    np.testing.assert_allclose(pm.cic_read(x, mesh, cell), ref, atol=1e-12)
+
+
+def test_cic_read_grad_matches_finite_difference():
+    rng = np.random.default_rng(3)
+    n, cell = 8, 1.3
+    mesh = rng.standard_normal((n, n, n))
+    x = rng.uniform(0, n * cell, (50, 3))
+    g = pm.cic_read_grad(x, mesh, cell)
+    eps = 1e-7
+    for d in range(3):
+        dx = np.zeros(3)
+        dx[d] = eps
+        fd = (pm.cic_read(x + dx, mesh, cell) - pm.cic_read(x - dx, mesh, cell)) / (2 * eps)
+        np.testing.assert_allclose(g[:, d], fd, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_force_mesh_against_direct_dft(n):
+    # Green's function x gradient via explicit O(N^6) complex DFT sums on the
+    # full k grid, with the same k = 0 and Nyquist (index n/2) zeroing.
+    rng = np.random.default_rng(n)
+    box, om = 10.0, 0.3
+    st = Setup(n, n, box, pm.Cosmology(om))
+    x = rng.uniform(0, box, (3 * n, 3))
+    h = box / n
+    rho = st.alpha * pm.cic_paint(x, n, h) - 1.0
+    idx = np.array(list(itertools.product(range(n), repeat=3)))
+    nvec = np.where(idx < n // 2, idx, idx - n)                  # n in [-N/2, N/2)
+    kvec = 2 * np.pi / box * nvec
+    cpos = idx * h
+    dft = np.exp(-1j * kvec @ cpos.T)                            # [k, c]
+    rho_k = dft @ rho.ravel()
+    k2 = np.sum(kvec ** 2, axis=1)
+    got = pm.force_meshes(x, st)
+    for j in range(3):
+        mult = np.where((k2 > 0) & (idx[:, j] != n // 2),
+                        1j * kvec[:, j] * 1.5 * om / np.where(k2 > 0, k2, 1.0), 0.0)
+        fj = (np.conj(dft).T @ (mult * rho_k)) / n ** 3
+        assert np.max(np.abs(fj.imag)) < 1e-12
+        np.testing.assert_allclose(got[j].ravel(), fj.real, atol=1e-12)
+
+
+def _force_at(x, setup, mass_x):
+    # force at x of the particles mass_x, painted with the same alpha
+    rho = setup.alpha * pm.cic_paint(mass_x, setup.n_m, setup.cell) - 1.0
+    mult = pm.gradient_green_multipliers(setup.n_m, setup.box, setup.cosmo.omega_m)
+    meshes = [pm.irfftn(m * pm.rfftn(rho), setup.n_m) for m in mult]
+    return np.stack([pm.cic_read(x, mm, setup.cell) for mm in meshes], axis=1)
+
+
+def test_gravity_attracts_and_newton_third_law():
+    st = Setup(4, 16, 16.0)
+    a = np.array([[5.3, 7.1, 8.2]])
+    b = np.array([[9.6, 8.0, 6.9]])
+    f_ab = _force_at(a, st, b)          # on a due to b
+    f_ba = _force_at(b, st, a)
+    assert np.dot(f_ab[0], (b - a)[0]) > 0          # attractive
+    np.testing.assert_allclose(f_ab, -f_ba, atol=1e-13)
+    np.testing.assert_allclose(_force_at(a, st, a), 0.0, atol=1e-13)   # no self force
+
+
+def test_total_force_vanishes():
+    rng = np.random.default_rng(4)
+    st = Setup(8, 16, 50.0)
+    s = rng.normal(0, 3.0, (8 ** 3, 3))
+    f = pm.force(s, st)
+    assert np.max(np.abs(f.sum(0))) < 1e-10 * np.abs(f).sum()
+
+
+def test_linear_force_prefactor():
+    # A small longitudinal plane-wave displacement gives F -> 3/2 Om s as the
+    # mode becomes well resolved; the CIC/mesh correction falls as (k h)^2.
+    # (One particle per cell, so no lattice aliasing enters.)
+    errs = []
+    for n_m in (32, 64):
+        st = Setup(n_m, n_m, 100.0, pm.Cosmology(0.3))
+        q = pm.lattice(n_m, 100.0, n_m)
+        k = 2 * np.pi / 100.0
+        s = np.zeros_like(q)
+        s[:, 0] = 1e-4 * np.sin(k * q[:, 0])
+        f = pm.force(s, st)
+        errs.append(np.max(np.abs(f[:, 0] - 1.5 * 0.3 * s[:, 0])) / np.max(np.abs(1.5 * 0.3 * s[:, 0])))
+        assert np.max(np.abs(f[:, 1:])) < 1e-12
+    assert errs[0] < 1e-2 and errs[1] < errs[0] / 3
+
+
+def test_force_vjp_matches_finite_difference():
+    rng = np.random.default_rng(5)
+    st = Setup(4, 8, 10.0)
+    s = rng.normal(0, 0.6, (64, 3))
+    v = rng.standard_normal((64, 3))
+    g = pm.force_vjp(s, v, st)
+    eps = 1e-6
+    for _ in range(6):
+        d = rng.standard_normal((64, 3))
+        fd = (np.sum(v * pm.force(s + eps * d, st)) - np.sum(v * pm.force(s - eps * d, st))) / (2 * eps)
+        assert abs(fd - np.sum(g * d)) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_power_of_cosine_mode_closed_form():
+    n, box, amp, m = 16, 40.0, 0.7, 3
+    c = np.arange(n) * box / n
+    delta = amp * np.cos(2 * np.pi * m / box * c)[:, None, None] * np.ones((n, n, n))
+    k_mean, p, nm = pm.power_of_mesh(delta, box)
+    expect = np.zeros(n // 2)
+    expect[m - 1] = box ** 3 * amp ** 2 / (2 * nm[m - 1])
+    np.testing.assert_allclose(p, expect, atol=1e-12 * box ** 3)
+
+
+def test_power_mode_counts_brute_force():
+    n, box = 12, 30.0
+    _, _, nm = pm.power_of_mesh(np.zeros((n, n, n)), box)
+    rng_n = np.arange(-n // 2, n // 2)
+    nv = np.array(list(itertools.product(rng_n, repeat=3)))
+    kk = np.sqrt(np.sum(nv ** 2, axis=1))
+    b = np.floor(kk - 0.5).astype(int)
+    ok = (kk > 0) & (b < n // 2)
+    np.testing.assert_array_equal(nm, np.bincount(b[ok], minlength=n // 2))
+
+
+def test_power_of_white_noise_is_flat():
+    n, box = 32, 64.0
+    rng = np.random.default_rng(6)
+    ratios = []
+    for _ in range(4):
+        _, p, nm = pm.power_of_mesh(rng.standard_normal((n, n, n)), box)
+        ratios.append(p[nm > 200] / (box ** 3 / n ** 3))
+    assert abs(np.mean(ratios) - 1.0) < 0.02
