@@ -1,0 +1,190 @@
+/*
+ * pmgb.h -- C ABI of the GB300 particle-mesh (PM) library.
+ *
+ * The library implements the hot path of the differentiable cosmological
+ * particle-mesh method of pmwd (arXiv:2211.09958): a PM force evaluation per
+ * time step inside growth-factor kick-drift-kick (KDK) integration (paper,
+ * Summary: "particle-mesh (PM) simulation"), and the adjoint method that
+ * integrates backward in time by reversing the trajectory instead of storing
+ * it (Summary; Statement of Need: adjoint method, reverse time integration,
+ * discretize-then-optimize).  The paper prints no equations; the operations
+ * below are its prose written in the standard comoving PM form:
+ *
+ *   units      box L [Mpc/h], H0 = 1, flat LCDM, E(a)^2 = Om a^-3 + 1 - Om
+ *   lattice    q_i = i L / n_p + h / 2 (half a mesh cell h = L / n_m off the
+ *              mesh nodes), lattice order: i = (ix n_p + iy) n_p + iz
+ *   state      displacement s = x - q [Mpc/h], momentum p = a^3 E dx/da
+ *   density    delta(c) = alpha sum_i W(x_i - c) - 1, CIC weights W,
+ *              alpha = (n_m / n_p)^3, periodic
+ *   force      F_j(k) = i k_j (3/2) Om delta(k) / k^2, zero at k = 0 and at
+ *              the Nyquist index of axis j; F_i = sum_c W(x_i - c) F(c)
+ *   step n     p += K_a[n] F(s); s += Dr[n] p; p += K_b[n] F(s), with
+ *              growth-matched factors K(a->b; c) = (g_p(b) - g_p(a)) / g_f(c),
+ *              Dr(a->b; c) = (D1(b) - D1(a)) / g_p(c), g_p = a^3 E D1',
+ *              g_f = 3/2 Om D1, steps uniform in a from a_init to a_final
+ *   ICs        unit white noise -> delta_L(k) = noise(k) sqrt(P(k) / V_c),
+ *              BBKS P(k) normalised to sigma8, 2LPT at a_init
+ *
+ * Memory: every particle or mesh pointer is caller-owned DEVICE memory,
+ * contiguous, 4-byte aligned float32 unless stated, on the device that was
+ * current at pm_create.  Particle arrays are [n_batch][n_p^3][3] (xyz
+ * innermost).  Meshes handed across the boundary are [n_batch][n_m^3]
+ * (z fastest).  Host outputs are marked "host".  The library owns its
+ * scratch meshes, cuFFT plans and coefficient tables and frees them in
+ * pm_destroy.
+ *
+ * Streams: every call enqueues its work on the context stream (pm_set_stream,
+ * default: the legacy default stream) and returns without waiting, except
+ * calls that fill host outputs, which synchronise that stream before
+ * returning.
+ *
+ * Errors: calls return PM_OK (0) or a negative PM_E* code and never abort or
+ * trap; pm_last_error gives a message.  After an error the outputs of that
+ * call are unspecified and the context stays usable.
+ */
+#ifndef PMGB_H
+#define PMGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PM_OK 0
+#define PM_EINVAL (-1)    /* bad size, NULL pointer or argument            */
+#define PM_ENOMEM (-2)    /* device or host allocation failed              */
+#define PM_ECUDA (-3)     /* a CUDA runtime call or launch failed          */
+#define PM_ECUFFT (-4)    /* a cuFFT call failed                           */
+#define PM_ERANGE (-5)    /* sizes overflow the supported index range      */
+#define PM_ESTATE (-6)    /* call not valid in the context's state         */
+
+/* pm_adjoint_integrate flag: the caller guarantees mu (the cotangent of the
+ * final momentum) is zero, so the VJP of the last half kick is skipped. */
+#define PM_ADJ_MU_ZERO 1u
+
+typedef struct pm_ctx pm_ctx;
+
+typedef struct pm_config {
+    int32_t n_p;        /* particles per side of each simulation; even, >= 2  */
+    int32_t n_m;        /* mesh cells per side; even, >= 4, <= 4096           */
+    int32_t n_batch;    /* independent simulations sharing the geometry, >= 1 */
+    int32_t n_steps;    /* KDK steps from a_init to a_final, >= 1             */
+    double box;         /* L [Mpc/h], > 0                                     */
+    double a_init;      /* start scale factor (2LPT), 0 < a_init < a_final    */
+    double a_final;     /* end scale factor                                   */
+    double h;           /* dimensionless Hubble parameter (BBKS shape Om h)   */
+    double n_s;         /* primordial spectral index                          */
+    const double *omega_m; /* host [n_batch]: matter density, (0, 1]         */
+    const double *sigma8;  /* host [n_batch]: amplitude at a = 1, > 0         */
+} pm_config;
+
+/* Create a context: validates cfg, computes the FP64 growth and coefficient
+ * tables on the host, allocates the scratch meshes and creates the cuFFT
+ * plans.  *out receives the context (NULL on error). */
+int pm_create(const pm_config *cfg, pm_ctx **out);
+
+/* Free everything the context owns.  NULL is accepted. */
+int pm_destroy(pm_ctx *ctx);
+
+/* Message of the last error on ctx (or of the last failed pm_create when
+ * ctx is NULL).  The string is owned by the library. */
+const char *pm_last_error(const pm_ctx *ctx);
+
+/* Set the CUDA stream (a cudaStream_t passed as void*) used by later calls. */
+int pm_set_stream(pm_ctx *ctx, void *stream);
+
+/* Replace the cosmology of every simulation (host [n_batch] arrays) and
+ * recompute the host tables. */
+int pm_set_cosmology(pm_ctx *ctx, const double *omega_m, const double *sigma8);
+
+/* Host copy of the KDK factors: out[b][n][0..2] = K_a, Dr, K_b of step n,
+ * and (if dout != NULL) their derivatives with respect to Om. */
+int pm_get_coefficients(pm_ctx *ctx, double *out, double *dout);
+
+/* init_lpt -- 2LPT initial conditions at a_init (paper: initial conditions
+ * of the Universe as optimisation variables, Statement of Need).
+ *   noise  device [n_batch][n_p^3] unit white noise, or NULL to draw it on
+ *          the device with Philox4x32-10 (key = seed + b, counter = site)
+ *          and Box-Muller.
+ *   s, p   device [n_batch][n_p^3][3] outputs (displacement, momentum). */
+int pm_init_lpt(pm_ctx *ctx, const float *noise, uint64_t seed, float *s, float *p);
+
+/* Adjoint of pm_init_lpt: cotangents (lam, mu) of (s, p) -> cotangent of the
+ * noise and of (Om, sigma8).
+ *   noise  as in pm_init_lpt (NULL: regenerate from seed)
+ *   lam,mu device [n_batch][n_p^3][3] inputs
+ *   dnoise device [n_batch][n_p^3] output (may be NULL)
+ *   dcosmo host [n_batch][2] output: dL/dOm, dL/dsigma8 of this stage. */
+int pm_init_lpt_adjoint(pm_ctx *ctx, const float *noise, uint64_t seed,
+                        const float *lam, const float *mu,
+                        float *dnoise, double *dcosmo);
+
+/* pm_force -- PM gravity on each particle: CIC paint, real FFT, Green's
+ * function times gradient, inverse FFTs, CIC read (paper: PM force).
+ *   s  device [n_batch][n_p^3][3] input; f same shape output. */
+int pm_force(pm_ctx *ctx, const float *s, float *f);
+
+/* kdk_step -- one KDK step n (0 <= n < n_steps) in place:
+ * (s_n, p_n, f = F(s_n)) -> (s_{n+1}, p_{n+1}, F(s_{n+1})). */
+int pm_kdk_step(pm_ctx *ctx, int32_t step, float *s, float *p, float *f);
+
+/* integrate -- steps [step_begin, step_end) in place: (s, p) at
+ * a[step_begin] -> (s, p) at a[step_end]; f receives F(s) at a[step_end].
+ * Kicks of adjacent steps are merged; step_end - step_begin + 1 force
+ * evaluations. */
+int pm_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end,
+                 float *s, float *p, float *f);
+
+/* adjoint_integrate -- reverse-time adjoint of pm_integrate over the same
+ * steps (paper: adjoint method with reverse time integration,
+ * discretize-then-optimize).  In: the state (s, p) at a[step_end] with
+ * f = F(s), the cotangents lam = dL/ds, mu = dL/dp there.  Out, in place:
+ * (s, p) reconstructed at a[step_begin], (lam, mu) = dL/d(s, p) there.
+ * f is read only.  domega (host [n_batch], may be NULL) receives dL/dOm of
+ * the dynamics (through the KDK factors and the force prefactor).
+ * flags: PM_ADJ_MU_ZERO or 0. */
+int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end,
+                         float *s, float *p, const float *f,
+                         float *lam, float *mu, double *domega, uint32_t flags);
+
+/* CIC density contrast alpha sum W - 1 of the particles at s.
+ *   delta  device [n_batch][n_m^3] output. */
+int pm_density(pm_ctx *ctx, const float *s, float *delta);
+
+/* Adjoint of pm_density: ds = sum_c ddelta(c) d delta(c)/ds.
+ *   ddelta device [n_batch][n_m^3] input; ds [n_batch][n_p^3][3] output. */
+int pm_density_adjoint(pm_ctx *ctx, const float *s, const float *ddelta, float *ds);
+
+/* MSE of the final CIC density against a target field (the loss of the
+ * gradient workload) and its adjoint seed:
+ *   L_b = n_m^-3 sum_c (delta_b(c) - target_b(c))^2,
+ *   dlds = dL/ds = sum_c 2 (delta - target)(c) / n_m^3 d delta(c)/ds.
+ *   target device [n_batch][n_m^3]; loss host [n_batch];
+ *   dlds device [n_batch][n_p^3][3] output or NULL. */
+int pm_mse_loss(pm_ctx *ctx, const float *s, const float *target, double *loss, float *dlds);
+
+/* power_spectrum -- binned power of the CIC density contrast (paper:
+ * summary statistics such as the power spectrum, Statement of Need).
+ * Bins b = 0 .. n_m/2 - 1 have edges (b + 1/2) k_F .. (b + 3/2) k_F,
+ * k_F = 2 pi / L, over the full k space; k = 0 excluded; no shot-noise or
+ * window correction.  P_b = L^3 / n_m^6 <|delta_k|^2>.
+ *   k_mean, power, n_modes  host [n_batch][n_m/2] outputs. */
+int pm_power_spectrum(pm_ctx *ctx, const float *s, double *k_mean,
+                      double *power, double *n_modes);
+
+/* Host-only (needs no GPU): the FP64 tables pm_create would compute.
+ *   kdk   [n_batch][n_steps][3]  K_a, Dr, K_b per step       (may be NULL)
+ *   dkdk  same shape, d/dOm                                    (may be NULL)
+ *   lpt   [n_batch][4]  D1, D2, g1 = a^3 E D1', g2 = a^3 E D2' at a_init
+ *   amp   [n_batch][2]  P(k) amplitude A and d ln A / dOm      (may be NULL) */
+int pm_host_coefficients(const pm_config *cfg, double *kdk, double *dkdk, double *lpt, double *amp);
+
+/* Device-kernel launch counter since pm_create (for benchmarking). */
+int64_t pm_launch_count(const pm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMGB_H */

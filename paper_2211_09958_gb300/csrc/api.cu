@@ -1,0 +1,721 @@
+// C ABI of the GB300 PM library: context, cuFFT plans and the pipelines
+// (force, KDK step, integration, reverse-time adjoint, initial conditions,
+// density, power spectrum).  See include/pmgb.h for the contract.
+
+#include <cufft.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pmgb.h"
+#include "pm_internal.h"
+
+using namespace pmgb;
+
+namespace {
+
+constexpr int kMeshFields = 4;   // scratch meshes: density/force (0..2), adjoint psi (3)
+constexpr int kLatFields = 14;   // IC lattice fields (see pm_init_lpt_adjoint)
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct pm_ctx {
+    Params P;
+    std::vector<double> om, s8;
+    std::vector<HostTables> tabs;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Geom g{};
+    int64_t mesh_pad = 0;  // floats of one padded n_m^3 field
+    int64_t lat_pad = 0;   // floats of one padded n_p^3 field
+    float *mesh = nullptr;
+    float *lat = nullptr;
+    float4 *d_table = nullptr;
+    float *d_pref = nullptr;
+    float4 *d_fac = nullptr;
+    LinParams *d_lin = nullptr;
+    double *d_red = nullptr;
+    double *d_pk = nullptr;
+    double *d_lred = nullptr;
+    cufftHandle r2c = 0, c2r = 0, lr2c = 0, lc2r = 0;
+    bool have_plans = false;
+    void *work = nullptr;
+    std::string err;
+    int64_t launches = 0;
+};
+
+namespace {
+
+int fail(pm_ctx *ctx, int code, const std::string &msg) {
+    if (ctx)
+        ctx->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+#define PM_CUDA(ctx, x)                                                                                   \
+    do {                                                                                                  \
+        cudaError_t e_ = (x);                                                                             \
+        if (e_ != cudaSuccess) return fail(ctx, PM_ECUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define PM_LAUNCH(ctx, x)                                                                                 \
+    do {                                                                                                  \
+        cudaError_t e_ = (x);                                                                             \
+        (ctx)->launches++;                                                                                \
+        if (e_ != cudaSuccess) return fail(ctx, PM_ECUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define PM_FFT(ctx, x)                                                                     \
+    do {                                                                                   \
+        cufftResult r_ = (x);                                                              \
+        if (r_ != CUFFT_SUCCESS)                                                           \
+            return fail(ctx, PM_ECUFFT, std::string(#x ": cufft error ") + std::to_string((int)r_)); \
+    } while (0)
+
+#define PM_TRY(x)              \
+    do {                       \
+        int rc_ = (x);         \
+        if (rc_ != PM_OK) return rc_; \
+    } while (0)
+
+int64_t padded(int n) { return (int64_t)n * n * 2 * (n / 2 + 1); }
+
+int make_plan(pm_ctx *ctx, cufftHandle *h, int n, bool r2c, long long batch, size_t *ws) {
+    PM_FFT(ctx, cufftCreate(h));
+    PM_FFT(ctx, cufftSetAutoAllocation(*h, 0));
+    long long dims[3] = {n, n, n};
+    long long rembed[3] = {n, n, 2LL * (n / 2 + 1)};
+    long long cembed[3] = {n, n, n / 2 + 1};
+    const long long rdist = (long long)n * n * 2 * (n / 2 + 1);
+    const long long cdist = (long long)n * n * (n / 2 + 1);
+    if (r2c)
+        PM_FFT(ctx, cufftMakePlanMany64(*h, 3, dims, rembed, 1, rdist, cembed, 1, cdist, CUFFT_R2C, batch, ws));
+    else
+        PM_FFT(ctx, cufftMakePlanMany64(*h, 3, dims, cembed, 1, cdist, rembed, 1, rdist, CUFFT_C2R, batch, ws));
+    return PM_OK;
+}
+
+int upload_tables(pm_ctx *ctx) {
+    const int B = ctx->P.n_batch, N = ctx->P.n_steps;
+    ctx->tabs.resize(B);
+    for (int b = 0; b < B; ++b) host_tables(ctx->P, ctx->om[b], ctx->s8[b], &ctx->tabs[b]);
+    std::vector<float4> table((size_t)N * B);
+    std::vector<float> pref(B);
+    std::vector<float4> fac(B);
+    std::vector<LinParams> lin(B);
+    const double n3 = (double)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
+    const double vc = std::pow(ctx->P.box / ctx->P.n_p, 3);
+    for (int b = 0; b < B; ++b) {
+        const HostTables &t = ctx->tabs[b];
+        for (int n = 0; n < N; ++n) {
+            const double merged = t.ka[n] + (n > 0 ? t.kb[n - 1] : 0.0);
+            table[(size_t)n * B + b] = make_float4((float)t.ka[n], (float)t.dr[n], (float)t.kb[n], (float)merged);
+        }
+        pref[b] = (float)(1.5 * ctx->om[b] / n3);
+        fac[b] = make_float4((float)t.lpt[0], (float)t.lpt[1], (float)t.lpt[2], (float)t.lpt[3]);
+        lin[b] = LinParams{t.amp, ctx->om[b], ctx->P.h, ctx->P.n_s, t.dlnamp, 1.0 / vc};
+    }
+    PM_CUDA(ctx, cudaMemcpy(ctx->d_table, table.data(), sizeof(float4) * table.size(), cudaMemcpyHostToDevice));
+    PM_CUDA(ctx, cudaMemcpy(ctx->d_pref, pref.data(), sizeof(float) * B, cudaMemcpyHostToDevice));
+    PM_CUDA(ctx, cudaMemcpy(ctx->d_fac, fac.data(), sizeof(float4) * B, cudaMemcpyHostToDevice));
+    PM_CUDA(ctx, cudaMemcpy(ctx->d_lin, lin.data(), sizeof(LinParams) * B, cudaMemcpyHostToDevice));
+    return PM_OK;
+}
+
+int check_cosmology(pm_ctx *ctx, const double *om, const double *s8, int B) {
+    if (!om || !s8) return fail(ctx, PM_EINVAL, "omega_m and sigma8 must be host arrays of n_batch values");
+    for (int b = 0; b < B; ++b) {
+        if (!(om[b] > 0.0 && om[b] <= 1.0)) return fail(ctx, PM_EINVAL, "omega_m must be in (0, 1]");
+        if (!(s8[b] > 0.0)) return fail(ctx, PM_EINVAL, "sigma8 must be > 0");
+    }
+    return PM_OK;
+}
+
+// --------------------------------------------------------------- pieces --
+
+MeshRef mesh_ref(pm_ctx *ctx) {
+    return MeshRef{ctx->mesh, ctx->mesh_pad * ctx->P.n_batch, ctx->mesh_pad, 2 * (ctx->P.n_m / 2 + 1)};
+}
+
+Spec mesh_spec(pm_ctx *ctx) {
+    const int64_t modes = ctx->mesh_pad / 2;
+    return Spec{reinterpret_cast<float2 *>(ctx->mesh), modes * ctx->P.n_batch, modes, ctx->P.n_m, ctx->P.n_batch,
+                (float)(2.0 * M_PI / ctx->P.box)};
+}
+
+MeshRef lat_ref(pm_ctx *ctx) {
+    return MeshRef{ctx->lat, ctx->lat_pad * ctx->P.n_batch, ctx->lat_pad, 2 * (ctx->P.n_p / 2 + 1)};
+}
+
+Spec lat_spec(pm_ctx *ctx) {
+    const int64_t modes = ctx->lat_pad / 2;
+    return Spec{reinterpret_cast<float2 *>(ctx->lat), modes * ctx->P.n_batch, modes, ctx->P.n_p, ctx->P.n_batch,
+                (float)(2.0 * M_PI / ctx->P.box)};
+}
+
+float *mesh_field(pm_ctx *ctx, int f) { return ctx->mesh + (int64_t)f * ctx->mesh_pad * ctx->P.n_batch; }
+float *lat_field(pm_ctx *ctx, int f) { return ctx->lat + (int64_t)f * ctx->lat_pad * ctx->P.n_batch; }
+
+int fft_fields(pm_ctx *ctx, cufftHandle plan, bool r2c, float *base, int64_t fstride, int f0, int nf) {
+    for (int f = f0; f < f0 + nf; ++f) {
+        float *p = base + (int64_t)f * fstride;
+        if (r2c)
+            PM_FFT(ctx, cufftExecR2C(plan, p, reinterpret_cast<cufftComplex *>(p)));
+        else
+            PM_FFT(ctx, cufftExecC2R(plan, reinterpret_cast<cufftComplex *>(p), p));
+    }
+    return PM_OK;
+}
+
+int mesh_r2c(pm_ctx *ctx, int f0, int nf) {
+    return fft_fields(ctx, ctx->r2c, true, ctx->mesh, ctx->mesh_pad * ctx->P.n_batch, f0, nf);
+}
+int mesh_c2r(pm_ctx *ctx, int f0, int nf) {
+    return fft_fields(ctx, ctx->c2r, false, ctx->mesh, ctx->mesh_pad * ctx->P.n_batch, f0, nf);
+}
+int lat_r2c(pm_ctx *ctx, int f0, int nf) {
+    return fft_fields(ctx, ctx->lr2c, true, ctx->lat, ctx->lat_pad * ctx->P.n_batch, f0, nf);
+}
+int lat_c2r(pm_ctx *ctx, int f0, int nf) {
+    return fft_fields(ctx, ctx->lc2r, false, ctx->lat, ctx->lat_pad * ctx->P.n_batch, f0, nf);
+}
+
+PaintArgs paint_args(pm_ctx *ctx, float *s) {
+    PaintArgs a{};
+    a.g = ctx->g;
+    a.s = s;
+    a.mesh = mesh_ref(ctx);
+    a.table = ctx->d_table;
+    a.red_bstride = 2 * (ctx->P.n_steps + 1);
+    return a;
+}
+
+ReadArgs read_args(pm_ctx *ctx, float *s) {
+    ReadArgs a{};
+    a.g = ctx->g;
+    a.s = s;
+    a.mesh = mesh_ref(ctx);
+    a.table = ctx->d_table;
+    a.red_bstride = 2 * (ctx->P.n_steps + 1);
+    return a;
+}
+
+// Paint (after zeroing the painted fields), forward transform, spectral
+// multiply and inverse transforms; leaves the force meshes (and psi for the
+// adjoint) in the scratch fields.
+int force_meshes(pm_ctx *ctx, int paint_mode, const PaintArgs &pa) {
+    const bool adj = paint_mode == PAINT_ADJ || paint_mode == PAINT_ADJ_DRIFT;
+    const int nf = adj ? 4 : 1;
+    PM_CUDA(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * ctx->P.n_batch * nf, ctx->stream));
+    PM_LAUNCH(ctx, launch_paint(paint_mode, pa, ctx->stream));
+    PM_TRY(mesh_r2c(ctx, 0, nf));
+    PM_LAUNCH(ctx, launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream));
+    PM_TRY(mesh_c2r(ctx, 0, adj ? 4 : 3));
+    return PM_OK;
+}
+
+int check_ptr(pm_ctx *ctx, const void *p, const char *name) {
+    if (!p) return fail(ctx, PM_EINVAL, std::string(name) + " must not be NULL");
+    if ((uintptr_t)p % 4) return fail(ctx, PM_EINVAL, std::string(name) + " must be 4-byte aligned");
+    return PM_OK;
+}
+
+int ensure_lattice(pm_ctx *ctx) {
+    if (ctx->lat) return PM_OK;
+    const size_t bytes = sizeof(float) * (size_t)ctx->lat_pad * ctx->P.n_batch * kLatFields;
+    if (cudaMalloc(&ctx->lat, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->lat = nullptr;
+        return fail(ctx, PM_ENOMEM, "cannot allocate the initial-condition lattice fields");
+    }
+    return PM_OK;
+}
+
+// White noise -> s1 (fields 0..2), phi (3..8), S (9), s2 (10..12).
+int lpt_forward_fields(pm_ctx *ctx, const float *noise, uint64_t seed) {
+    PM_TRY(ensure_lattice(ctx));
+    const int np = ctx->P.n_p, B = ctx->P.n_batch;
+    MeshRef lr = lat_ref(ctx);
+    PM_LAUNCH(ctx, launch_noise(noise, seed, lr, np, B, ctx->stream));
+    PM_TRY(lat_r2c(ctx, 0, 1));
+    PM_LAUNCH(ctx, launch_lpt_linear(lat_spec(ctx), ctx->d_lin, ctx->stream));
+    PM_TRY(lat_c2r(ctx, 0, 9));
+    PM_LAUNCH(ctx, launch_lpt_source(lr, np, B, 3, 9, ctx->stream));
+    PM_TRY(lat_r2c(ctx, 9, 1));
+    PM_LAUNCH(ctx, launch_lpt_second(lat_spec(ctx), 9, 10, -1.f, ctx->stream));
+    PM_TRY(lat_c2r(ctx, 10, 3));
+    return PM_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI ===
+
+extern "C" {
+
+const char *pm_last_error(const pm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int64_t pm_launch_count(const pm_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int pm_create(const pm_config *cfg, pm_ctx **out) {
+    if (!out) return fail(nullptr, PM_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, PM_EINVAL, "cfg must not be NULL");
+    const pm_config &c = *cfg;
+    if (c.n_p < 2 || c.n_p % 2 || c.n_p > 4096) return fail(nullptr, PM_EINVAL, "n_p must be even, 2..4096");
+    if (c.n_m < 4 || c.n_m % 2 || c.n_m > 4096) return fail(nullptr, PM_EINVAL, "n_m must be even, 4..4096");
+    if (c.n_batch < 1 || c.n_batch > 65535) return fail(nullptr, PM_EINVAL, "n_batch must be 1..65535");
+    if (c.n_steps < 1 || c.n_steps > 100000) return fail(nullptr, PM_EINVAL, "n_steps must be 1..100000");
+    if (!(c.box > 0)) return fail(nullptr, PM_EINVAL, "box must be > 0");
+    if (!(c.a_init > 0 && c.a_final > c.a_init)) return fail(nullptr, PM_EINVAL, "need 0 < a_init < a_final");
+    if (!(c.h > 0)) return fail(nullptr, PM_EINVAL, "h must be > 0");
+    {
+        int rc = check_cosmology(nullptr, c.omega_m, c.sigma8, c.n_batch);
+        if (rc) return rc;
+    }
+    const int64_t npart = (int64_t)c.n_p * c.n_p * c.n_p;
+    if (npart * c.n_batch * 3 > ((int64_t)1 << 40)) return fail(nullptr, PM_ERANGE, "too many particles");
+
+    pm_ctx *ctx = new pm_ctx();
+    ctx->P = Params{c.n_p, c.n_m, c.n_batch, c.n_steps, c.box, c.a_init, c.a_final, c.h, c.n_s};
+    ctx->om.assign(c.omega_m, c.omega_m + c.n_batch);
+    ctx->s8.assign(c.sigma8, c.sigma8 + c.n_batch);
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        delete ctx;
+        return fail(nullptr, PM_ECUDA, "no CUDA device");
+    }
+    ctx->g.np = c.n_p;
+    ctx->g.nm = c.n_m;
+    ctx->g.nb = c.n_batch;
+    ctx->g.npart = npart;
+    ctx->g.ratio = (c.n_m % c.n_p == 0) ? c.n_m / c.n_p : 0;
+    ctx->g.inv_np = 1.0f / c.n_p;
+    ctx->g.inv_h = (float)(c.n_m / c.box);
+    ctx->g.alpha = (float)std::pow((double)c.n_m / c.n_p, 3);
+    ctx->mesh_pad = padded(c.n_m);
+    ctx->lat_pad = padded(c.n_p);
+
+    auto bail = [&](int code) {
+        std::string msg = ctx->err;
+        pm_destroy(ctx);
+        g_create_error = msg;
+        return code;
+    };
+    const int B = c.n_batch;
+    if (cudaMalloc(&ctx->mesh, sizeof(float) * (size_t)ctx->mesh_pad * B * kMeshFields) != cudaSuccess ||
+        cudaMalloc(&ctx->d_table, sizeof(float4) * (size_t)c.n_steps * B) != cudaSuccess ||
+        cudaMalloc(&ctx->d_pref, sizeof(float) * B) != cudaSuccess ||
+        cudaMalloc(&ctx->d_fac, sizeof(float4) * B) != cudaSuccess ||
+        cudaMalloc(&ctx->d_lin, sizeof(LinParams) * B) != cudaSuccess ||
+        cudaMalloc(&ctx->d_red, sizeof(double) * B * 2 * (c.n_steps + 1)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_pk, sizeof(double) * B * 3 * (c.n_m / 2)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_lred, sizeof(double) * B * 8) != cudaSuccess) {
+        cudaGetLastError();
+        fail(ctx, PM_ENOMEM, "device allocation failed in pm_create");
+        return bail(PM_ENOMEM);
+    }
+    int rc = upload_tables(ctx);
+    if (rc) return bail(rc);
+    size_t ws[4] = {0, 0, 0, 0};
+    if ((rc = make_plan(ctx, &ctx->r2c, c.n_m, true, B, &ws[0])) ||
+        (rc = make_plan(ctx, &ctx->c2r, c.n_m, false, B, &ws[1])) ||
+        (rc = make_plan(ctx, &ctx->lr2c, c.n_p, true, B, &ws[2])) ||
+        (rc = make_plan(ctx, &ctx->lc2r, c.n_p, false, B, &ws[3])))
+        return bail(rc);
+    ctx->have_plans = true;
+    size_t wmax = 0;
+    for (size_t w : ws) wmax = w > wmax ? w : wmax;
+    if (wmax) {
+        if (cudaMalloc(&ctx->work, wmax) != cudaSuccess) {
+            cudaGetLastError();
+            fail(ctx, PM_ENOMEM, "cannot allocate the cuFFT work area");
+            return bail(PM_ENOMEM);
+        }
+    }
+    for (cufftHandle h : {ctx->r2c, ctx->c2r, ctx->lr2c, ctx->lc2r}) {
+        if (cufftSetWorkArea(h, ctx->work) != CUFFT_SUCCESS) {
+            fail(ctx, PM_ECUFFT, "cufftSetWorkArea failed");
+            return bail(PM_ECUFFT);
+        }
+    }
+    rc = pm_set_stream(ctx, nullptr);
+    if (rc) return bail(rc);
+    *out = ctx;
+    return PM_OK;
+}
+
+int pm_destroy(pm_ctx *ctx) {
+    if (!ctx) return PM_OK;
+    DeviceGuard guard(ctx->device);
+    if (ctx->have_plans || ctx->r2c) {
+        for (cufftHandle h : {ctx->r2c, ctx->c2r, ctx->lr2c, ctx->lc2r})
+            if (h) cufftDestroy(h);
+    }
+    for (void *p : {(void *)ctx->mesh, (void *)ctx->lat, (void *)ctx->d_table, (void *)ctx->d_pref,
+                    (void *)ctx->d_fac, (void *)ctx->d_lin, (void *)ctx->d_red, (void *)ctx->d_pk,
+                    (void *)ctx->d_lred, ctx->work})
+        if (p) cudaFree(p);
+    delete ctx;
+    return PM_OK;
+}
+
+int pm_set_stream(pm_ctx *ctx, void *stream) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    for (cufftHandle h : {ctx->r2c, ctx->c2r, ctx->lr2c, ctx->lc2r}) PM_FFT(ctx, cufftSetStream(h, ctx->stream));
+    return PM_OK;
+}
+
+int pm_set_cosmology(pm_ctx *ctx, const double *omega_m, const double *sigma8) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    DeviceGuard guard(ctx->device);
+    PM_TRY(check_cosmology(ctx, omega_m, sigma8, ctx->P.n_batch));
+    PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->om.assign(omega_m, omega_m + ctx->P.n_batch);
+    ctx->s8.assign(sigma8, sigma8 + ctx->P.n_batch);
+    return upload_tables(ctx);
+}
+
+int pm_get_coefficients(pm_ctx *ctx, double *out, double *dout) {
+    if (!ctx || !out) return fail(ctx, PM_EINVAL, "ctx and out must not be NULL");
+    const int N = ctx->P.n_steps;
+    for (int b = 0; b < ctx->P.n_batch; ++b)
+        for (int n = 0; n < N; ++n) {
+            const HostTables &t = ctx->tabs[b];
+            double *o = out + ((size_t)b * N + n) * 3;
+            o[0] = t.ka[n];
+            o[1] = t.dr[n];
+            o[2] = t.kb[n];
+            if (dout) {
+                double *d = dout + ((size_t)b * N + n) * 3;
+                d[0] = t.dka[n];
+                d[1] = t.ddr[n];
+                d[2] = t.dkb[n];
+            }
+        }
+    return PM_OK;
+}
+
+int pm_host_coefficients(const pm_config *cfg, double *kdk, double *dkdk, double *lpt, double *amp) {
+    if (!cfg) return fail(nullptr, PM_EINVAL, "cfg must not be NULL");
+    if (cfg->n_batch < 1 || cfg->n_steps < 1 || !(cfg->a_init > 0 && cfg->a_final > cfg->a_init))
+        return fail(nullptr, PM_EINVAL, "bad n_batch, n_steps or a range");
+    {
+        int rc = check_cosmology(nullptr, cfg->omega_m, cfg->sigma8, cfg->n_batch);
+        if (rc) return rc;
+    }
+    Params P{cfg->n_p, cfg->n_m, cfg->n_batch, cfg->n_steps, cfg->box, cfg->a_init, cfg->a_final, cfg->h, cfg->n_s};
+    const int N = cfg->n_steps;
+    for (int b = 0; b < cfg->n_batch; ++b) {
+        HostTables t;
+        host_tables(P, cfg->omega_m[b], cfg->sigma8[b], &t);
+        for (int n = 0; n < N; ++n) {
+            const size_t o = ((size_t)b * N + n) * 3;
+            if (kdk) {
+                kdk[o] = t.ka[n];
+                kdk[o + 1] = t.dr[n];
+                kdk[o + 2] = t.kb[n];
+            }
+            if (dkdk) {
+                dkdk[o] = t.dka[n];
+                dkdk[o + 1] = t.ddr[n];
+                dkdk[o + 2] = t.dkb[n];
+            }
+        }
+        if (lpt)
+            for (int i = 0; i < 4; ++i) lpt[4 * b + i] = t.lpt[i];
+        if (amp) {
+            amp[2 * b] = t.amp;
+            amp[2 * b + 1] = t.dlnamp;
+        }
+    }
+    return PM_OK;
+}
+
+int pm_force(pm_ctx *ctx, const float *s, float *f) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    PM_TRY(check_ptr(ctx, f, "f"));
+    DeviceGuard guard(ctx->device);
+    PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
+    PM_TRY(force_meshes(ctx, PAINT_DENSITY, pa));
+    ReadArgs ra = read_args(ctx, const_cast<float *>(s));
+    ra.f = f;
+    PM_LAUNCH(ctx, launch_read(READ_FORCE, ra, ctx->stream));
+    return PM_OK;
+}
+
+int pm_kdk_step(pm_ctx *ctx, int32_t step, float *s, float *p, float *f) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    PM_TRY(check_ptr(ctx, p, "p"));
+    PM_TRY(check_ptr(ctx, f, "f"));
+    if (step < 0 || step >= ctx->P.n_steps) return fail(ctx, PM_EINVAL, "step out of range");
+    DeviceGuard guard(ctx->device);
+    PaintArgs pa = paint_args(ctx, s);
+    pa.p = p;
+    pa.f = f;
+    pa.step = step;
+    PM_TRY(force_meshes(ctx, PAINT_KDK_PRE, pa));
+    ReadArgs ra = read_args(ctx, s);
+    ra.p = p;
+    ra.f = f;
+    ra.kick_step = step;
+    ra.kick_sel = KICK_B;
+    PM_LAUNCH(ctx, launch_read(READ_HALF_KICK, ra, ctx->stream));
+    return PM_OK;
+}
+
+int pm_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, float *p, float *f) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    PM_TRY(check_ptr(ctx, p, "p"));
+    PM_TRY(check_ptr(ctx, f, "f"));
+    if (step_begin < 0 || step_end > ctx->P.n_steps || step_begin >= step_end)
+        return fail(ctx, PM_EINVAL, "need 0 <= step_begin < step_end <= n_steps");
+    DeviceGuard guard(ctx->device);
+    PaintArgs pa = paint_args(ctx, s);
+    ReadArgs ra = read_args(ctx, s);
+    ra.p = p;
+    ra.f = f;
+    for (int n = step_begin; n < step_end; ++n) {
+        PM_TRY(force_meshes(ctx, PAINT_DENSITY, pa));
+        ra.kick_step = n;
+        ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
+        ra.drift_step = n;
+        PM_LAUNCH(ctx, launch_read(READ_KICK_DRIFT, ra, ctx->stream));
+    }
+    PM_TRY(force_meshes(ctx, PAINT_DENSITY, pa));
+    ra.kick_step = step_end - 1;
+    ra.kick_sel = KICK_B;
+    PM_LAUNCH(ctx, launch_read(READ_HALF_KICK, ra, ctx->stream));
+    return PM_OK;
+}
+
+int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, float *p, const float *f,
+                         float *lam, float *mu, double *domega, uint32_t flags) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    PM_TRY(check_ptr(ctx, p, "p"));
+    PM_TRY(check_ptr(ctx, f, "f"));
+    PM_TRY(check_ptr(ctx, lam, "lam"));
+    PM_TRY(check_ptr(ctx, mu, "mu"));
+    if (step_begin < 0 || step_end > ctx->P.n_steps || step_begin >= step_end)
+        return fail(ctx, PM_EINVAL, "need 0 <= step_begin < step_end <= n_steps");
+    DeviceGuard guard(ctx->device);
+    const int N = ctx->P.n_steps, B = ctx->P.n_batch;
+    PM_CUDA(ctx, cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * B * 2 * (N + 1), ctx->stream));
+    const int last = step_end - 1;
+    if (flags & PM_ADJ_MU_ZERO) {
+        PM_LAUNCH(ctx, launch_kick(ctx->g, p, f, ctx->d_table, last, KICK_B, -1.f, ctx->stream));
+    } else {
+        PaintArgs pa = paint_args(ctx, s);
+        pa.mu = mu;
+        PM_TRY(force_meshes(ctx, PAINT_ADJ, pa));
+        ReadArgs ra = read_args(ctx, s);
+        ra.p = p;
+        ra.lam = lam;
+        ra.mu = mu;
+        ra.kick_step = last;
+        ra.kick_sel = KICK_B;
+        ra.red = ctx->d_red + 2 * N;
+        PM_LAUNCH(ctx, launch_read(READ_ADJ, ra, ctx->stream));
+    }
+    for (int n = last; n >= step_begin; --n) {
+        PaintArgs pa = paint_args(ctx, s);
+        pa.p = p;
+        pa.lam = lam;
+        pa.mu = mu;
+        pa.step = n;
+        pa.red = ctx->d_red + 2 * n + 1;
+        PM_TRY(force_meshes(ctx, PAINT_ADJ_DRIFT, pa));
+        ReadArgs ra = read_args(ctx, s);
+        ra.p = p;
+        ra.lam = lam;
+        ra.mu = mu;
+        ra.kick_step = n;
+        ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
+        ra.red = ctx->d_red + 2 * n;
+        PM_LAUNCH(ctx, launch_read(READ_ADJ, ra, ctx->stream));
+    }
+    if (domega) {
+        std::vector<double> red((size_t)B * 2 * (N + 1));
+        PM_CUDA(ctx, cudaMemcpyAsync(red.data(), ctx->d_red, sizeof(double) * red.size(), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+        PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int b = 0; b < B; ++b) {
+            const HostTables &t = ctx->tabs[b];
+            const double om = ctx->om[b];
+            const double *r = red.data() + (size_t)b * 2 * (N + 1);
+            double acc = 0.0;
+            for (int n = step_begin; n < step_end; ++n) {
+                const double c = t.ka[n] + (n > step_begin ? t.kb[n - 1] : 0.0);
+                const double dc = t.dka[n] + (n > step_begin ? t.dkb[n - 1] : 0.0);
+                acc += r[2 * n] * (dc + c / om) + r[2 * n + 1] * t.ddr[n];
+            }
+            acc += r[2 * N] * (t.dkb[last] + t.kb[last] / om);
+            domega[b] = acc;
+        }
+    }
+    return PM_OK;
+}
+
+int pm_init_lpt(pm_ctx *ctx, const float *noise, uint64_t seed, float *s, float *p) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    PM_TRY(check_ptr(ctx, p, "p"));
+    if (noise) PM_TRY(check_ptr(ctx, noise, "noise"));
+    DeviceGuard guard(ctx->device);
+    PM_TRY(lpt_forward_fields(ctx, noise, seed));
+    PM_LAUNCH(ctx, launch_lpt_combine(lat_ref(ctx), ctx->P.n_p, ctx->P.n_batch, ctx->d_fac, s, p, ctx->stream));
+    return PM_OK;
+}
+
+int pm_init_lpt_adjoint(pm_ctx *ctx, const float *noise, uint64_t seed, const float *lam, const float *mu,
+                        float *dnoise, double *dcosmo) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, lam, "lam"));
+    PM_TRY(check_ptr(ctx, mu, "mu"));
+    if (noise) PM_TRY(check_ptr(ctx, noise, "noise"));
+    if (dnoise) PM_TRY(check_ptr(ctx, dnoise, "dnoise"));
+    DeviceGuard guard(ctx->device);
+    const int np = ctx->P.n_p, B = ctx->P.n_batch;
+    PM_TRY(lpt_forward_fields(ctx, noise, seed));
+    MeshRef lr = lat_ref(ctx);
+    PM_CUDA(ctx, cudaMemsetAsync(ctx->d_lred, 0, sizeof(double) * B * 8, ctx->stream));
+    // gs1 -> 0..2, gs2 -> 10..12, reductions (lam.s1, lam.s2, mu.s1, mu.s2)
+    PM_LAUNCH(ctx, launch_lpt_adj_seed(lr, np, B, ctx->d_fac, lam, mu, ctx->d_lred, ctx->stream));
+    // S_bar = adjoint of s2 = IDFT(-i k / k^2 DFT S)
+    PM_TRY(lat_r2c(ctx, 10, 3));
+    PM_LAUNCH(ctx, launch_lpt_adj_second(lat_spec(ctx), 10, 9, ctx->stream));
+    PM_TRY(lat_c2r(ctx, 9, 1));
+    PM_LAUNCH(ctx, launch_lpt_adj_phi(lr, np, B, ctx->stream));
+    PM_TRY(lat_r2c(ctx, 0, 9));
+    PM_LAUNCH(ctx, launch_noise(noise, seed, MeshRef{lat_field(ctx, 13), 0, ctx->lat_pad, lr.zs}, np, B,
+                                ctx->stream));
+    PM_TRY(lat_r2c(ctx, 13, 1));
+    PM_LAUNCH(ctx, launch_lpt_adj_final(lat_spec(ctx), ctx->d_lin, 13, ctx->d_lred + 4 * B, ctx->stream));
+    if (dnoise) {
+        PM_TRY(lat_c2r(ctx, 0, 1));
+        PM_LAUNCH(ctx, launch_unpad(ctx->lat, ctx->lat_pad, lr.zs, dnoise, np, B, ctx->stream));
+    }
+    if (dcosmo) {
+        std::vector<double> red((size_t)B * 8);
+        PM_CUDA(ctx, cudaMemcpyAsync(red.data(), ctx->d_lred, sizeof(double) * red.size(), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+        PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        const double n3 = (double)np * np * np;
+        for (int b = 0; b < B; ++b) {
+            const HostTables &t = ctx->tabs[b];
+            const double *g = red.data() + 4 * b;
+            const double *pr = red.data() + 4 * B + 2 * b;
+            double om = pr[1] / n3;
+            for (int i = 0; i < 4; ++i) om += g[i] * t.dlpt[i];
+            dcosmo[2 * b] = om;
+            dcosmo[2 * b + 1] = pr[0] / n3 / ctx->s8[b];
+        }
+    }
+    return PM_OK;
+}
+
+int pm_density(pm_ctx *ctx, const float *s, float *delta) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    PM_TRY(check_ptr(ctx, delta, "delta"));
+    DeviceGuard guard(ctx->device);
+    const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
+    PM_LAUNCH(ctx, launch_fill(delta, n3 * ctx->P.n_batch, -1.f, ctx->stream));
+    PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
+    pa.mesh = MeshRef{delta, 0, n3, ctx->P.n_m};
+    PM_LAUNCH(ctx, launch_paint(PAINT_DENSITY, pa, ctx->stream));
+    return PM_OK;
+}
+
+int pm_density_adjoint(pm_ctx *ctx, const float *s, const float *ddelta, float *ds) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    PM_TRY(check_ptr(ctx, ddelta, "ddelta"));
+    PM_TRY(check_ptr(ctx, ds, "ds"));
+    DeviceGuard guard(ctx->device);
+    const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
+    ReadArgs ra = read_args(ctx, const_cast<float *>(s));
+    ra.mesh = MeshRef{const_cast<float *>(ddelta), 0, n3, ctx->P.n_m};
+    ra.f = ds;
+    PM_LAUNCH(ctx, launch_read(READ_GRAD, ra, ctx->stream));
+    return PM_OK;
+}
+
+int pm_mse_loss(pm_ctx *ctx, const float *s, const float *target, double *loss, float *dlds) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    PM_TRY(check_ptr(ctx, target, "target"));
+    if (!loss) return fail(ctx, PM_EINVAL, "loss must not be NULL");
+    if (dlds) PM_TRY(check_ptr(ctx, dlds, "dlds"));
+    DeviceGuard guard(ctx->device);
+    const int B = ctx->P.n_batch;
+    PM_CUDA(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * B, ctx->stream));
+    PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
+    PM_LAUNCH(ctx, launch_paint(PAINT_DENSITY, pa, ctx->stream));
+    PM_CUDA(ctx, cudaMemsetAsync(ctx->d_pk, 0, sizeof(double) * B, ctx->stream));
+    PM_LAUNCH(ctx, launch_mse(mesh_ref(ctx), target, ctx->P.n_m, B, ctx->d_pk, ctx->stream));
+    if (dlds) {
+        ReadArgs ra = read_args(ctx, const_cast<float *>(s));
+        ra.f = dlds;
+        PM_LAUNCH(ctx, launch_read(READ_GRAD, ra, ctx->stream));
+    }
+    std::vector<double> acc(B);
+    PM_CUDA(ctx, cudaMemcpyAsync(acc.data(), ctx->d_pk, sizeof(double) * B, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const double n3 = std::pow((double)ctx->P.n_m, 3);
+    for (int b = 0; b < B; ++b) loss[b] = acc[b] / n3;
+    return PM_OK;
+}
+
+int pm_power_spectrum(pm_ctx *ctx, const float *s, double *k_mean, double *power, double *n_modes) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    if (!k_mean || !power || !n_modes) return fail(ctx, PM_EINVAL, "host outputs must not be NULL");
+    DeviceGuard guard(ctx->device);
+    const int B = ctx->P.n_batch, nb = ctx->P.n_m / 2;
+    PM_CUDA(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * B, ctx->stream));
+    PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
+    PM_LAUNCH(ctx, launch_paint(PAINT_DENSITY, pa, ctx->stream));
+    PM_TRY(mesh_r2c(ctx, 0, 1));
+    PM_CUDA(ctx, cudaMemsetAsync(ctx->d_pk, 0, sizeof(double) * B * 3 * nb, ctx->stream));
+    PM_LAUNCH(ctx, launch_power_bins(mesh_spec(ctx), ctx->d_pk, nb, ctx->stream));
+    std::vector<double> acc((size_t)B * 3 * nb);
+    PM_CUDA(ctx, cudaMemcpyAsync(acc.data(), ctx->d_pk, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const double vol = std::pow(ctx->P.box, 3);
+    const double n6 = std::pow((double)ctx->P.n_m, 6);
+    for (int b = 0; b < B; ++b)
+        for (int i = 0; i < nb; ++i) {
+            const double *a = acc.data() + ((size_t)b * nb + i) * 3;
+            const double cnt = a[0] > 0 ? a[0] : 1.0;
+            n_modes[(size_t)b * nb + i] = a[0];
+            k_mean[(size_t)b * nb + i] = a[1] / cnt;
+            power[(size_t)b * nb + i] = vol / n6 * a[2] / cnt;
+        }
+    return PM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Internal declarations of the GB300 PM library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace pmgb {
+
+// ------------------------------------------------------------ host side --
+
+struct Params {
+    int n_p, n_m, n_batch, n_steps;
+    double box, a_init, a_final, h, n_s;
+};
+
+struct Growth {
+    double D1, dD1, D2, dD2, gp, gp2, gf;
+};
+
+struct HostTables {
+    std::vector<double> ka, dr, kb;     // per step
+    std::vector<double> dka, ddr, dkb;  // d/dOm
+    double lpt[4];                      // D1, D2, g1, g2 at a_init
+    double dlpt[4];                     // d/dOm
+    double amp;                         // P(k) amplitude A
+    double dlnamp;                      // d ln A / dOm
+};
+
+double hubble_e(double a, double om);
+void growth_at(double om, const std::vector<double> &a, std::vector<Growth> *out);
+void kdk_factors(double om, double a_init, double a_final, int n_steps, std::vector<double> *ka,
+                 std::vector<double> *dr, std::vector<double> *kb);
+void lpt_factors(double om, double a_init, double out[4]);
+double bbks_transfer(double k, double om, double h);
+double power_amplitude(double om, double s8, double h, double ns);
+void host_tables(const Params &p, double om, double s8, HostTables *t);
+
+// ---------------------------------------------------------- device side --
+
+// Particle / mesh geometry shared by the particle kernels.
+struct Geom {
+    int np, nm, nb;      // particles per side, mesh per side, batch
+    int64_t npart;       // np^3 particles per simulation
+    int ratio;           // nm / np when it divides, else 0
+    float inv_np;        // 1 / np
+    float inv_h;         // nm / box
+    float alpha;         // (nm / np)^3
+};
+
+// A set of real meshes: field f of batch b starts at ptr + f*fstride + b*bstride;
+// rows along z are zs floats apart (zs = 2 (nm/2 + 1) for the in-place FFT
+// layout, nm for a caller's plain mesh).
+struct MeshRef {
+    float *ptr;
+    int64_t fstride, bstride;
+    int zs;
+};
+
+// Per step and simulation KDK factors on the device: x = K_a, y = Dr,
+// z = K_b, w = K_a + K_b of the previous step (merged kick).
+enum KickSel { KICK_A = 0, KICK_MERGED = 1, KICK_B = 2 };
+
+enum PaintMode {
+    PAINT_DENSITY = 0,   // paint weight alpha at s
+    PAINT_KDK_PRE = 1,   // p += K_a f; s += Dr p; paint alpha at the new s
+    PAINT_ADJ = 2,       // paint (alpha, mu_x, mu_y, mu_z) at s into 4 fields
+    PAINT_ADJ_DRIFT = 3  // s -= Dr p; mu += Dr lam (reduce lam.p); then PAINT_ADJ
+};
+
+struct PaintArgs {
+    Geom g;
+    float *s, *p;
+    const float *f;
+    const float *lam;
+    float *mu;
+    MeshRef mesh;
+    const float4 *table;  // [n_steps][nb]
+    int step;
+    double *red;          // drift reduction of this step (batch stride red_bstride)
+    int red_bstride;
+};
+
+enum ReadMode {
+    READ_FORCE = 0,       // f = F(s)
+    READ_KICK_DRIFT = 1,  // p += c F; s += Dr p
+    READ_HALF_KICK = 2,   // p += c F; f = F
+    READ_ADJ = 3,         // F, vjp: lam += c vjp; p -= c F; reduce mu.F
+    READ_GRAD = 4         // ds = alpha sum grad W mesh
+};
+
+struct ReadArgs {
+    Geom g;
+    float *s, *p, *f, *lam;
+    const float *mu;
+    MeshRef mesh;
+    const float4 *table;
+    int kick_step, kick_sel, drift_step;
+    double *red;          // kick reduction (batch stride red_bstride)
+    int red_bstride;
+};
+
+cudaError_t launch_paint(int mode, const PaintArgs &a, cudaStream_t st);
+cudaError_t launch_read(int mode, const ReadArgs &a, cudaStream_t st);
+cudaError_t launch_fill(float *ptr, int64_t n, float v, cudaStream_t st);
+cudaError_t launch_unpad(const float *src, int64_t bstride, int zs, float *dst, int n, int nb, cudaStream_t st);
+cudaError_t launch_mse(MeshRef mesh, const float *target, int n, int nb, double *acc, cudaStream_t st);
+cudaError_t launch_kick(const Geom &g, float *p, const float *f, const float4 *table, int step, int sel,
+                        float sign, cudaStream_t st);
+
+// Spectral kernels over an rfft grid n x n x (n/2+1) (complex elements);
+// field f of batch b starts at c + f*fstride + b*bstride (complex elements).
+struct Spec {
+    float2 *c;
+    int64_t fstride, bstride;
+    int n, nb;
+    float kf;  // 2 pi / box
+};
+
+enum SpecMode { SPEC_FORCE = 0, SPEC_ADJ = 1 };
+cudaError_t launch_spectral(int mode, const Spec &sp, const float *pref, cudaStream_t st);
+cudaError_t launch_power_bins(const Spec &sp, double *acc, int nbins, cudaStream_t st);
+
+// Initial conditions (lattice fields, same layout rules).
+struct LinParams {
+    double amp, om, h, ns, dlnamp, inv_vc;
+};
+cudaError_t launch_noise(const float *noise, uint64_t seed, MeshRef dst, int np, int nb, cudaStream_t st);
+cudaError_t launch_lpt_linear(const Spec &sp, const LinParams *lp, cudaStream_t st);
+cudaError_t launch_lpt_source(MeshRef lat, int np, int nb, int f_phi, int f_src, cudaStream_t st);
+cudaError_t launch_lpt_second(const Spec &sp, int f_src, int f_out, float sign, cudaStream_t st);
+cudaError_t launch_lpt_adj_second(const Spec &sp, int f_in, int f_out, cudaStream_t st);
+cudaError_t launch_lpt_combine(MeshRef lat, int np, int nb, const float4 *fac, float *s, float *p, cudaStream_t st);
+cudaError_t launch_lpt_adj_seed(MeshRef lat, int np, int nb, const float4 *fac, const float *lam, const float *mu,
+                                double *red, cudaStream_t st);
+cudaError_t launch_lpt_adj_phi(MeshRef lat, int np, int nb, cudaStream_t st);
+cudaError_t launch_lpt_adj_final(const Spec &sp, const LinParams *lp, int f_noise, double *red, cudaStream_t st);
+
+}  // namespace pmgb

@@ -1,0 +1,488 @@
+// Fourier-space kernels: Green's function times gradient (forward and
+// adjoint), the binned power spectrum, white noise and the 2LPT spectral
+// steps with their adjoints.
+//
+// Paper (pmwd, arXiv:2211.09958): PM gravity (Summary), power spectrum as a
+// summary statistic and initial conditions as inference variables
+// (Statement of Need).  The rfft grid of an n^3 real field has n x n x
+// (n/2 + 1) complex entries; wavenumber index j maps to n_j = j for
+// j < n/2 and j - n otherwise (the Nyquist index n/2 maps to -n/2 on the
+// full axes and +n/2 on the half axis).
+//   force    F_j(k) = i k_j (3/2) Om delta(k) / k^2 / n^3, zero at k = 0 and
+//            where index j is the Nyquist index (inverse transforms real)
+//   adjoint  psi(k) = sum_j conj(i k_j (3/2) Om / k^2 / n^3) u_j(k)
+//   2LPT     s1_j = i k_j / k^2 delta_L, phi_ij = k_i k_j / k^2 delta_L,
+//            s2_j = -i k_j / k^2 S, delta_L = noise(k) sqrt(P(k) / V_c)
+
+#include "pm_internal.h"
+
+namespace pmgb {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void mode_ijk(int64_t m, int n, int &ix, int &iy, int &iz) {
+    const int nz = n / 2 + 1;
+    const int64_t r = m / nz;
+    iz = (int)(m - r * nz);
+    const int64_t x = r / n;
+    iy = (int)(r - x * n);
+    ix = (int)x;
+}
+
+__device__ __forceinline__ int signed_index(int j, int n) { return j < n / 2 ? j : j - n; }
+
+__device__ __forceinline__ float2 times_i(float2 v, float s) { return make_float2(-s * v.y, s * v.x); }
+
+__global__ void __launch_bounds__(kThreads) k_spec_force(Spec sp, const float *pref) {
+    const int b = blockIdx.y;
+    const int n = sp.n;
+    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (m >= nmodes) return;
+    int ix, iy, iz;
+    mode_ijk(m, n, ix, iy, iz);
+    const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
+    const float k2 = kx * kx + ky * ky + kz * kz;
+    const float g = k2 > 0.f ? pref[b] / k2 : 0.f;
+    float2 *c0 = sp.c + (int64_t)b * sp.bstride + m;
+    const float2 d = *c0;
+    const int h = n / 2;
+    const float2 fx = times_i(d, ix == h ? 0.f : kx * g);
+    const float2 fy = times_i(d, iy == h ? 0.f : ky * g);
+    const float2 fz = times_i(d, iz == h ? 0.f : kz * g);
+    c0[0] = fx;
+    c0[sp.fstride] = fy;
+    c0[2 * sp.fstride] = fz;
+}
+
+__global__ void __launch_bounds__(kThreads) k_spec_adj(Spec sp, const float *pref) {
+    const int b = blockIdx.y;
+    const int n = sp.n;
+    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (m >= nmodes) return;
+    int ix, iy, iz;
+    mode_ijk(m, n, ix, iy, iz);
+    const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
+    const float k2 = kx * kx + ky * ky + kz * kz;
+    const float g = k2 > 0.f ? pref[b] / k2 : 0.f;
+    float2 *c0 = sp.c + (int64_t)b * sp.bstride + m;
+    const int64_t fs = sp.fstride;
+    const float2 d = c0[0], ux = c0[fs], uy = c0[2 * fs], uz = c0[3 * fs];
+    const int h = n / 2;
+    const float ax = ix == h ? 0.f : kx * g, ay = iy == h ? 0.f : ky * g, az = iz == h ? 0.f : kz * g;
+    c0[0] = times_i(d, ax);
+    c0[fs] = times_i(d, ay);
+    c0[2 * fs] = times_i(d, az);
+    const float2 px = times_i(ux, -ax), py = times_i(uy, -ay), pz = times_i(uz, -az);
+    c0[3 * fs] = make_float2(px.x + py.x + pz.x, px.y + py.y + pz.y);
+}
+
+// |delta_k|^2 binned in |k| shells; acc[b][bin][0..2] += (n_modes, sum |k|, sum |delta|^2).
+__global__ void __launch_bounds__(kThreads) k_power_bins(Spec sp, double *acc, int nbins) {
+    extern __shared__ double sh[];
+    const int b = blockIdx.y;
+    const int n = sp.n;
+    for (int q = threadIdx.x; q < 3 * nbins; q += blockDim.x) sh[q] = 0.0;
+    __syncthreads();
+    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const float2 *c0 = sp.c + (int64_t)b * sp.bstride;
+    for (int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x; m < nmodes; m += (int64_t)gridDim.x * kThreads) {
+        int ix, iy, iz;
+        mode_ijk(m, n, ix, iy, iz);
+        const int nx = signed_index(ix, n), ny = signed_index(iy, n);
+        const int64_t n2 = (int64_t)nx * nx + (int64_t)ny * ny + (int64_t)iz * iz;
+        if (n2 == 0) continue;
+        const double kn = sqrt((double)n2);
+        const int bin = (int)floor(kn - 0.5);
+        if (bin < 0 || bin >= nbins) continue;
+        const double w = (iz == 0 || iz == n / 2) ? 1.0 : 2.0;
+        const float2 d = c0[m];
+        const double p2 = (double)d.x * d.x + (double)d.y * d.y;
+        atomicAdd(&sh[3 * bin], w);
+        atomicAdd(&sh[3 * bin + 1], w * kn * sp.kf);
+        atomicAdd(&sh[3 * bin + 2], w * p2);
+    }
+    __syncthreads();
+    double *dst = acc + (int64_t)b * 3 * nbins;
+    for (int q = threadIdx.x; q < 3 * nbins; q += blockDim.x)
+        if (sh[q] != 0.0) atomicAdd(dst + q, sh[q]);
+}
+
+// ------------------------------------------------------------ white noise --
+
+// Philox4x32-10 (Salmon et al. 2011) with the published multipliers and
+// Weyl key increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__global__ void k_noise(const float *noise, uint64_t seed, MeshRef dst, int np) {
+    const int b = blockIdx.y;
+    const int64_t n3 = (int64_t)np * np * np;
+    const uint64_t key = seed + (uint64_t)b;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        float v;
+        if (noise) {
+            v = noise[(int64_t)b * n3 + i];
+        } else {
+            const uint4 r = philox4x32_10(make_uint4((unsigned)i, (unsigned)((uint64_t)i >> 32), 0u, 0u),
+                                          make_uint2((unsigned)key, (unsigned)(key >> 32)));
+            const double u1 = ((double)r.x + 0.5) * 2.3283064365386963e-10;
+            const double u2 = ((double)r.y + 0.5) * 2.3283064365386963e-10;
+            v = (float)(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
+        }
+        const int64_t row = i / np;
+        dst.ptr[(int64_t)b * dst.bstride + row * dst.zs + (i - row * np)] = v;
+    }
+}
+
+// ------------------------------------------------------------------ 2LPT --
+
+__device__ __forceinline__ double bbks_t(double q) {
+    const double x = 2.34 * q;
+    const double lead = x > 1e-8 ? log1p(x) / x : 1.0 - 0.5 * x;
+    const double a = 16.1 * q, b = 5.46 * q, c = 6.71 * q;
+    const double poly = 1.0 + 3.89 * q + a * a + b * b * b + (c * c) * (c * c);
+    return lead * rsqrt(sqrt(poly));
+}
+
+// d ln T / d ln q of the BBKS form.
+__device__ __forceinline__ double bbks_dlnt_dlnq(double q) {
+    const double x = 2.34 * q;
+    const double dlead = x > 1e-6 ? x / ((1.0 + x) * log1p(x)) - 1.0 : -0.5 * x;
+    const double a = 16.1 * q, b = 5.46 * q, c = 6.71 * q;
+    const double poly = 1.0 + 3.89 * q + a * a + b * b * b + (c * c) * (c * c);
+    const double qdpoly = 3.89 * q + 2.0 * a * a + 3.0 * b * b * b + 4.0 * (c * c) * (c * c);
+    return dlead - 0.25 * qdpoly / poly;
+}
+
+// sqrt(P(k) / V_c) (m) and its d/dOm (dm) for |k| in h/Mpc.
+__device__ __forceinline__ void linear_mult(double k, const LinParams &lp, double &m, double &dm) {
+    if (k <= 0.0) {
+        m = dm = 0.0;
+        return;
+    }
+    const double q = k / (lp.om * lp.h);
+    const double t = bbks_t(q);
+    const double pk = lp.amp * pow(k, lp.ns) * t * t;
+    m = sqrt(pk * lp.inv_vc);
+    const double dlnp = lp.dlnamp - 2.0 * bbks_dlnt_dlnq(q) / lp.om;
+    dm = 0.5 * m * dlnp;
+}
+
+// omega(k) in field 0 -> s1_j (fields 0..2) and phi_ij (fields 3..8:
+// xx, yy, zz, xy, xz, yz), all scaled by 1/n^3 for the inverse transform.
+__global__ void __launch_bounds__(kThreads) k_lpt_linear(Spec sp, const LinParams *lps) {
+    const int b = blockIdx.y;
+    const int n = sp.n;
+    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (m >= nmodes) return;
+    int ix, iy, iz;
+    mode_ijk(m, n, ix, iy, iz);
+    const double kx = sp.kf * (double)signed_index(ix, n), ky = sp.kf * (double)signed_index(iy, n),
+                 kz = sp.kf * (double)iz;
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    double ml, dml;
+    linear_mult(sqrt(k2), lps[b], ml, dml);
+    float2 *c0 = sp.c + (int64_t)b * sp.bstride + m;
+    const int64_t fs = sp.fstride;
+    const float2 w = c0[0];
+    const double inv = k2 > 0.0 ? ml / (k2 * (double)n * n * n) : 0.0;
+    const double dx = w.x * inv, dy = w.y * inv;  // delta_L / (k^2 n^3)
+    const int h = n / 2;
+    const bool nx = ix == h, ny = iy == h, nz = iz == h;
+    const double k[3] = {kx, ky, kz};
+    const bool ny3[3] = {nx, ny, nz};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const double a = ny3[j] ? 0.0 : k[j];
+        c0[j * fs] = make_float2((float)(-a * dy), (float)(a * dx));
+    }
+    const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const bool zero = (pi[q] != pj[q]) && (ny3[pi[q]] || ny3[pj[q]]);
+        const double a = zero ? 0.0 : k[pi[q]] * k[pj[q]];
+        c0[(3 + q) * fs] = make_float2((float)(a * dx), (float)(a * dy));
+    }
+}
+
+// S = phi_xx phi_yy + phi_xx phi_zz + phi_yy phi_zz - phi_xy^2 - phi_xz^2 - phi_yz^2
+__global__ void k_lpt_source(MeshRef lat, int np, int f_phi, int f_src) {
+    const int b = blockIdx.y;
+    const int64_t n3 = (int64_t)np * np * np;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / np;
+        const int64_t o = (int64_t)b * lat.bstride + row * lat.zs + (i - row * np);
+        const float *ph = lat.ptr + f_phi * lat.fstride + o;
+        const float xx = ph[0], yy = ph[lat.fstride], zz = ph[2 * lat.fstride];
+        const float xy = ph[3 * lat.fstride], xz = ph[4 * lat.fstride], yz = ph[5 * lat.fstride];
+        lat.ptr[f_src * lat.fstride + o] = xx * yy + xx * zz + yy * zz - xy * xy - xz * xz - yz * yz;
+    }
+}
+
+// out_j = sign * i k_j / k^2 * S(k) / n^3 (Nyquist along j zero)
+__global__ void __launch_bounds__(kThreads) k_lpt_second(Spec sp, int f_src, int f_out, float sign) {
+    const int b = blockIdx.y;
+    const int n = sp.n;
+    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (m >= nmodes) return;
+    int ix, iy, iz;
+    mode_ijk(m, n, ix, iy, iz);
+    const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
+    const float k2 = kx * kx + ky * ky + kz * kz;
+    const float g = k2 > 0.f ? sign / (k2 * (float)n * n * n) : 0.f;
+    float2 *c0 = sp.c + (int64_t)b * sp.bstride + m;
+    const float2 s = c0[f_src * sp.fstride];
+    const int h = n / 2;
+    c0[f_out * sp.fstride] = times_i(s, ix == h ? 0.f : kx * g);
+    c0[(f_out + 1) * sp.fstride] = times_i(s, iy == h ? 0.f : ky * g);
+    c0[(f_out + 2) * sp.fstride] = times_i(s, iz == h ? 0.f : kz * g);
+}
+
+// Adjoint of k_lpt_second with sign -1: S_bar(k) = sum_j (+i k_j / k^2) G_j(k) / n^3.
+__global__ void __launch_bounds__(kThreads) k_lpt_adj_second(Spec sp, int f_in, int f_out) {
+    const int b = blockIdx.y;
+    const int n = sp.n;
+    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (m >= nmodes) return;
+    int ix, iy, iz;
+    mode_ijk(m, n, ix, iy, iz);
+    const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
+    const float k2 = kx * kx + ky * ky + kz * kz;
+    const float g = k2 > 0.f ? 1.f / (k2 * (float)n * n * n) : 0.f;
+    float2 *c0 = sp.c + (int64_t)b * sp.bstride + m;
+    const int h = n / 2;
+    const float2 a = times_i(c0[f_in * sp.fstride], ix == h ? 0.f : kx * g);
+    const float2 bb = times_i(c0[(f_in + 1) * sp.fstride], iy == h ? 0.f : ky * g);
+    const float2 c = times_i(c0[(f_in + 2) * sp.fstride], iz == h ? 0.f : kz * g);
+    c0[f_out * sp.fstride] = make_float2(a.x + bb.x + c.x, a.y + bb.y + c.y);
+}
+
+__device__ __forceinline__ int64_t lat_off(const MeshRef &lat, int b, int64_t i, int np) {
+    const int64_t row = i / np;
+    return (int64_t)b * lat.bstride + row * lat.zs + (i - row * np);
+}
+
+// s = D1 s1 + D2 s2, p = g1 s1 + g2 s2 (s1 in fields 0..2, s2 in 10..12).
+__global__ void k_lpt_combine(MeshRef lat, int np, const float4 *fac, float *s, float *p) {
+    const int b = blockIdx.y;
+    const int64_t n3 = (int64_t)np * np * np;
+    const float4 c = fac[b];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = lat_off(lat, b, i, np);
+        const int64_t gi = ((int64_t)b * n3 + i) * 3;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float a1 = lat.ptr[j * lat.fstride + o];
+            const float a2 = lat.ptr[(10 + j) * lat.fstride + o];
+            s[gi + j] = c.x * a1 + c.y * a2;
+            p[gi + j] = c.z * a1 + c.w * a2;
+        }
+    }
+}
+
+// Reductions (lam.s1, lam.s2, mu.s1, mu.s2) per batch and cotangents
+// gs1 = D1 lam + g1 mu -> fields 0..2, gs2 = D2 lam + g2 mu -> fields 10..12.
+__global__ void __launch_bounds__(kThreads) k_lpt_adj_seed(MeshRef lat, int np, const float4 *fac, const float *lam,
+                                                           const float *mu, double *red) {
+    const int b = blockIdx.y;
+    const int64_t n3 = (int64_t)np * np * np;
+    const float4 c = fac[b];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = lat_off(lat, b, i, np);
+        const int64_t gi = ((int64_t)b * n3 + i) * 3;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float l = lam[gi + j], u = mu[gi + j];
+            float *f1 = lat.ptr + j * lat.fstride + o;
+            float *f2 = lat.ptr + (10 + j) * lat.fstride + o;
+            const float a1 = *f1, a2 = *f2;
+            acc[0] += (double)(l * a1);
+            acc[1] += (double)(l * a2);
+            acc[2] += (double)(u * a1);
+            acc[3] += (double)(u * a2);
+            *f1 = c.x * l + c.z * u;
+            *f2 = c.y * l + c.w * u;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double v = acc[q];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(red + 4 * b + q, v);
+    }
+}
+
+// phi_bar from S_bar (field 9) and phi (fields 3..8), in place over phi.
+__global__ void k_lpt_adj_phi(MeshRef lat, int np) {
+    const int b = blockIdx.y;
+    const int64_t n3 = (int64_t)np * np * np;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = lat_off(lat, b, i, np);
+        const int64_t fs = lat.fstride;
+        float *ph = lat.ptr + 3 * fs + o;
+        const float sb = lat.ptr[9 * fs + o];
+        const float xx = ph[0], yy = ph[fs], zz = ph[2 * fs], xy = ph[3 * fs], xz = ph[4 * fs], yz = ph[5 * fs];
+        ph[0] = sb * (yy + zz);
+        ph[fs] = sb * (xx + zz);
+        ph[2 * fs] = sb * (xx + yy);
+        ph[3 * fs] = -2.f * sb * xy;
+        ph[4 * fs] = -2.f * sb * xz;
+        ph[5 * fs] = -2.f * sb * yz;
+    }
+}
+
+// delta_bar(k) = sum_j conj(i k_j / k^2) G1_j + sum_q m_q Phi_bar_q from
+// fields 0..8; omega_bar(k) = m_lin delta_bar / n^3 -> field 0; reductions
+// red[b][0] += w Re(conj(delta_bar) m_lin omega), red[b][1] the same with
+// d m_lin / dOm (Parseval; scaled by 1/n^3 on the host).
+__global__ void __launch_bounds__(kThreads) k_lpt_adj_final(Spec sp, const LinParams *lps, int f_noise, double *red) {
+    const int b = blockIdx.y;
+    const int n = sp.n;
+    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    double r0 = 0.0, r1 = 0.0;
+    if (m < nmodes) {
+        int ix, iy, iz;
+        mode_ijk(m, n, ix, iy, iz);
+        const double kx = sp.kf * (double)signed_index(ix, n), ky = sp.kf * (double)signed_index(iy, n),
+                     kz = sp.kf * (double)iz;
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        double ml, dml;
+        linear_mult(sqrt(k2), lps[b], ml, dml);
+        float2 *c0 = sp.c + (int64_t)b * sp.bstride + m;
+        const int64_t fs = sp.fstride;
+        const int h = n / 2;
+        const bool nyq[3] = {ix == h, iy == h, iz == h};
+        const double k[3] = {kx, ky, kz};
+        const double inv = k2 > 0.0 ? 1.0 / k2 : 0.0;
+        double ax = 0.0, ay = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double a = nyq[j] ? 0.0 : -k[j] * inv;  // conj(i k_j / k^2) = -i k_j / k^2
+            const float2 g = c0[j * fs];
+            ax += -a * g.y;
+            ay += a * g.x;
+        }
+        const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const bool zero = (pi[q] != pj[q]) && (nyq[pi[q]] || nyq[pj[q]]);
+            const double a = zero ? 0.0 : k[pi[q]] * k[pj[q]] * inv;
+            const float2 g = c0[(3 + q) * fs];
+            ax += a * g.x;
+            ay += a * g.y;
+        }
+        const float2 w = c0[f_noise * fs];
+        const double wt = (iz == 0 || iz == h) ? 1.0 : 2.0;
+        r0 = wt * ml * (ax * w.x + ay * w.y);
+        r1 = wt * dml * (ax * w.x + ay * w.y);
+        const double sc = ml / ((double)n * n * n);
+        c0[0] = make_float2((float)(sc * ax), (float)(sc * ay));
+    }
+    for (int o = 16; o; o >>= 1) {
+        r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+        r1 += __shfl_xor_sync(0xffffffffu, r1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(red + 2 * b, r0);
+        atomicAdd(red + 2 * b + 1, r1);
+    }
+}
+
+dim3 mode_grid(const Spec &sp) {
+    const int64_t nmodes = (int64_t)sp.n * sp.n * (sp.n / 2 + 1);
+    return dim3((unsigned)((nmodes + kThreads - 1) / kThreads), sp.nb);
+}
+
+dim3 site_grid(int np, int nb) {
+    const int64_t n3 = (int64_t)np * np * np;
+    const int64_t blocks = (n3 + kThreads - 1) / kThreads;
+    return dim3((unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), nb);
+}
+
+}  // namespace
+
+cudaError_t launch_spectral(int mode, const Spec &sp, const float *pref, cudaStream_t st) {
+    if (mode == SPEC_FORCE)
+        k_spec_force<<<mode_grid(sp), kThreads, 0, st>>>(sp, pref);
+    else
+        k_spec_adj<<<mode_grid(sp), kThreads, 0, st>>>(sp, pref);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_power_bins(const Spec &sp, double *acc, int nbins, cudaStream_t st) {
+    const size_t smem = sizeof(double) * 3 * nbins;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_power_bins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t nmodes = (int64_t)sp.n * sp.n * (sp.n / 2 + 1);
+    const int64_t blocks = (nmodes + kThreads - 1) / kThreads;
+    k_power_bins<<<dim3((unsigned)(blocks < 152 * 4 ? blocks : 152 * 4), sp.nb), kThreads, smem, st>>>(sp, acc, nbins);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_noise(const float *noise, uint64_t seed, MeshRef dst, int np, int nb, cudaStream_t st) {
+    k_noise<<<site_grid(np, nb), kThreads, 0, st>>>(noise, seed, dst, np);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lpt_linear(const Spec &sp, const LinParams *lp, cudaStream_t st) {
+    k_lpt_linear<<<mode_grid(sp), kThreads, 0, st>>>(sp, lp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lpt_source(MeshRef lat, int np, int nb, int f_phi, int f_src, cudaStream_t st) {
+    k_lpt_source<<<site_grid(np, nb), kThreads, 0, st>>>(lat, np, f_phi, f_src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lpt_second(const Spec &sp, int f_src, int f_out, float sign, cudaStream_t st) {
+    k_lpt_second<<<mode_grid(sp), kThreads, 0, st>>>(sp, f_src, f_out, sign);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lpt_adj_second(const Spec &sp, int f_in, int f_out, cudaStream_t st) {
+    k_lpt_adj_second<<<mode_grid(sp), kThreads, 0, st>>>(sp, f_in, f_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lpt_combine(MeshRef lat, int np, int nb, const float4 *fac, float *s, float *p, cudaStream_t st) {
+    k_lpt_combine<<<site_grid(np, nb), kThreads, 0, st>>>(lat, np, fac, s, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lpt_adj_seed(MeshRef lat, int np, int nb, const float4 *fac, const float *lam, const float *mu,
+                                double *red, cudaStream_t st) {
+    k_lpt_adj_seed<<<site_grid(np, nb), kThreads, 0, st>>>(lat, np, fac, lam, mu, red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lpt_adj_phi(MeshRef lat, int np, int nb, cudaStream_t st) {
+    k_lpt_adj_phi<<<site_grid(np, nb), kThreads, 0, st>>>(lat, np);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lpt_adj_final(const Spec &sp, const LinParams *lp, int f_noise, double *red, cudaStream_t st) {
+    k_lpt_adj_final<<<mode_grid(sp), kThreads, 0, st>>>(sp, lp, f_noise, red);
+    return cudaGetLastError();
+}
+
+}  // namespace pmgb
