@@ -1,0 +1,393 @@
+"""Benchmark of the differentiable PM hot path on GB300.
+
+One bench step = the whole hot path over one synthetic realisation of the
+workload: 2LPT initial conditions from white noise, forward KDK integration
+over all time steps, MSE loss of the final CIC density against a target
+field, the reverse-time adjoint back to a_init, and the adjoint of the
+initial conditions (gradients w.r.t. the white noise, Omega_m and sigma8).
+Metric: particle-steps/s = n_batch * n_p^3 * n_steps / time, forward +
+adjoint together (also reported separately).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--sim-steps S]
+
+With N > 1 (under torchrun) every rank runs an independent replica (the
+path does not shard; no data-path collective), value = all ranks' work /
+max time.  --impl reference times the FP64 CPU oracle instead.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2211_09958_gb300.configs import WORKLOADS  # noqa: E402
+
+METRIC = "particle-steps/s (fwd+adjoint) at 512³"
+UNIT = "particle-steps/s"
+DEFAULT_WORKLOAD = "pm512_mesh1024"
+ORACLE_SAMPLE = dict(n_p=64, n_m=128, box=125.0, n_steps=1)
+
+
+# --------------------------------------------------------------- helpers --
+
+def _dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# Algorithmic HBM bytes per launch of each library kernel (FP32 state,
+# (N, 3) particle arrays; mesh bytes counted on the unpadded n_m^3 grid,
+# complex modes on the n_m^2 (n_m/2+1) rfft grid).
+def algorithmic_bytes(kind, npart, ncell, nmodes):
+    per = {
+        "paint_density": 12 * npart + 4 * ncell,
+        "paint_kdk": (36 + 24) * npart + 4 * ncell,
+        "paint_adj": 24 * npart + 16 * ncell,
+        "paint_adj_drift": (48 + 24) * npart + 16 * ncell,
+        "read_force": 24 * npart + 12 * ncell,
+        "read_kick_drift": 48 * npart + 12 * ncell,
+        "read_half_kick": (24 + 24) * npart + 12 * ncell,
+        "read_adj": (48 + 24) * npart + 16 * ncell,
+        "read_grad": 24 * npart + 4 * ncell,
+        "spectral_force": (8 + 24) * nmodes,
+        "spectral_adj": (32 + 32) * nmodes,
+    }
+    return per.get(kind)
+
+
+def _source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2211_09958_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cpp", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kind, workload):
+    """DRAM bytes per launch from the committed ncu capture, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    if d.get("source_digest") != _source_digest():
+        return None
+    ent = d.get("kernels", {}).get(kind)
+    if not ent:
+        return None
+    scale = ent.get("scale_to", {}).get(workload)
+    return ent["dram_bytes_per_launch"] * (scale if scale else 1.0) if (scale or ent.get("workload") == workload) else None
+
+
+# ----------------------------------------------------------------- oracle --
+
+def oracle_sample(seed=0):
+    """Time the FP64 oracle on a bounded sample: one KDK step forward and
+    its adjoint step for 64^3 particles on a 128^3 mesh in a 125 Mpc/h box
+    (the 512^3 / 1024^3 / 1 Gpc/h workload's recipe and resolution at 1/512
+    of the particles)."""
+    from oracle import pm as opm
+    from oracle.cosmology import Cosmology
+    from paper_2211_09958_gb300 import inputs
+
+    smp = ORACLE_SAMPLE
+    st = opm.Setup(smp["n_p"], smp["n_m"], smp["box"], Cosmology(0.3, 0.8), n_steps=smp["n_steps"])
+    s0 = inputs.random_displacements(st.n_p, st.box, seed, scale=0.5).astype(np.float64)
+    p0 = 0.01 * s0
+    target = inputs.target_field(st.n_m, seed + 1).astype(np.float64)
+    t0 = time.perf_counter()
+    s, p, f = opm.integrate(s0, p0, st)
+    t1 = time.perf_counter()
+    lam = opm.mse_loss_grad(s, target, st)
+    opm.adjoint_integrate(s, p, f, lam, np.zeros_like(p), st)
+    t2 = time.perf_counter()
+    work = st.n_p ** 3 * st.n_steps
+    return {"value": work / (t2 - t0), "fwd_s": t1 - t0, "adj_s": t2 - t1, "seconds": t2 - t0}
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+SAMPLE_TEXT = ("FP64 oracle (numpy + scipy.fft), one forward KDK step plus its adjoint step, "
+               "64^3 particles on a 128^3 mesh, 125 Mpc/h (the 512^3 workload's recipe and resolution "
+               "at 1/512 of its particles), 2LPT excluded; particle-steps/s of that sample")
+
+
+def run_reference(args):
+    rank, _, world = _dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample()
+    times, vals = [], []
+    for k in range(args.steps):
+        r = oracle_sample(seed=k)
+        times.append(r["seconds"])
+        vals.append(r["value"])
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "sample": ORACLE_SAMPLE},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": SAMPLE_TEXT},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------- ours --
+
+def run_ours(args):
+    rank, local_rank, world = _dist_env()
+    w = WORKLOADS[args.workload]
+    n_steps = args.sim_steps or w.n_steps
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        runs = [oracle_sample(seed=k) for k in range(2)]      # before any GPU call
+        cpu = {"value": float(np.mean([r["value"] for r in runs]))}
+
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    from paper_2211_09958_gb300 import _pmgb
+    from paper_2211_09958_gb300.pm import ParticleMesh
+
+    if w.n_batch > 1:
+        from paper_2211_09958_gb300.inputs import batch_cosmologies
+        om, s8 = batch_cosmologies(w.n_batch)
+    else:
+        om, s8 = w.omega_m, w.sigma8
+    pm = ParticleMesh(w.n_p, w.n_m, w.box, om, s8, n_steps, w.a_init, w.a_final, w.h, w.n_s)
+    dev = pm.device
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.ic_seed + 7919 * rank)
+    noise = torch.randn((pm.n_batch, w.n_p, w.n_p, w.n_p), generator=gen, device=dev, dtype=torch.float32)
+    target = torch.randn((pm.n_batch, w.n_m, w.n_m, w.n_m), generator=gen, device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+
+    def hot_path(nz, tg, ev=None):
+        s, p = pm.init_lpt(nz)
+        f = pm.integrate(s, p)
+        if ev is not None:
+            ev.record(stream)
+        loss, lam = pm.mse_loss(s, tg)
+        mu = torch.zeros_like(p)
+        dom = pm.adjoint_integrate(s, p, f, lam, mu, mu_zero=True)
+        dn, dcos = pm.init_lpt_adjoint(lam, mu, nz)
+        return dn, loss, dom, dcos
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        hot_path(noise, target)
+    barrier()
+
+    # device-resident timing, with the library's per-kernel event timing on
+    lib = pm._lib
+    lib.pm_profile(pm._ctx, 1)
+    lib.pm_profile_read(pm._ctx, None, None, 0)           # clear warm-up records
+    launches0 = pm.launch_count()
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_m = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        barrier()
+        for k in range(args.steps):
+            ev_a[k].record(stream)
+            hot_path(noise, target, ev_m[k])
+            ev_b[k].record(stream)
+        barrier()
+    launches = pm.launch_count() - launches0
+    nk = lib.pm_profile_kinds(pm._ctx)
+    import ctypes
+    counts = (ctypes.c_int64 * nk)()
+    kms = (ctypes.c_double * nk)()
+    lib.pm_profile_read(pm._ctx, counts, kms, nk)
+    lib.pm_profile(pm._ctx, 0)
+    kernels = {lib.pm_profile_name(pm._ctx, i).decode(): (int(counts[i]), float(kms[i])) for i in range(nk)}
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev_a, ev_b)]
+    fwd_ms = [a.elapsed_time(m) for a, m in zip(ev_a, ev_m)]
+    total_ms = float(sum(step_ms))
+
+    # end to end: pinned host inputs in, gradient out, every step
+    h_noise = noise.cpu().pin_memory()
+    h_target = target.cpu().pin_memory()
+    h_grad = torch.empty_like(h_noise).pin_memory()
+    hot_path(h_noise.to(dev, non_blocking=True), h_target.to(dev, non_blocking=True))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dn, loss, dom, dcos = hot_path(h_noise.to(dev, non_blocking=True), h_target.to(dev, non_blocking=True))
+        h_grad.copy_(dn, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    h2d = h_noise.numel() * 4 + h_target.numel() * 4
+    d2h = h_grad.numel() * 4 + 8 * pm.n_batch * 4        # dnoise + loss, dOm (dyn, IC), dsigma8
+
+    work = pm.n_batch * w.n_p ** 3 * n_steps            # particle-steps per rank per bench step
+    t_max = total_ms
+    e2e_max = e2e_ms
+    if dist is not None:
+        t = torch.tensor([total_ms, e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, e2e_max = float(t[0]), float(t[1])
+    value = world * work * args.steps / (t_max / 1e3)
+    e2e_value = world * work * args.steps / (e2e_max / 1e3)
+
+    if rank == 0:
+        hbm, peak_src = _peaks()
+        npart, ncell, nmodes = pm.n_batch * w.n_p ** 3, pm.n_batch * w.n_m ** 3, pm.n_batch * w.n_m ** 2 * (w.n_m // 2 + 1)
+        table = {}
+        for kind, (cnt, ms) in kernels.items():
+            ab = algorithmic_bytes(kind, npart, ncell, nmodes)
+            ent = {"launches": cnt, "total_ms": round(ms, 3), "share": round(ms / total_ms, 4)}
+            if ab is not None and cnt:
+                ent["gbs"] = round(ab / (ms / cnt / 1e3) / 1e9, 1)
+                ent["frac"] = round(ent["gbs"] / hbm, 3)
+            table[kind] = ent
+        mine = {k: v for k, v in table.items() if "gbs" in v}
+        dom_kind = max(mine, key=lambda k: mine[k]["total_ms"])
+        dk = mine[dom_kind]
+        cnt, ms = kernels[dom_kind]
+        traffic = _ncu_traffic(dom_kind, w.name)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n_p": w.n_p, "n_m": w.n_m, "box_mpc_h": w.box, "n_steps": n_steps,
+                       "n_batch": pm.n_batch, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (each mesh field > 129 MB)"},
+            "forward": {"value": world * work * args.steps / (sum(fwd_ms) / 1e3), "unit": UNIT,
+                        "ms_per_step": float(np.mean(fwd_ms))},
+            "adjoint": {"value": world * work * args.steps / ((total_ms - sum(fwd_ms)) / 1e3), "unit": UNIT,
+                        "ms_per_step": float(np.mean(step_ms) - np.mean(fwd_ms))},
+            "roofline": {"bound": "hbm", "kernel": dom_kind, "achieved": dk["gbs"], "peak": hbm, "unit": "GB/s",
+                         "frac": dk["frac"], "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": algorithmic_bytes(dom_kind, npart, ncell, nmodes),
+                         "traffic": traffic},
+            "kernels": table,
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "cpu_baseline": None if cpu is None else {
+                "value": cpu["value"], "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": SAMPLE_TEXT},
+        }
+        print(json.dumps(line))
+    pm.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--sim-steps", type=int, default=0, help="override the number of KDK steps")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

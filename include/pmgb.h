@@ -183,6 +183,17 @@ int pm_host_coefficients(const pm_config *cfg, double *kdk, double *dkdk, double
 /* Device-kernel launch counter since pm_create (for benchmarking). */
 int64_t pm_launch_count(const pm_ctx *ctx);
 
+/* Kernel timing.  pm_profile(ctx, 1) makes every later library kernel, cuFFT
+ * call and scratch memset record a CUDA event pair on the context stream,
+ * tagged with a kind name; pm_profile_read synchronises that stream and
+ * returns per kind (index 0 .. pm_profile_kinds() - 1, named by
+ * pm_profile_name) the number of launches and the summed device time in ms
+ * (host arrays of n entries), then clears the records. */
+int pm_profile(pm_ctx *ctx, int enable);
+int pm_profile_kinds(const pm_ctx *ctx);
+const char *pm_profile_name(const pm_ctx *ctx, int kind);
+int pm_profile_read(pm_ctx *ctx, int64_t *counts, double *ms, int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,12 @@ struct pm_ctx {
     void *work = nullptr;
     std::string err;
     int64_t launches = 0;
+    // kernel timing (pm_profile): event pairs per launch, grouped by kind
+    bool prof = false;
+    std::vector<std::string> kinds;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    std::vector<int> rec_kind;
 };
 
 namespace {
@@ -70,16 +76,84 @@ struct DeviceGuard {
     }
 };
 
+int kind_id(pm_ctx *ctx, const char *name) {
+    for (size_t i = 0; i < ctx->kinds.size(); ++i)
+        if (ctx->kinds[i] == name) return (int)i;
+    ctx->kinds.emplace_back(name);
+    return (int)ctx->kinds.size() - 1;
+}
+
+cudaEvent_t pool_event(pm_ctx *ctx) {
+    if (ctx->pool_used == ctx->pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->pool.push_back(e);
+    }
+    return ctx->pool[ctx->pool_used++];
+}
+
+// Records an event pair around one launch on the context stream when
+// profiling is on; a failure to get events only drops that record.
+struct ProfScope {
+    pm_ctx *ctx;
+    const char *kind;
+    cudaEvent_t a = nullptr;
+    ProfScope(pm_ctx *c, const char *k) : ctx(c), kind(k) {
+        if (ctx->prof && (a = pool_event(ctx)) != nullptr) cudaEventRecord(a, ctx->stream);
+    }
+    void end() {
+        if (!a) return;
+        cudaEvent_t b = pool_event(ctx);
+        if (!b) {
+            ctx->pool_used--;
+            a = nullptr;
+            return;
+        }
+        cudaEventRecord(b, ctx->stream);
+        ctx->rec_kind.push_back(kind_id(ctx, kind));
+        a = nullptr;
+    }
+};
+
+const char *paint_kind(int mode) {
+    switch (mode) {
+        case PAINT_DENSITY: return "paint_density";
+        case PAINT_KDK_PRE: return "paint_kdk";
+        case PAINT_ADJ: return "paint_adj";
+        default: return "paint_adj_drift";
+    }
+}
+
+const char *read_kind(int mode) {
+    switch (mode) {
+        case READ_FORCE: return "read_force";
+        case READ_KICK_DRIFT: return "read_kick_drift";
+        case READ_HALF_KICK: return "read_half_kick";
+        case READ_ADJ: return "read_adj";
+        default: return "read_grad";
+    }
+}
+
 #define PM_CUDA(ctx, x)                                                                                   \
     do {                                                                                                  \
         cudaError_t e_ = (x);                                                                             \
         if (e_ != cudaSuccess) return fail(ctx, PM_ECUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
-#define PM_LAUNCH(ctx, x)                                                                                 \
+#define PM_LAUNCH(ctx, kind, x)                                                                           \
     do {                                                                                                  \
+        ProfScope ps_(ctx, kind);                                                                         \
         cudaError_t e_ = (x);                                                                             \
+        ps_.end();                                                                                        \
         (ctx)->launches++;                                                                                \
+        if (e_ != cudaSuccess) return fail(ctx, PM_ECUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define PM_MEMSET(ctx, x)                                                                                 \
+    do {                                                                                                  \
+        ProfScope ps_(ctx, "memset");                                                                     \
+        cudaError_t e_ = (x);                                                                             \
+        ps_.end();                                                                                        \
         if (e_ != cudaSuccess) return fail(ctx, PM_ECUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
@@ -177,10 +251,11 @@ float *lat_field(pm_ctx *ctx, int f) { return ctx->lat + (int64_t)f * ctx->lat_p
 int fft_fields(pm_ctx *ctx, cufftHandle plan, bool r2c, float *base, int64_t fstride, int f0, int nf) {
     for (int f = f0; f < f0 + nf; ++f) {
         float *p = base + (int64_t)f * fstride;
-        if (r2c)
-            PM_FFT(ctx, cufftExecR2C(plan, p, reinterpret_cast<cufftComplex *>(p)));
-        else
-            PM_FFT(ctx, cufftExecC2R(plan, reinterpret_cast<cufftComplex *>(p), p));
+        ProfScope ps(ctx, r2c ? "cufft_r2c" : "cufft_c2r");
+        const cufftResult r = r2c ? cufftExecR2C(plan, p, reinterpret_cast<cufftComplex *>(p))
+                                  : cufftExecC2R(plan, reinterpret_cast<cufftComplex *>(p), p);
+        ps.end();
+        PM_FFT(ctx, r);
     }
     return PM_OK;
 }
@@ -224,10 +299,10 @@ ReadArgs read_args(pm_ctx *ctx, float *s) {
 int force_meshes(pm_ctx *ctx, int paint_mode, const PaintArgs &pa) {
     const bool adj = paint_mode == PAINT_ADJ || paint_mode == PAINT_ADJ_DRIFT;
     const int nf = adj ? 4 : 1;
-    PM_CUDA(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * ctx->P.n_batch * nf, ctx->stream));
-    PM_LAUNCH(ctx, launch_paint(paint_mode, pa, ctx->stream));
+    PM_MEMSET(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * ctx->P.n_batch * nf, ctx->stream));
+    PM_LAUNCH(ctx, paint_kind(paint_mode), launch_paint(paint_mode, pa, ctx->stream));
     PM_TRY(mesh_r2c(ctx, 0, nf));
-    PM_LAUNCH(ctx, launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream));
+    PM_LAUNCH(ctx, (adj ? "spectral_adj" : "spectral_force"), launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream));
     PM_TRY(mesh_c2r(ctx, 0, adj ? 4 : 3));
     return PM_OK;
 }
@@ -254,13 +329,13 @@ int lpt_forward_fields(pm_ctx *ctx, const float *noise, uint64_t seed) {
     PM_TRY(ensure_lattice(ctx));
     const int np = ctx->P.n_p, B = ctx->P.n_batch;
     MeshRef lr = lat_ref(ctx);
-    PM_LAUNCH(ctx, launch_noise(noise, seed, lr, np, B, ctx->stream));
+    PM_LAUNCH(ctx, "noise", launch_noise(noise, seed, lr, np, B, ctx->stream));
     PM_TRY(lat_r2c(ctx, 0, 1));
-    PM_LAUNCH(ctx, launch_lpt_linear(lat_spec(ctx), ctx->d_lin, ctx->stream));
+    PM_LAUNCH(ctx, "lpt_linear", launch_lpt_linear(lat_spec(ctx), ctx->d_lin, ctx->stream));
     PM_TRY(lat_c2r(ctx, 0, 9));
-    PM_LAUNCH(ctx, launch_lpt_source(lr, np, B, 3, 9, ctx->stream));
+    PM_LAUNCH(ctx, "lpt_source", launch_lpt_source(lr, np, B, 3, 9, ctx->stream));
     PM_TRY(lat_r2c(ctx, 9, 1));
-    PM_LAUNCH(ctx, launch_lpt_second(lat_spec(ctx), 9, 10, -1.f, ctx->stream));
+    PM_LAUNCH(ctx, "lpt_second", launch_lpt_second(lat_spec(ctx), 9, 10, -1.f, ctx->stream));
     PM_TRY(lat_c2r(ctx, 10, 3));
     return PM_OK;
 }
@@ -274,6 +349,41 @@ extern "C" {
 const char *pm_last_error(const pm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
 int64_t pm_launch_count(const pm_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int pm_profile(pm_ctx *ctx, int enable) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    ctx->prof = enable != 0;
+    return PM_OK;
+}
+
+int pm_profile_kinds(const pm_ctx *ctx) { return ctx ? (int)ctx->kinds.size() : 0; }
+
+const char *pm_profile_name(const pm_ctx *ctx, int kind) {
+    if (!ctx || kind < 0 || kind >= (int)ctx->kinds.size()) return "";
+    return ctx->kinds[kind].c_str();
+}
+
+int pm_profile_read(pm_ctx *ctx, int64_t *counts, double *ms, int n) {
+    if (!ctx || (n > 0 && (!counts || !ms))) return fail(ctx, PM_EINVAL, "bad arguments");
+    DeviceGuard guard(ctx->device);
+    PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < n; ++i) {
+        counts[i] = 0;
+        ms[i] = 0.0;
+    }
+    for (size_t r = 0; r < ctx->rec_kind.size(); ++r) {
+        float t = 0.f;
+        PM_CUDA(ctx, cudaEventElapsedTime(&t, ctx->pool[2 * r], ctx->pool[2 * r + 1]));
+        const int k = ctx->rec_kind[r];
+        if (k < n) {
+            counts[k] += 1;
+            ms[k] += t;
+        }
+    }
+    ctx->rec_kind.clear();
+    ctx->pool_used = 0;
+    return PM_OK;
+}
 
 int pm_create(const pm_config *cfg, pm_ctx **out) {
     if (!out) return fail(nullptr, PM_EINVAL, "out must not be NULL");
@@ -369,6 +479,7 @@ int pm_destroy(pm_ctx *ctx) {
         for (cufftHandle h : {ctx->r2c, ctx->c2r, ctx->lr2c, ctx->lc2r})
             if (h) cufftDestroy(h);
     }
+    for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
     for (void *p : {(void *)ctx->mesh, (void *)ctx->lat, (void *)ctx->d_table, (void *)ctx->d_pref,
                     (void *)ctx->d_fac, (void *)ctx->d_lin, (void *)ctx->d_red, (void *)ctx->d_pk,
                     (void *)ctx->d_lred, ctx->work})
@@ -459,7 +570,7 @@ int pm_force(pm_ctx *ctx, const float *s, float *f) {
     PM_TRY(force_meshes(ctx, PAINT_DENSITY, pa));
     ReadArgs ra = read_args(ctx, const_cast<float *>(s));
     ra.f = f;
-    PM_LAUNCH(ctx, launch_read(READ_FORCE, ra, ctx->stream));
+    PM_LAUNCH(ctx, read_kind(READ_FORCE), launch_read(READ_FORCE, ra, ctx->stream));
     return PM_OK;
 }
 
@@ -480,7 +591,7 @@ int pm_kdk_step(pm_ctx *ctx, int32_t step, float *s, float *p, float *f) {
     ra.f = f;
     ra.kick_step = step;
     ra.kick_sel = KICK_B;
-    PM_LAUNCH(ctx, launch_read(READ_HALF_KICK, ra, ctx->stream));
+    PM_LAUNCH(ctx, read_kind(READ_HALF_KICK), launch_read(READ_HALF_KICK, ra, ctx->stream));
     return PM_OK;
 }
 
@@ -501,12 +612,12 @@ int pm_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, fl
         ra.kick_step = n;
         ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
         ra.drift_step = n;
-        PM_LAUNCH(ctx, launch_read(READ_KICK_DRIFT, ra, ctx->stream));
+        PM_LAUNCH(ctx, read_kind(READ_KICK_DRIFT), launch_read(READ_KICK_DRIFT, ra, ctx->stream));
     }
     PM_TRY(force_meshes(ctx, PAINT_DENSITY, pa));
     ra.kick_step = step_end - 1;
     ra.kick_sel = KICK_B;
-    PM_LAUNCH(ctx, launch_read(READ_HALF_KICK, ra, ctx->stream));
+    PM_LAUNCH(ctx, read_kind(READ_HALF_KICK), launch_read(READ_HALF_KICK, ra, ctx->stream));
     return PM_OK;
 }
 
@@ -522,10 +633,10 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
         return fail(ctx, PM_EINVAL, "need 0 <= step_begin < step_end <= n_steps");
     DeviceGuard guard(ctx->device);
     const int N = ctx->P.n_steps, B = ctx->P.n_batch;
-    PM_CUDA(ctx, cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * B * 2 * (N + 1), ctx->stream));
+    PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * B * 2 * (N + 1), ctx->stream));
     const int last = step_end - 1;
     if (flags & PM_ADJ_MU_ZERO) {
-        PM_LAUNCH(ctx, launch_kick(ctx->g, p, f, ctx->d_table, last, KICK_B, -1.f, ctx->stream));
+        PM_LAUNCH(ctx, "kick", launch_kick(ctx->g, p, f, ctx->d_table, last, KICK_B, -1.f, ctx->stream));
     } else {
         PaintArgs pa = paint_args(ctx, s);
         pa.mu = mu;
@@ -537,7 +648,7 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
         ra.kick_step = last;
         ra.kick_sel = KICK_B;
         ra.red = ctx->d_red + 2 * N;
-        PM_LAUNCH(ctx, launch_read(READ_ADJ, ra, ctx->stream));
+        PM_LAUNCH(ctx, read_kind(READ_ADJ), launch_read(READ_ADJ, ra, ctx->stream));
     }
     for (int n = last; n >= step_begin; --n) {
         PaintArgs pa = paint_args(ctx, s);
@@ -554,7 +665,7 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
         ra.kick_step = n;
         ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
         ra.red = ctx->d_red + 2 * n;
-        PM_LAUNCH(ctx, launch_read(READ_ADJ, ra, ctx->stream));
+        PM_LAUNCH(ctx, read_kind(READ_ADJ), launch_read(READ_ADJ, ra, ctx->stream));
     }
     if (domega) {
         std::vector<double> red((size_t)B * 2 * (N + 1));
@@ -585,7 +696,7 @@ int pm_init_lpt(pm_ctx *ctx, const float *noise, uint64_t seed, float *s, float 
     if (noise) PM_TRY(check_ptr(ctx, noise, "noise"));
     DeviceGuard guard(ctx->device);
     PM_TRY(lpt_forward_fields(ctx, noise, seed));
-    PM_LAUNCH(ctx, launch_lpt_combine(lat_ref(ctx), ctx->P.n_p, ctx->P.n_batch, ctx->d_fac, s, p, ctx->stream));
+    PM_LAUNCH(ctx, "lpt_combine", launch_lpt_combine(lat_ref(ctx), ctx->P.n_p, ctx->P.n_batch, ctx->d_fac, s, p, ctx->stream));
     return PM_OK;
 }
 
@@ -600,22 +711,22 @@ int pm_init_lpt_adjoint(pm_ctx *ctx, const float *noise, uint64_t seed, const fl
     const int np = ctx->P.n_p, B = ctx->P.n_batch;
     PM_TRY(lpt_forward_fields(ctx, noise, seed));
     MeshRef lr = lat_ref(ctx);
-    PM_CUDA(ctx, cudaMemsetAsync(ctx->d_lred, 0, sizeof(double) * B * 8, ctx->stream));
+    PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_lred, 0, sizeof(double) * B * 8, ctx->stream));
     // gs1 -> 0..2, gs2 -> 10..12, reductions (lam.s1, lam.s2, mu.s1, mu.s2)
-    PM_LAUNCH(ctx, launch_lpt_adj_seed(lr, np, B, ctx->d_fac, lam, mu, ctx->d_lred, ctx->stream));
+    PM_LAUNCH(ctx, "lpt_adj_seed", launch_lpt_adj_seed(lr, np, B, ctx->d_fac, lam, mu, ctx->d_lred, ctx->stream));
     // S_bar = adjoint of s2 = IDFT(-i k / k^2 DFT S)
     PM_TRY(lat_r2c(ctx, 10, 3));
-    PM_LAUNCH(ctx, launch_lpt_adj_second(lat_spec(ctx), 10, 9, ctx->stream));
+    PM_LAUNCH(ctx, "lpt_adj_second", launch_lpt_adj_second(lat_spec(ctx), 10, 9, ctx->stream));
     PM_TRY(lat_c2r(ctx, 9, 1));
-    PM_LAUNCH(ctx, launch_lpt_adj_phi(lr, np, B, ctx->stream));
+    PM_LAUNCH(ctx, "lpt_adj_phi", launch_lpt_adj_phi(lr, np, B, ctx->stream));
     PM_TRY(lat_r2c(ctx, 0, 9));
-    PM_LAUNCH(ctx, launch_noise(noise, seed, MeshRef{lat_field(ctx, 13), 0, ctx->lat_pad, lr.zs}, np, B,
+    PM_LAUNCH(ctx, "noise", launch_noise(noise, seed, MeshRef{lat_field(ctx, 13), 0, ctx->lat_pad, lr.zs}, np, B,
                                 ctx->stream));
     PM_TRY(lat_r2c(ctx, 13, 1));
-    PM_LAUNCH(ctx, launch_lpt_adj_final(lat_spec(ctx), ctx->d_lin, 13, ctx->d_lred + 4 * B, ctx->stream));
+    PM_LAUNCH(ctx, "lpt_adj_final", launch_lpt_adj_final(lat_spec(ctx), ctx->d_lin, 13, ctx->d_lred + 4 * B, ctx->stream));
     if (dnoise) {
         PM_TRY(lat_c2r(ctx, 0, 1));
-        PM_LAUNCH(ctx, launch_unpad(ctx->lat, ctx->lat_pad, lr.zs, dnoise, np, B, ctx->stream));
+        PM_LAUNCH(ctx, "unpad", launch_unpad(ctx->lat, ctx->lat_pad, lr.zs, dnoise, np, B, ctx->stream));
     }
     if (dcosmo) {
         std::vector<double> red((size_t)B * 8);
@@ -642,10 +753,10 @@ int pm_density(pm_ctx *ctx, const float *s, float *delta) {
     PM_TRY(check_ptr(ctx, delta, "delta"));
     DeviceGuard guard(ctx->device);
     const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
-    PM_LAUNCH(ctx, launch_fill(delta, n3 * ctx->P.n_batch, -1.f, ctx->stream));
+    PM_LAUNCH(ctx, "fill", launch_fill(delta, n3 * ctx->P.n_batch, -1.f, ctx->stream));
     PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
     pa.mesh = MeshRef{delta, 0, n3, ctx->P.n_m};
-    PM_LAUNCH(ctx, launch_paint(PAINT_DENSITY, pa, ctx->stream));
+    PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
     return PM_OK;
 }
 
@@ -659,7 +770,7 @@ int pm_density_adjoint(pm_ctx *ctx, const float *s, const float *ddelta, float *
     ReadArgs ra = read_args(ctx, const_cast<float *>(s));
     ra.mesh = MeshRef{const_cast<float *>(ddelta), 0, n3, ctx->P.n_m};
     ra.f = ds;
-    PM_LAUNCH(ctx, launch_read(READ_GRAD, ra, ctx->stream));
+    PM_LAUNCH(ctx, read_kind(READ_GRAD), launch_read(READ_GRAD, ra, ctx->stream));
     return PM_OK;
 }
 
@@ -671,15 +782,15 @@ int pm_mse_loss(pm_ctx *ctx, const float *s, const float *target, double *loss, 
     if (dlds) PM_TRY(check_ptr(ctx, dlds, "dlds"));
     DeviceGuard guard(ctx->device);
     const int B = ctx->P.n_batch;
-    PM_CUDA(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * B, ctx->stream));
+    PM_MEMSET(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * B, ctx->stream));
     PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
-    PM_LAUNCH(ctx, launch_paint(PAINT_DENSITY, pa, ctx->stream));
-    PM_CUDA(ctx, cudaMemsetAsync(ctx->d_pk, 0, sizeof(double) * B, ctx->stream));
-    PM_LAUNCH(ctx, launch_mse(mesh_ref(ctx), target, ctx->P.n_m, B, ctx->d_pk, ctx->stream));
+    PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
+    PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_pk, 0, sizeof(double) * B, ctx->stream));
+    PM_LAUNCH(ctx, "mse", launch_mse(mesh_ref(ctx), target, ctx->P.n_m, B, ctx->d_pk, ctx->stream));
     if (dlds) {
         ReadArgs ra = read_args(ctx, const_cast<float *>(s));
         ra.f = dlds;
-        PM_LAUNCH(ctx, launch_read(READ_GRAD, ra, ctx->stream));
+        PM_LAUNCH(ctx, read_kind(READ_GRAD), launch_read(READ_GRAD, ra, ctx->stream));
     }
     std::vector<double> acc(B);
     PM_CUDA(ctx, cudaMemcpyAsync(acc.data(), ctx->d_pk, sizeof(double) * B, cudaMemcpyDeviceToHost, ctx->stream));
@@ -695,12 +806,12 @@ int pm_power_spectrum(pm_ctx *ctx, const float *s, double *k_mean, double *power
     if (!k_mean || !power || !n_modes) return fail(ctx, PM_EINVAL, "host outputs must not be NULL");
     DeviceGuard guard(ctx->device);
     const int B = ctx->P.n_batch, nb = ctx->P.n_m / 2;
-    PM_CUDA(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * B, ctx->stream));
+    PM_MEMSET(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * B, ctx->stream));
     PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
-    PM_LAUNCH(ctx, launch_paint(PAINT_DENSITY, pa, ctx->stream));
+    PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
     PM_TRY(mesh_r2c(ctx, 0, 1));
-    PM_CUDA(ctx, cudaMemsetAsync(ctx->d_pk, 0, sizeof(double) * B * 3 * nb, ctx->stream));
-    PM_LAUNCH(ctx, launch_power_bins(mesh_spec(ctx), ctx->d_pk, nb, ctx->stream));
+    PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_pk, 0, sizeof(double) * B * 3 * nb, ctx->stream));
+    PM_LAUNCH(ctx, "power_bins", launch_power_bins(mesh_spec(ctx), ctx->d_pk, nb, ctx->stream));
     std::vector<double> acc((size_t)B * 3 * nb);
     PM_CUDA(ctx, cudaMemcpyAsync(acc.data(), ctx->d_pk, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost,
                                  ctx->stream));
@@ -712,7 +823,7 @@ int pm_power_spectrum(pm_ctx *ctx, const float *s, double *k_mean, double *power
             const double *a = acc.data() + ((size_t)b * nb + i) * 3;
             const double cnt = a[0] > 0 ? a[0] : 1.0;
             n_modes[(size_t)b * nb + i] = a[0];
-            k_mean[(size_t)b * nb + i] = a[1] / cnt;
+            k_mean[(size_t)b * nb + i] = a[1] / cnt * (2.0 * M_PI / ctx->P.box);
             power[(size_t)b * nb + i] = vol / n6 * a[2] / cnt;
         }
     return PM_OK;

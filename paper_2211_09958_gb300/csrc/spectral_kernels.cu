@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_spec_adj(Spec sp, const float *pre
     c0[3 * fs] = make_float2(px.x + py.x + pz.x, px.y + py.y + pz.y);
 }
 
-// |delta_k|^2 binned in |k| shells; acc[b][bin][0..2] += (n_modes, sum |k|, sum |delta|^2).
+// |delta_k|^2 binned in |k| shells; acc[b][bin][0..2] += (n_modes, sum |k| / k_F, sum |delta|^2).
 __global__ void __launch_bounds__(kThreads) k_power_bins(Spec sp, double *acc, int nbins) {
     extern __shared__ double sh[];
     const int b = blockIdx.y;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_power_bins(Spec sp, double *acc, i
         const float2 d = c0[m];
         const double p2 = (double)d.x * d.x + (double)d.y * d.y;
         atomicAdd(&sh[3 * bin], w);
-        atomicAdd(&sh[3 * bin + 1], w * kn * sp.kf);
+        atomicAdd(&sh[3 * bin + 1], w * kn);
         atomicAdd(&sh[3 * bin + 2], w * p2);
     }
     __syncthreads();

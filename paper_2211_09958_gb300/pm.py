@@ -203,6 +203,8 @@ class _Simulate(torch.autograd.Function):
         f = pm.integrate(s, p)
         ctx.pm = pm
         ctx.cosmo = (pm.omega_m.copy(), pm.sigma8.copy())
+        ctx.cosmo_dev = (omega_m.device, sigma8.device)
+        ctx.cosmo_dtype = (omega_m.dtype, sigma8.dtype)
         ctx.save_for_backward(noise, s, p, f)
         return s, p
 
@@ -216,9 +218,10 @@ class _Simulate(torch.autograd.Function):
         mu = gp.contiguous().clone() if gp is not None else torch.zeros_like(p)
         dom = pm.adjoint_integrate(s, p, f, lam, mu, mu_zero=gp is None)
         dnoise, dcos = pm.init_lpt_adjoint(lam, mu, noise, want_noise_grad=ctx.needs_input_grad[0])
-        dev = noise.device
-        g_om = torch.as_tensor(dom + dcos[:, 0], dtype=torch.float64, device=dev) if ctx.needs_input_grad[1] else None
-        g_s8 = torch.as_tensor(dcos[:, 1], dtype=torch.float64, device=dev) if ctx.needs_input_grad[2] else None
+        g_om = torch.as_tensor(dom + dcos[:, 0], dtype=ctx.cosmo_dtype[0], device=ctx.cosmo_dev[0]) \
+            if ctx.needs_input_grad[1] else None
+        g_s8 = torch.as_tensor(dcos[:, 1], dtype=ctx.cosmo_dtype[1], device=ctx.cosmo_dev[1]) \
+            if ctx.needs_input_grad[2] else None
         return dnoise, g_om, g_s8, None
 
 
