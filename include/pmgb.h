@@ -164,6 +164,34 @@ int pm_density_adjoint(pm_ctx *ctx, const float *s, const float *ddelta, float *
  *   dlds device [n_batch][n_p^3][3] output or NULL. */
 int pm_mse_loss(pm_ctx *ctx, const float *s, const float *target, double *loss, float *dlds);
 
+/* Allocation-free variant of pm_mse_loss, for callers that cannot call
+ * cudaMalloc: code whose device memory is all reserved up front by another
+ * allocator (a framework's caching pool, a serving process's fixed arena)
+ * and latency-critical loops that cannot take the implicit device-wide
+ * synchronisation of cudaMalloc / cudaFree.  The paper has no counterpart;
+ * this is an interface convenience.
+ *
+ * Needs no context.  Computes the same loss and adjoint seed as
+ * pm_mse_loss for the geometry (n_p, n_m, n_batch, box) on the given CUDA
+ * stream (void* cudaStream_t, NULL = legacy default stream), asynchronously.
+ *   s       device [n_batch][n_p^3][3] displacements
+ *   target  device [n_batch][n_m^3]
+ *   loss    device [n_batch] doubles (8-byte aligned) output
+ *   dlds    device [n_batch][n_p^3][3] output, or NULL
+ * Scratch: one file-scope __device__ array (8 MiB + 512 B) that every GPU
+ * loading the library holds until exit; it limits n_batch * n_m^3 to 2^21
+ * cells (a single 128^3 mesh) and n_batch to 64 -- larger sizes return
+ * PM_ERANGE before any device work.  Nothing is allocated or freed.  All
+ * calls share that array: each call clears what it needs, and calls that
+ * overlap on the GPU (on different streams, or concurrently from several
+ * host threads) race on it and give wrong results.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress, once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Returns PM_OK, PM_EINVAL (bad size, NULL or misaligned pointer),
+ * PM_ERANGE or PM_ECUDA; there is no error message for this entry point. */
+int pm_mse_loss_noalloc(int32_t n_p, int32_t n_m, int32_t n_batch, double box, const float *s,
+                        const float *target, double *loss, float *dlds, void *stream);
+
 /* power_spectrum -- binned power of the CIC density contrast (paper:
  * summary statistics such as the power spectrum, Statement of Need).
  * Bins b = 0 .. n_m/2 - 1 have edges (b + 1/2) k_F .. (b + 3/2) k_F,
