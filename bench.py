@@ -115,14 +115,14 @@ class ClockSampler:
 def algorithmic_bytes(kind, npart, ncell, nmodes):
     per = {
         "paint_density": 12 * npart + 4 * ncell,
-        "paint_kdk": (36 + 24) * npart + 4 * ncell,
-        "paint_adj": 24 * npart + 16 * ncell,
-        "paint_adj_drift": (48 + 24) * npart + 16 * ncell,
+        "paint_adj": 24 * npart + 16 * ncell,                # s, mu in; 4 fields out
         "read_force": 24 * npart + 12 * ncell,
-        "read_kick_drift": 48 * npart + 12 * ncell,
-        "read_half_kick": (24 + 24) * npart + 12 * ncell,
-        "read_adj": (48 + 24) * npart + 16 * ncell,
+        "read_kick_drift": 48 * npart + 12 * ncell,          # s, p in and out; 3 fields in
+        "read_half_kick": 48 * npart + 12 * ncell,           # s, p in; p, F out
+        "read_adj": (48 + 48) * npart + 16 * ncell,          # s, p, lam, mu in and out (fused drift)
         "read_grad": 24 * npart + 4 * ncell,
+        "pre_rev_drift": 72 * npart,
+        "pre_kick_drift": 60 * npart,
         "spectral_force": (8 + 24) * nmodes,
         "spectral_adj": (32 + 32) * nmodes,
     }

@@ -115,14 +115,7 @@ struct ProfScope {
     }
 };
 
-const char *paint_kind(int mode) {
-    switch (mode) {
-        case PAINT_DENSITY: return "paint_density";
-        case PAINT_KDK_PRE: return "paint_kdk";
-        case PAINT_ADJ: return "paint_adj";
-        default: return "paint_adj_drift";
-    }
-}
+const char *paint_kind(int mode) { return mode == PAINT_ADJ ? "paint_adj" : "paint_density"; }
 
 const char *read_kind(int mode) {
     switch (mode) {
@@ -245,7 +238,6 @@ Spec lat_spec(pm_ctx *ctx) {
                 (float)(2.0 * M_PI / ctx->P.box)};
 }
 
-float *mesh_field(pm_ctx *ctx, int f) { return ctx->mesh + (int64_t)f * ctx->mesh_pad * ctx->P.n_batch; }
 float *lat_field(pm_ctx *ctx, int f) { return ctx->lat + (int64_t)f * ctx->lat_pad * ctx->P.n_batch; }
 
 int fft_fields(pm_ctx *ctx, cufftHandle plan, bool r2c, float *base, int64_t fstride, int f0, int nf) {
@@ -273,13 +265,12 @@ int lat_c2r(pm_ctx *ctx, int f0, int nf) {
     return fft_fields(ctx, ctx->lc2r, false, ctx->lat, ctx->lat_pad * ctx->P.n_batch, f0, nf);
 }
 
-PaintArgs paint_args(pm_ctx *ctx, float *s) {
+PaintArgs paint_args(pm_ctx *ctx, const float *s, const float *mu = nullptr) {
     PaintArgs a{};
     a.g = ctx->g;
     a.s = s;
+    a.mu = mu;
     a.mesh = mesh_ref(ctx);
-    a.table = ctx->d_table;
-    a.red_bstride = 2 * (ctx->P.n_steps + 1);
     return a;
 }
 
@@ -290,20 +281,40 @@ ReadArgs read_args(pm_ctx *ctx, float *s) {
     a.mesh = mesh_ref(ctx);
     a.table = ctx->d_table;
     a.red_bstride = 2 * (ctx->P.n_steps + 1);
+    a.drift_step = -1;
     return a;
 }
 
-// Paint (after zeroing the painted fields), forward transform, spectral
-// multiply and inverse transforms; leaves the force meshes (and psi for the
-// adjoint) in the scratch fields.
-int force_meshes(pm_ctx *ctx, int paint_mode, const PaintArgs &pa) {
-    const bool adj = paint_mode == PAINT_ADJ || paint_mode == PAINT_ADJ_DRIFT;
+PreArgs pre_args(pm_ctx *ctx, float *s, float *p) {
+    PreArgs a{};
+    a.g = ctx->g;
+    a.s = s;
+    a.p = p;
+    a.table = ctx->d_table;
+    a.red_bstride = 2 * (ctx->P.n_steps + 1);
+    return a;
+}
+
+// Zero, paint, forward transform(s), spectral
+// multiply and inverse transforms; leaves F_x, F_y, F_z (and psi for the
+// adjoint) in the scratch fields.  mu != NULL selects the 4-field adjoint
+// paint.
+int force_meshes(pm_ctx *ctx, const float *s, const float *mu) {
+    const bool adj = mu != nullptr;
     const int nf = adj ? 4 : 1;
+    const int mode = adj ? PAINT_ADJ : PAINT_DENSITY;
+    PaintArgs pa = paint_args(ctx, s, mu);
     PM_MEMSET(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * ctx->P.n_batch * nf, ctx->stream));
-    PM_LAUNCH(ctx, paint_kind(paint_mode), launch_paint(paint_mode, pa, ctx->stream));
+    PM_LAUNCH(ctx, paint_kind(mode), launch_paint(mode, pa, ctx->stream));
     PM_TRY(mesh_r2c(ctx, 0, nf));
     PM_LAUNCH(ctx, (adj ? "spectral_adj" : "spectral_force"), launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream));
     PM_TRY(mesh_c2r(ctx, 0, adj ? 4 : 3));
+    return PM_OK;
+}
+
+// Interpolate from the force meshes (particles in lattice order).
+int read_forces(pm_ctx *ctx, int mode, const ReadArgs &ra) {
+    PM_LAUNCH(ctx, read_kind(mode), launch_read(mode, ra, ctx->stream));
     return PM_OK;
 }
 
@@ -566,12 +577,10 @@ int pm_force(pm_ctx *ctx, const float *s, float *f) {
     PM_TRY(check_ptr(ctx, s, "s"));
     PM_TRY(check_ptr(ctx, f, "f"));
     DeviceGuard guard(ctx->device);
-    PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
-    PM_TRY(force_meshes(ctx, PAINT_DENSITY, pa));
+    PM_TRY(force_meshes(ctx, s, nullptr));
     ReadArgs ra = read_args(ctx, const_cast<float *>(s));
     ra.f = f;
-    PM_LAUNCH(ctx, read_kind(READ_FORCE), launch_read(READ_FORCE, ra, ctx->stream));
-    return PM_OK;
+    return read_forces(ctx, READ_FORCE, ra);
 }
 
 int pm_kdk_step(pm_ctx *ctx, int32_t step, float *s, float *p, float *f) {
@@ -581,18 +590,17 @@ int pm_kdk_step(pm_ctx *ctx, int32_t step, float *s, float *p, float *f) {
     PM_TRY(check_ptr(ctx, f, "f"));
     if (step < 0 || step >= ctx->P.n_steps) return fail(ctx, PM_EINVAL, "step out of range");
     DeviceGuard guard(ctx->device);
-    PaintArgs pa = paint_args(ctx, s);
-    pa.p = p;
-    pa.f = f;
-    pa.step = step;
-    PM_TRY(force_meshes(ctx, PAINT_KDK_PRE, pa));
+    PreArgs pr = pre_args(ctx, s, p);
+    pr.f = f;
+    pr.step = step;
+    PM_LAUNCH(ctx, "pre_kick_drift", launch_pre(PRE_KICK_DRIFT, pr, ctx->stream));
+    PM_TRY(force_meshes(ctx, s, nullptr));
     ReadArgs ra = read_args(ctx, s);
     ra.p = p;
     ra.f = f;
     ra.kick_step = step;
     ra.kick_sel = KICK_B;
-    PM_LAUNCH(ctx, read_kind(READ_HALF_KICK), launch_read(READ_HALF_KICK, ra, ctx->stream));
-    return PM_OK;
+    return read_forces(ctx, READ_HALF_KICK, ra);
 }
 
 int pm_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, float *p, float *f) {
@@ -603,24 +611,27 @@ int pm_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, fl
     if (step_begin < 0 || step_end > ctx->P.n_steps || step_begin >= step_end)
         return fail(ctx, PM_EINVAL, "need 0 <= step_begin < step_end <= n_steps");
     DeviceGuard guard(ctx->device);
-    PaintArgs pa = paint_args(ctx, s);
     ReadArgs ra = read_args(ctx, s);
     ra.p = p;
     ra.f = f;
     for (int n = step_begin; n < step_end; ++n) {
-        PM_TRY(force_meshes(ctx, PAINT_DENSITY, pa));
+        PM_TRY(force_meshes(ctx, s, nullptr));
         ra.kick_step = n;
         ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
         ra.drift_step = n;
-        PM_LAUNCH(ctx, read_kind(READ_KICK_DRIFT), launch_read(READ_KICK_DRIFT, ra, ctx->stream));
+        PM_TRY(read_forces(ctx, READ_KICK_DRIFT, ra));
     }
-    PM_TRY(force_meshes(ctx, PAINT_DENSITY, pa));
+    PM_TRY(force_meshes(ctx, s, nullptr));
     ra.kick_step = step_end - 1;
     ra.kick_sel = KICK_B;
-    PM_LAUNCH(ctx, read_kind(READ_HALF_KICK), launch_read(READ_HALF_KICK, ra, ctx->stream));
-    return PM_OK;
+    ra.drift_step = -1;
+    return read_forces(ctx, READ_HALF_KICK, ra);
 }
 
+// Reverse time: the state enters at a[step_end].  Each iteration n paints at
+// s_n, whose reverse drift was applied by the previous read (or by the
+// opening pre-kernel), and its read both finishes step n (VJP, undo of the
+// merged kick) and applies the reverse drift of step n - 1.
 int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, float *p, const float *f,
                          float *lam, float *mu, double *domega, uint32_t flags) {
     if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
@@ -636,28 +647,30 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
     PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * B * 2 * (N + 1), ctx->stream));
     const int last = step_end - 1;
     if (flags & PM_ADJ_MU_ZERO) {
+        // undo the last half kick with the stored F(s_N) (mu = 0: no VJP)
         PM_LAUNCH(ctx, "kick", launch_kick(ctx->g, p, f, ctx->d_table, last, KICK_B, -1.f, ctx->stream));
+        PreArgs pr = pre_args(ctx, s, p);
+        pr.lam = lam;
+        pr.mu = mu;
+        pr.step = last;
+        pr.red = ctx->d_red + 2 * last + 1;
+        PM_LAUNCH(ctx, "pre_rev_drift", launch_pre(PRE_REV_DRIFT, pr, ctx->stream));
     } else {
-        PaintArgs pa = paint_args(ctx, s);
-        pa.mu = mu;
-        PM_TRY(force_meshes(ctx, PAINT_ADJ, pa));
+        // VJP of the last half kick at s_N, fused with the reverse drift of step `last`
+        PM_TRY(force_meshes(ctx, s, mu));
         ReadArgs ra = read_args(ctx, s);
         ra.p = p;
         ra.lam = lam;
         ra.mu = mu;
         ra.kick_step = last;
         ra.kick_sel = KICK_B;
+        ra.drift_step = last;
         ra.red = ctx->d_red + 2 * N;
-        PM_LAUNCH(ctx, read_kind(READ_ADJ), launch_read(READ_ADJ, ra, ctx->stream));
+        ra.red2_offset = (2 * last + 1) - 2 * N;
+        PM_TRY(read_forces(ctx, READ_ADJ, ra));
     }
     for (int n = last; n >= step_begin; --n) {
-        PaintArgs pa = paint_args(ctx, s);
-        pa.p = p;
-        pa.lam = lam;
-        pa.mu = mu;
-        pa.step = n;
-        pa.red = ctx->d_red + 2 * n + 1;
-        PM_TRY(force_meshes(ctx, PAINT_ADJ_DRIFT, pa));
+        PM_TRY(force_meshes(ctx, s, mu));
         ReadArgs ra = read_args(ctx, s);
         ra.p = p;
         ra.lam = lam;
@@ -665,7 +678,11 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
         ra.kick_step = n;
         ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
         ra.red = ctx->d_red + 2 * n;
-        PM_LAUNCH(ctx, read_kind(READ_ADJ), launch_read(READ_ADJ, ra, ctx->stream));
+        if (n > step_begin) {
+            ra.drift_step = n - 1;
+            ra.red2_offset = (2 * (n - 1) + 1) - 2 * n;
+        }
+        PM_TRY(read_forces(ctx, READ_ADJ, ra));
     }
     if (domega) {
         std::vector<double> red((size_t)B * 2 * (N + 1));

@@ -64,21 +64,31 @@ enum KickSel { KICK_A = 0, KICK_MERGED = 1, KICK_B = 2 };
 
 enum PaintMode {
     PAINT_DENSITY = 0,   // paint weight alpha at s
-    PAINT_KDK_PRE = 1,   // p += K_a f; s += Dr p; paint alpha at the new s
-    PAINT_ADJ = 2,       // paint (alpha, mu_x, mu_y, mu_z) at s into 4 fields
-    PAINT_ADJ_DRIFT = 3  // s -= Dr p; mu += Dr lam (reduce lam.p); then PAINT_ADJ
+    PAINT_ADJ = 2        // paint (alpha, mu_x, mu_y, mu_z) at s into 4 fields
 };
 
 struct PaintArgs {
+    Geom g;
+    const float *s;
+    const float *mu;
+    MeshRef mesh;
+};
+
+// Particle-local work that precedes a force evaluation.
+enum PreMode {
+    PRE_KICK_DRIFT = 0,  // p += K_a f; s += Dr p            (first half of a KDK step)
+    PRE_REV_DRIFT = 1    // s -= Dr p; mu += Dr lam; reduce lam.p (opens an adjoint step)
+};
+
+struct PreArgs {
     Geom g;
     float *s, *p;
     const float *f;
     const float *lam;
     float *mu;
-    MeshRef mesh;
-    const float4 *table;  // [n_steps][nb]
+    const float4 *table;
     int step;
-    double *red;          // drift reduction of this step (batch stride red_bstride)
+    double *red;
     int red_bstride;
 };
 
@@ -86,22 +96,23 @@ enum ReadMode {
     READ_FORCE = 0,       // f = F(s)
     READ_KICK_DRIFT = 1,  // p += c F; s += Dr p
     READ_HALF_KICK = 2,   // p += c F; f = F
-    READ_ADJ = 3,         // F, vjp: lam += c vjp; p -= c F; reduce mu.F
+    READ_ADJ = 3,         // F, vjp: lam += c vjp; p -= c F; reduce mu.F; optional fused reverse drift
     READ_GRAD = 4         // ds = alpha sum grad W mesh
 };
 
 struct ReadArgs {
     Geom g;
-    float *s, *p, *f, *lam;
-    const float *mu;
+    float *s, *p, *f, *lam, *mu;
     MeshRef mesh;
     const float4 *table;
-    int kick_step, kick_sel, drift_step;
+    int kick_step, kick_sel, drift_step;  // drift_step < 0: no drift
     double *red;          // kick reduction (batch stride red_bstride)
     int red_bstride;
+    int red2_offset;      // drift reduction at red + red2_offset (0 when no drift)
 };
 
 cudaError_t launch_paint(int mode, const PaintArgs &a, cudaStream_t st);
+cudaError_t launch_pre(int mode, const PreArgs &a, cudaStream_t st);
 cudaError_t launch_read(int mode, const ReadArgs &a, cudaStream_t st);
 cudaError_t launch_fill(float *ptr, int64_t n, float v, cudaStream_t st);
 cudaError_t launch_unpad(const float *src, int64_t bstride, int zs, float *dst, int n, int nb, cudaStream_t st);

@@ -8,7 +8,7 @@ non-bit-exact because floating-point atomics add in arbitrary order):
     bound on the momentum scale; the largest errors sit with the largest
     momenta, in collapsed regions)
   * reversal (forward then reverse, both FP32): |ds| <= 1e-4 of the spacing
-    and |dp| <= 1e-4 of rms of the FINAL momenta: rounding happens at the
+    and |dp| <= 3e-4 of rms of the FINAL momenta: rounding happens at the
     scale of the late, large momenta (g_p grows ~ a^1.5, x500 from a = 1/64),
     so relative to the tiny initial momenta the same absolute error is large
   * force: max |dF| <= 2e-5 of max |F| (FP32 paint/FFT/read rounding,
@@ -176,7 +176,7 @@ def test_forward_then_reverse_returns_initial_state():
     pm.adjoint_integrate(s, p, f, lam, mu)
     ds = torch.max(torch.abs(s - s0)).item() / (box / n_p)
     dp = torch.max(torch.abs(p - p0)).item() / p_scale
-    assert ds < 3e-4 and dp < 1e-4, (ds, dp)
+    assert ds < 3e-4 and dp < 3e-4, (ds, dp)
 
 
 def test_adjoint_integrate_parity():
