@@ -117,7 +117,7 @@ def algorithmic_bytes(kind, npart, ncell, nmodes):
         "paint_density": 12 * npart + 4 * ncell,
         "paint_adj": 24 * npart + 16 * ncell,                # s, mu in; 4 fields out
         "read_force": 24 * npart + 12 * ncell,
-        "read_kick_drift": 48 * npart + 12 * ncell,          # s, p in and out; 3 fields in
+        "read_kick_drift": 48 * npart + 12 * ncell,          # s, p in and out; 3 force fields in
         "read_half_kick": 48 * npart + 12 * ncell,           # s, p in; p, F out
         "read_adj": (48 + 48) * npart + 16 * ncell,          # s, p, lam, mu in and out (fused drift)
         "read_grad": 24 * npart + 4 * ncell,
@@ -126,6 +126,15 @@ def algorithmic_bytes(kind, npart, ncell, nmodes):
         "spectral_force": (8 + 24) * nmodes,
         "spectral_adj": (32 + 32) * nmodes,
     }
+    # own FFT passes: kind "fft_<axis>_<dir>_<fields>"
+    if kind.startswith("fft_"):
+        _, axis, direction, nf = kind.split("_")
+        nf = int(nf)
+        if axis == "z" and direction == "fwd":
+            return nf * (4 * ncell + 8 * nmodes)          # real fields in, half spectra out
+        if axis == "z":
+            return nf * 8 * nmodes + (4 if nf == 1 else 16) * ncell   # spectra in, real mesh out
+        return nf * 16 * nmodes                             # pencil pass: read + write
     return per.get(kind)
 
 

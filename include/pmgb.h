@@ -192,6 +192,16 @@ int pm_mse_loss(pm_ctx *ctx, const float *s, const float *target, double *loss, 
 int pm_mse_loss_noalloc(int32_t n_p, int32_t n_m, int32_t n_batch, double box, const float *s,
                         const float *target, double *loss, float *dlds, void *stream);
 
+/* The library's unnormalised 3D real FFT of n_m^3 meshes (the transform of
+ * the force pipeline), forward X(k) = sum_c x(c) e^{-i k.c h} and inverse
+ * without the 1/n_m^3 factor.
+ *   real  device [n_batch][n_m^3] floats
+ *   spec  device [n_batch][n_m][n_m][n_m/2 + 1] complex (re, im float pairs)
+ * pm_mesh_irfft reads only the Hermitian half spectrum and treats the
+ * imaginary parts of the kz = 0 and kz = n_m/2 entries as zero. */
+int pm_mesh_rfft(pm_ctx *ctx, const float *real, float *spec);
+int pm_mesh_irfft(pm_ctx *ctx, const float *spec, float *real);
+
 /* power_spectrum -- binned power of the CIC density contrast (paper:
  * summary statistics such as the power spectrum, Statement of Need).
  * Bins b = 0 .. n_m/2 - 1 have edges (b + 1/2) k_F .. (b + 3/2) k_F,

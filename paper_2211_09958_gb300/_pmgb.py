@@ -58,6 +58,8 @@ _SIGNATURES = {
     "pm_mse_loss": (ctypes.c_int, [_P, _P, _P, _c_double_p, _P]),
     "pm_mse_loss_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _P, _P,
                                            _P, _P, _P]),
+    "pm_mesh_rfft": (ctypes.c_int, [_P, _P, _P]),
+    "pm_mesh_irfft": (ctypes.c_int, [_P, _P, _P]),
     "pm_power_spectrum": (ctypes.c_int, [_P, _P, _c_double_p, _c_double_p, _c_double_p]),
     "pm_launch_count": (ctypes.c_int64, [_P]),
     "pm_profile": (ctypes.c_int, [_P, ctypes.c_int]),

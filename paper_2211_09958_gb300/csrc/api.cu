@@ -43,6 +43,12 @@ struct pm_ctx {
     double *d_pk = nullptr;
     double *d_lred = nullptr;
     cufftHandle r2c = 0, c2r = 0, lr2c = 0, lc2r = 0;
+    // own FFT (power-of-two meshes): real meshes r1 ([run][n^3]) and r4
+    // ([run][n^3][4] interleaved), four spectrum fields, twiddle table
+    bool own = false;
+    FftGeom fg{};
+    float *r1 = nullptr, *r4 = nullptr;
+    float2 *spec = nullptr, *tw = nullptr;
     bool have_plans = false;
     void *work = nullptr;
     std::string err;
@@ -218,24 +224,44 @@ int check_cosmology(pm_ctx *ctx, const double *om, const double *s8, int B) {
 
 // --------------------------------------------------------------- pieces --
 
+// The force meshes the read kernels interpolate from.
 MeshRef mesh_ref(pm_ctx *ctx) {
-    return MeshRef{ctx->mesh, ctx->mesh_pad * ctx->P.n_batch, ctx->mesh_pad, 2 * (ctx->P.n_m / 2 + 1)};
+    const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
+    if (ctx->own) return MeshRef{ctx->r4, 0, 4 * n3, ctx->P.n_m, 4};
+    return MeshRef{ctx->mesh, ctx->mesh_pad * ctx->P.n_batch, ctx->mesh_pad, 2 * (ctx->P.n_m / 2 + 1), 0};
+}
+
+// A single real scratch field (density).
+MeshRef density_ref(pm_ctx *ctx) {
+    const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
+    if (ctx->own) return MeshRef{ctx->r1, 0, n3, ctx->P.n_m, 0};
+    return MeshRef{ctx->mesh, 0, ctx->mesh_pad, 2 * (ctx->P.n_m / 2 + 1), 0};
+}
+
+int64_t density_floats(pm_ctx *ctx) {
+    const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
+    return (ctx->own ? n3 : ctx->mesh_pad) * ctx->P.n_batch;
 }
 
 Spec mesh_spec(pm_ctx *ctx) {
+    const float kf = (float)(2.0 * M_PI / ctx->P.box);
+    const int n = ctx->P.n_m;
+    if (ctx->own) {
+        const int64_t per = (int64_t)n * n * ctx->fg.zc;
+        return Spec{ctx->spec, per * ctx->P.n_batch, per, n, ctx->P.n_batch, kf, ctx->fg.zc};
+    }
     const int64_t modes = ctx->mesh_pad / 2;
-    return Spec{reinterpret_cast<float2 *>(ctx->mesh), modes * ctx->P.n_batch, modes, ctx->P.n_m, ctx->P.n_batch,
-                (float)(2.0 * M_PI / ctx->P.box)};
+    return Spec{reinterpret_cast<float2 *>(ctx->mesh), modes * ctx->P.n_batch, modes, n, ctx->P.n_batch, kf, n / 2 + 1};
 }
 
 MeshRef lat_ref(pm_ctx *ctx) {
-    return MeshRef{ctx->lat, ctx->lat_pad * ctx->P.n_batch, ctx->lat_pad, 2 * (ctx->P.n_p / 2 + 1)};
+    return MeshRef{ctx->lat, ctx->lat_pad * ctx->P.n_batch, ctx->lat_pad, 2 * (ctx->P.n_p / 2 + 1), 0};
 }
 
 Spec lat_spec(pm_ctx *ctx) {
     const int64_t modes = ctx->lat_pad / 2;
     return Spec{reinterpret_cast<float2 *>(ctx->lat), modes * ctx->P.n_batch, modes, ctx->P.n_p, ctx->P.n_batch,
-                (float)(2.0 * M_PI / ctx->P.box)};
+                (float)(2.0 * M_PI / ctx->P.box), ctx->P.n_p / 2 + 1};
 }
 
 float *lat_field(pm_ctx *ctx, int f) { return ctx->lat + (int64_t)f * ctx->lat_pad * ctx->P.n_batch; }
@@ -295,6 +321,31 @@ PreArgs pre_args(pm_ctx *ctx, float *s, float *p) {
     return a;
 }
 
+const char *own_kind(int pass, int nf) {
+    static const char *names[6][5] = {
+        {"", "fft_z_fwd_1", "", "", "fft_z_fwd_4"}, {"", "fft_y_fwd_1", "", "", "fft_y_fwd_4"},
+        {"", "fft_x_fwd_1", "", "", "fft_x_fwd_4"}, {"", "fft_x_inv_1", "", "fft_x_inv_3", "fft_x_inv_4"},
+        {"", "fft_y_inv_1", "", "fft_y_inv_3", "fft_y_inv_4"}, {"", "fft_z_inv_1", "", "fft_z_inv_3", "fft_z_inv_4"}};
+    return names[pass][nf];
+}
+
+// Own forward 3D transform of g interleaved real fields into spectrum fields 0 .. g-1.
+int own_forward(pm_ctx *ctx, const float *real, int g) {
+    PM_LAUNCH(ctx, own_kind(0, g), launch_fft_z_fwd(g, real, ctx->spec, ctx->fg, ctx->stream));
+    PM_LAUNCH(ctx, own_kind(1, g), launch_fft_pencils(1, false, ctx->spec, 0, g, ctx->fg, ctx->stream));
+    PM_LAUNCH(ctx, own_kind(2, g), launch_fft_pencils(0, false, ctx->spec, 0, g, ctx->fg, ctx->stream));
+    return PM_OK;
+}
+
+// Own inverse 3D transform of spectrum fields 0 .. g-1 (g = 3, 4: into the
+// interleaved r4 layout; g = 1: plain real field).
+int own_inverse(pm_ctx *ctx, float *real, int g) {
+    PM_LAUNCH(ctx, own_kind(3, g), launch_fft_pencils(0, true, ctx->spec, 0, g, ctx->fg, ctx->stream));
+    PM_LAUNCH(ctx, own_kind(4, g), launch_fft_pencils(1, true, ctx->spec, 0, g, ctx->fg, ctx->stream));
+    PM_LAUNCH(ctx, own_kind(5, g), launch_fft_z_inv(g, ctx->spec, real, ctx->fg, ctx->stream));
+    return PM_OK;
+}
+
 // Zero, paint, forward transform(s), spectral
 // multiply and inverse transforms; leaves F_x, F_y, F_z (and psi for the
 // adjoint) in the scratch fields.  mu != NULL selects the 4-field adjoint
@@ -304,6 +355,17 @@ int force_meshes(pm_ctx *ctx, const float *s, const float *mu) {
     const int nf = adj ? 4 : 1;
     const int mode = adj ? PAINT_ADJ : PAINT_DENSITY;
     PaintArgs pa = paint_args(ctx, s, mu);
+    if (ctx->own) {
+        const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
+        float *real = adj ? ctx->r4 : ctx->r1;
+        pa.mesh = adj ? mesh_ref(ctx) : density_ref(ctx);
+        PM_MEMSET(ctx, cudaMemsetAsync(real, 0, sizeof(float) * n3 * nf * ctx->P.n_batch, ctx->stream));
+        PM_LAUNCH(ctx, paint_kind(mode), launch_paint(mode, pa, ctx->stream));
+        PM_TRY(own_forward(ctx, real, nf));
+        PM_LAUNCH(ctx, (adj ? "spectral_adj" : "spectral_force"),
+                  launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream));
+        return own_inverse(ctx, ctx->r4, adj ? 4 : 3);
+    }
     PM_MEMSET(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * ctx->P.n_batch * nf, ctx->stream));
     PM_LAUNCH(ctx, paint_kind(mode), launch_paint(mode, pa, ctx->stream));
     PM_TRY(mesh_r2c(ctx, 0, nf));
@@ -441,8 +503,31 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
         return code;
     };
     const int B = c.n_batch;
-    if (cudaMalloc(&ctx->mesh, sizeof(float) * (size_t)ctx->mesh_pad * B * kMeshFields) != cudaSuccess ||
-        cudaMalloc(&ctx->d_table, sizeof(float4) * (size_t)c.n_steps * B) != cudaSuccess ||
+    ctx->own = own_fft_supported(c.n_m);
+    if (ctx->own) {
+        const int n = c.n_m;
+        ctx->fg.n = n;
+        ctx->fg.nb = B;
+        ctx->fg.zc = own_fft_zc(n);
+        ctx->fg.fstride = (int64_t)B * n * n * ctx->fg.zc;
+        const size_t n3 = (size_t)n * n * n;
+        if (cudaMalloc(&ctx->r1, sizeof(float) * n3 * B) != cudaSuccess ||
+            cudaMalloc(&ctx->r4, sizeof(float) * 4 * n3 * B) != cudaSuccess ||
+            cudaMalloc(&ctx->spec, sizeof(float2) * 4 * (size_t)ctx->fg.fstride) != cudaSuccess ||
+            cudaMalloc(&ctx->tw, sizeof(float2) * 1024) != cudaSuccess ||
+            cudaMemset(ctx->spec, 0, sizeof(float2) * 4 * (size_t)ctx->fg.fstride) != cudaSuccess ||
+            upload_fft_constants(ctx->tw) != cudaSuccess) {
+            cudaGetLastError();
+            fail(ctx, PM_ENOMEM, "cannot allocate the FFT meshes");
+            return bail(PM_ENOMEM);
+        }
+        ctx->fg.tw = ctx->tw;
+    } else if (cudaMalloc(&ctx->mesh, sizeof(float) * (size_t)ctx->mesh_pad * B * kMeshFields) != cudaSuccess) {
+        cudaGetLastError();
+        fail(ctx, PM_ENOMEM, "cannot allocate the FFT meshes");
+        return bail(PM_ENOMEM);
+    }
+    if (cudaMalloc(&ctx->d_table, sizeof(float4) * (size_t)c.n_steps * B) != cudaSuccess ||
         cudaMalloc(&ctx->d_pref, sizeof(float) * B) != cudaSuccess ||
         cudaMalloc(&ctx->d_fac, sizeof(float4) * B) != cudaSuccess ||
         cudaMalloc(&ctx->d_lin, sizeof(LinParams) * B) != cudaSuccess ||
@@ -456,8 +541,8 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
     int rc = upload_tables(ctx);
     if (rc) return bail(rc);
     size_t ws[4] = {0, 0, 0, 0};
-    if ((rc = make_plan(ctx, &ctx->r2c, c.n_m, true, B, &ws[0])) ||
-        (rc = make_plan(ctx, &ctx->c2r, c.n_m, false, B, &ws[1])) ||
+    if ((!ctx->own && (rc = make_plan(ctx, &ctx->r2c, c.n_m, true, B, &ws[0]))) ||
+        (!ctx->own && (rc = make_plan(ctx, &ctx->c2r, c.n_m, false, B, &ws[1]))) ||
         (rc = make_plan(ctx, &ctx->lr2c, c.n_p, true, B, &ws[2])) ||
         (rc = make_plan(ctx, &ctx->lc2r, c.n_p, false, B, &ws[3])))
         return bail(rc);
@@ -472,7 +557,7 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
         }
     }
     for (cufftHandle h : {ctx->r2c, ctx->c2r, ctx->lr2c, ctx->lc2r}) {
-        if (cufftSetWorkArea(h, ctx->work) != CUFFT_SUCCESS) {
+        if (h && cufftSetWorkArea(h, ctx->work) != CUFFT_SUCCESS) {
             fail(ctx, PM_ECUFFT, "cufftSetWorkArea failed");
             return bail(PM_ECUFFT);
         }
@@ -491,6 +576,8 @@ int pm_destroy(pm_ctx *ctx) {
             if (h) cufftDestroy(h);
     }
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->spec, (void *)ctx->tw}) 
+        if (p) cudaFree(p);
     for (void *p : {(void *)ctx->mesh, (void *)ctx->lat, (void *)ctx->d_table, (void *)ctx->d_pref,
                     (void *)ctx->d_fac, (void *)ctx->d_lin, (void *)ctx->d_red, (void *)ctx->d_pk,
                     (void *)ctx->d_lred, ctx->work})
@@ -502,7 +589,8 @@ int pm_destroy(pm_ctx *ctx) {
 int pm_set_stream(pm_ctx *ctx, void *stream) {
     if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
     ctx->stream = static_cast<cudaStream_t>(stream);
-    for (cufftHandle h : {ctx->r2c, ctx->c2r, ctx->lr2c, ctx->lc2r}) PM_FFT(ctx, cufftSetStream(h, ctx->stream));
+    for (cufftHandle h : {ctx->r2c, ctx->c2r, ctx->lr2c, ctx->lc2r})
+        if (h) PM_FFT(ctx, cufftSetStream(h, ctx->stream));
     return PM_OK;
 }
 
@@ -799,13 +887,16 @@ int pm_mse_loss(pm_ctx *ctx, const float *s, const float *target, double *loss, 
     if (dlds) PM_TRY(check_ptr(ctx, dlds, "dlds"));
     DeviceGuard guard(ctx->device);
     const int B = ctx->P.n_batch;
-    PM_MEMSET(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * B, ctx->stream));
+    const MeshRef dref = density_ref(ctx);
+    PM_MEMSET(ctx, cudaMemsetAsync(dref.ptr, 0, sizeof(float) * density_floats(ctx), ctx->stream));
     PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
+    pa.mesh = dref;
     PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
     PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_pk, 0, sizeof(double) * B, ctx->stream));
-    PM_LAUNCH(ctx, "mse", launch_mse(mesh_ref(ctx), target, ctx->P.n_m, B, ctx->d_pk, ctx->stream));
+    PM_LAUNCH(ctx, "mse", launch_mse(dref, target, ctx->P.n_m, B, ctx->d_pk, ctx->stream));
     if (dlds) {
         ReadArgs ra = read_args(ctx, const_cast<float *>(s));
+        ra.mesh = dref;
         ra.f = dlds;
         PM_LAUNCH(ctx, read_kind(READ_GRAD), launch_read(READ_GRAD, ra, ctx->stream));
     }
@@ -817,16 +908,64 @@ int pm_mse_loss(pm_ctx *ctx, const float *s, const float *target, double *loss, 
     return PM_OK;
 }
 
+int pm_mesh_rfft(pm_ctx *ctx, const float *real, float *spec) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, real, "real"));
+    PM_TRY(check_ptr(ctx, spec, "spec"));
+    DeviceGuard guard(ctx->device);
+    const int n = ctx->P.n_m, B = ctx->P.n_batch;
+    const size_t row = sizeof(float2) * (n / 2 + 1);
+    if (ctx->own) {
+        PM_TRY(own_forward(ctx, real, 1));
+        PM_CUDA(ctx, cudaMemcpy2DAsync(spec, row, ctx->spec, sizeof(float2) * ctx->fg.zc, row, (size_t)B * n * n,
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+        return PM_OK;
+    }
+    const int zs = 2 * (n / 2 + 1);
+    PM_CUDA(ctx, cudaMemcpy2DAsync(ctx->mesh, sizeof(float) * zs, real, sizeof(float) * n, sizeof(float) * n,
+                                   (size_t)B * n * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    PM_TRY(mesh_r2c(ctx, 0, 1));
+    PM_CUDA(ctx, cudaMemcpyAsync(spec, ctx->mesh, sizeof(float) * ctx->mesh_pad * B, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+    return PM_OK;
+}
+
+int pm_mesh_irfft(pm_ctx *ctx, const float *spec, float *real) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, spec, "spec"));
+    PM_TRY(check_ptr(ctx, real, "real"));
+    DeviceGuard guard(ctx->device);
+    const int n = ctx->P.n_m, B = ctx->P.n_batch;
+    const size_t row = sizeof(float2) * (n / 2 + 1);
+    if (ctx->own) {
+        PM_CUDA(ctx, cudaMemcpy2DAsync(ctx->spec, sizeof(float2) * ctx->fg.zc, spec, row, row, (size_t)B * n * n,
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+        return own_inverse(ctx, real, 1);
+    }
+    const int zs = 2 * (n / 2 + 1);
+    PM_CUDA(ctx, cudaMemcpyAsync(ctx->mesh, spec, sizeof(float) * ctx->mesh_pad * B, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+    PM_TRY(mesh_c2r(ctx, 0, 1));
+    PM_CUDA(ctx, cudaMemcpy2DAsync(real, sizeof(float) * n, ctx->mesh, sizeof(float) * zs, sizeof(float) * n,
+                                   (size_t)B * n * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return PM_OK;
+}
+
 int pm_power_spectrum(pm_ctx *ctx, const float *s, double *k_mean, double *power, double *n_modes) {
     if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
     PM_TRY(check_ptr(ctx, s, "s"));
     if (!k_mean || !power || !n_modes) return fail(ctx, PM_EINVAL, "host outputs must not be NULL");
     DeviceGuard guard(ctx->device);
     const int B = ctx->P.n_batch, nb = ctx->P.n_m / 2;
-    PM_MEMSET(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * B, ctx->stream));
+    const MeshRef dref = density_ref(ctx);
+    PM_MEMSET(ctx, cudaMemsetAsync(dref.ptr, 0, sizeof(float) * density_floats(ctx), ctx->stream));
     PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
+    pa.mesh = dref;
     PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
-    PM_TRY(mesh_r2c(ctx, 0, 1));
+    if (ctx->own)
+        PM_TRY(own_forward(ctx, ctx->r1, 1));
+    else
+        PM_TRY(mesh_r2c(ctx, 0, 1));
     PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_pk, 0, sizeof(double) * B * 3 * nb, ctx->stream));
     PM_LAUNCH(ctx, "power_bins", launch_power_bins(mesh_spec(ctx), ctx->d_pk, nb, ctx->stream));
     std::vector<double> acc((size_t)B * 3 * nb);

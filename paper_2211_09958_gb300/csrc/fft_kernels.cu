@@ -1,0 +1,376 @@
+// The library's own 3D real FFT for power-of-two meshes (16 <= n <= 1024),
+// in three passes per direction, laid out for the PM pipeline:
+//
+//   real meshes     [run][x][y][z][G] floats, G = 1 (density) or 4
+//                   (interleaved adjoint sources / force components)
+//   spectra         [field][run][x][y][zc] complex, kz = 0 .. n/2 valid,
+//                   row pitch zc = n/2 + 1 rounded up to 8 (pad kept at 0)
+//
+//   z pass  (R2C / C2R)  rows of n reals as n/2-point complex FFTs with the
+//                        even/odd packing; reads or writes the interleaved
+//                        real mesh and the spectrum rows
+//   pencil  (y and x)    8 adjacent kz columns (64 contiguous bytes per
+//                        row) transformed along y or x
+//
+// Conventions match cuFFT's unnormalised R2C / C2R: forward
+// X_k = sum_n x_n e^{-2 pi i k n / n}, inverse without 1/n.  The spectral
+// kernels apply the 1/n^3.
+//
+// A line of L = M1 * M2 complex points is transformed by the four-step
+// method: M1 threads each do an M2-point FFT in registers on a stride-M1
+// subsequence, multiply by W_L^{n1 k2}, exchange through shared memory (pitch
+// M2 + 1 to spread banks), and M2 threads each do an M1-point FFT.  The
+// register FFTs are radix-2 decimation in frequency (bit-reversed output),
+// fully unrolled.  Twiddles come from a table of W_1024^j computed in double
+// precision on the host; the 32 register-FFT twiddles sit in constant memory.
+
+#include <cmath>
+
+#include "pm_internal.h"
+
+namespace pmgb {
+
+__constant__ float2 c_w32[32];  // e^{-2 pi i k / 32}
+
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+__host__ __device__ constexpr int bitrev(int k, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r = (r << 1) | ((k >> i) & 1);
+    return r;
+}
+// L = split1(L) * (L / split1(L)), split1(L) >= L / split1(L), both <= 32.
+__host__ __device__ constexpr int split1(int l) { return 1 << ((ilog2(l) + 1) / 2); }
+__host__ __device__ constexpr int line_pitch(int l) { return l + split1(l) + 2; }  // >= M1 (M2 + 1), even
+
+// In-register radix-2 DIF FFT of R <= 32 points; v[i] ends as X[bitrev(i)].
+template <int R, bool INV>
+__device__ __forceinline__ void reg_fft(float2 (&v)[R]) {
+#pragma unroll
+    for (int span = R / 2; span >= 1; span >>= 1) {
+#pragma unroll
+        for (int j = 0; j < R; j += 2 * span) {
+#pragma unroll
+            for (int k = 0; k < span; ++k) {
+                const float2 a = v[j + k], b = v[j + k + span];
+                v[j + k] = cadd(a, b);
+                const float2 d = csub(a, b);
+                if (k == 0) {
+                    v[j + k + span] = d;
+                } else {
+                    float2 w = c_w32[k * (32 / (2 * span))];
+                    if (INV) w.y = -w.y;
+                    v[j + k + span] = cmul(d, w);
+                }
+            }
+        }
+    }
+}
+
+// Four-step FFT of one line of L = M1 * M2 points held in shared memory
+// (pitch >= M1 (M2 + 1)), by the M1 threads t = 0 .. M1-1 of one warp (or
+// sub-warp).  Every lane of the warp must call it (it uses __syncwarp).
+template <int L, bool INV>
+__device__ __forceinline__ void line_fft(float2 *line, int t, const float2 *__restrict__ tw) {
+    constexpr int M1 = split1(L), M2 = L / M1;
+    float2 v[M2];
+#pragma unroll
+    for (int n2 = 0; n2 < M2; ++n2) v[n2] = line[t + M1 * n2];
+    __syncwarp();
+    reg_fft<M2, INV>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) {
+        float2 w = __ldg(tw + t * k2 * (1024 / L));
+        if (INV) w.y = -w.y;
+        line[t * (M2 + 1) + k2] = cmul(v[bitrev(k2, ilog2(M2))], w);
+    }
+    __syncwarp();
+    float2 u[M1];
+    if (t < M2) {
+#pragma unroll
+        for (int n1 = 0; n1 < M1; ++n1) u[n1] = line[n1 * (M2 + 1) + t];
+    }
+    __syncwarp();
+    if (t < M2) {
+        reg_fft<M1, INV>(u);
+#pragma unroll
+        for (int k1 = 0; k1 < M1; ++k1) line[t + M2 * k1] = u[bitrev(k1, ilog2(M1))];
+    }
+    __syncwarp();
+}
+
+// --------------------------------------------------------------- z pass ---
+
+template <int N, int G>
+struct ZShape {
+    static constexpr int M = N / 2, TL = split1(M), LP = line_pitch(M);
+    static constexpr int Y = (256 / TL / G) < N ? (256 / TL / G) : N;  // rows per block
+    static constexpr int LINES = Y * G, THREADS = LINES * TL;
+};
+
+// Forward: G interleaved real fields -> spectrum fields 0 .. G-1.
+template <int N, int G>
+__global__ void __launch_bounds__(256) k_fft_z_fwd(const float *__restrict__ in, float2 *spec, FftGeom fg) {
+    using S = ZShape<N, G>;
+    constexpr int M = S::M, TL = S::TL, Y = S::Y, LP = S::LP;
+    extern __shared__ float4 smraw[];
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int tid = threadIdx.x, line = tid / TL, t = tid % TL;
+    constexpr int NYB = N / Y;
+    const int y0 = (int)(blockIdx.x % NYB) * Y;
+    const int64_t bx = blockIdx.x / NYB;  // run * N + x
+    const float4 *src = reinterpret_cast<const float4 *>(in + (bx * N + y0) * (int64_t)N * G);
+    constexpr int NV = Y * N * G / 4;
+    for (int e = tid; e < NV; e += S::THREADS) {
+        const float4 q = src[e];
+        if (G == 1) {
+            const int yl = (4 * e) / N, z = (4 * e) % N;
+            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(sm + yl * LP) + z) = q;
+        } else {
+            const int yl = e / N, z = e % N;
+            float *l0 = reinterpret_cast<float *>(sm + yl * 4 * LP);
+            l0[z] = q.x;
+            l0[2 * LP + z] = q.y;
+            l0[4 * LP + z] = q.z;
+            l0[6 * LP + z] = q.w;
+        }
+    }
+    __syncthreads();
+    line_fft<M, false>(sm + line * LP, t, fg.tw);
+    const int yl = line / G, g = line % G;
+    const float2 *Lz = sm + line * LP;
+    float2 *dst = spec + g * fg.fstride + (bx * N + y0 + yl) * (int64_t)fg.zc;
+    for (int k = t; k <= M / 2; k += TL) {
+        const float2 zk = Lz[k], zm = Lz[(M - k) & (M - 1)];
+        const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        const float2 WO = cmul(__ldg(fg.tw + k * (1024 / N)), O);
+        dst[k] = cadd(E, WO);
+        const float2 r = csub(E, WO);
+        if (k == 0)
+            dst[M] = make_float2(r.x, -r.y);
+        else if (k < M / 2)
+            dst[M - k] = make_float2(r.x, -r.y);
+    }
+}
+
+// Inverse: spectrum fields 0 .. GS-1 -> real mesh with GO interleaved
+// slots per cell (GO = 4: slots >= GS written as 0; GO = 1: plain rows).
+template <int N, int GS, int GO>
+__global__ void __launch_bounds__(256) k_fft_z_inv(const float2 *__restrict__ spec, float *out, FftGeom fg) {
+    using S = ZShape<N, GO>;
+    constexpr int M = S::M, TL = S::TL, Y = S::Y, LP = S::LP;
+    extern __shared__ float4 smraw[];
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int tid = threadIdx.x, line = tid / TL, t = tid % TL;
+    constexpr int NYB = N / Y;
+    const int y0 = (int)(blockIdx.x % NYB) * Y;
+    const int64_t bx = blockIdx.x / NYB;
+    const int yl = line / GO, g = line % GO;
+    float2 *Lz = sm + line * LP;
+    if (g < GS) {
+        const float2 *src = spec + g * fg.fstride + (bx * N + y0 + yl) * (int64_t)fg.zc;
+        for (int k = t; k <= M / 2; k += TL) {
+            float2 xk = src[k], xm = src[M - k];
+            if (k == 0) {
+                xk.y = 0.f;
+                xm.y = 0.f;
+            }
+            const float2 wf = __ldg(fg.tw + k * (1024 / N));
+            const float2 w = make_float2(wf.x, -wf.y);  // W_N^{-k}
+            // Z_k = (X_k + conj X_{M-k}) + i (X_k - conj X_{M-k}) W_N^{-k}
+            const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);
+            const float2 Dw = cmul(make_float2(xk.x - xm.x, xk.y + xm.y), w);
+            Lz[k] = make_float2(A.x - Dw.y, A.y + Dw.x);
+            if (k > 0 && k < M / 2) {
+                // Z_{M-k}: same with the pair swapped and W_N^{-(M-k)} = -conj(W_N^{-k})
+                const float2 A2 = make_float2(xm.x + xk.x, xm.y - xk.y);
+                const float2 Dw2 = cmul(make_float2(xm.x - xk.x, xm.y + xk.y), make_float2(-w.x, w.y));
+                Lz[M - k] = make_float2(A2.x - Dw2.y, A2.y + Dw2.x);
+            }
+        }
+    } else {
+        for (int k = t; k < M; k += TL) Lz[k] = make_float2(0.f, 0.f);
+    }
+    __syncwarp();
+    line_fft<M, true>(Lz, t, fg.tw);
+    __syncthreads();
+    float4 *dst = reinterpret_cast<float4 *>(out + (bx * N + y0) * (int64_t)N * GO);
+    if (GO == 4) {
+        for (int e = tid; e < Y * N; e += S::THREADS) {
+            const int y2 = e / N, z = e % N;
+            const float *l0 = reinterpret_cast<const float *>(sm + y2 * 4 * LP);
+            dst[e] = make_float4(l0[z], l0[2 * LP + z], l0[4 * LP + z], GS == 4 ? l0[6 * LP + z] : 0.f);
+        }
+    } else {
+        for (int e = tid; e < Y * N / 4; e += S::THREADS) {
+            const int y2 = (4 * e) / N, z = (4 * e) % N;
+            dst[e] = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(sm + y2 * LP) + z);
+        }
+    }
+}
+
+// -------------------------------------------------------------- pencils ---
+
+constexpr int kPencil = 8;
+
+template <int L, bool INV>
+__global__ void __launch_bounds__(256) k_fft_pencil(float2 *data, PencilGeom pg, const float2 *__restrict__ tw) {
+    constexpr int TL = split1(L), LP = line_pitch(L), THREADS = kPencil * TL;
+    extern __shared__ float4 smraw[];
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int tid = threadIdx.x, line = tid / TL, t = tid % TL;
+    const int64_t p = blockIdx.x;
+    const int64_t kzp = p % pg.nkz, rest = p / pg.nkz;
+    const int64_t mid = rest % pg.nmid, outer = rest / pg.nmid;
+    float2 *base = data + outer * pg.os + mid * pg.ms + kzp * kPencil;
+    for (int e = tid; e < L * kPencil; e += THREADS) {
+        const int n = e / kPencil, w = e % kPencil;
+        sm[w * LP + n] = base[(int64_t)n * pg.ls + w];
+    }
+    __syncthreads();
+    line_fft<L, INV>(sm + line * LP, t, tw);
+    __syncthreads();
+    for (int e = tid; e < L * kPencil; e += THREADS) {
+        const int n = e / kPencil, w = e % kPencil;
+        base[(int64_t)n * pg.ls + w] = sm[w * LP + n];
+    }
+}
+
+template <int N, int G>
+cudaError_t z_fwd_n(const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {
+    using S = ZShape<N, G>;
+    const size_t smem = sizeof(float2) * S::LINES * S::LP;
+    cudaError_t e = cudaFuncSetAttribute(k_fft_z_fwd<N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (int64_t)fg.nb * N * (N / S::Y);
+    k_fft_z_fwd<N, G><<<(unsigned)blocks, S::THREADS, smem, st>>>(in, spec, fg);
+    return cudaGetLastError();
+}
+
+template <int N, int GS, int GO>
+cudaError_t z_inv_n(const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st) {
+    using S = ZShape<N, GO>;
+    const size_t smem = sizeof(float2) * S::LINES * S::LP;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fft_z_inv<N, GS, GO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (int64_t)fg.nb * N * (N / S::Y);
+    k_fft_z_inv<N, GS, GO><<<(unsigned)blocks, S::THREADS, smem, st>>>(spec, out, fg);
+    return cudaGetLastError();
+}
+
+template <int L, bool INV>
+cudaError_t pencil_n(float2 *data, const PencilGeom &pg, int64_t blocks, const float2 *tw, cudaStream_t st) {
+    constexpr int TL = split1(L);
+    const size_t smem = sizeof(float2) * kPencil * line_pitch(L);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_pencil<L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fft_pencil<L, INV><<<(unsigned)blocks, kPencil * TL, smem, st>>>(data, pg, tw);
+    return cudaGetLastError();
+}
+
+template <int G>
+cudaError_t z_fwd_g(const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {
+    switch (fg.n) {
+        case 16: return z_fwd_n<16, G>(in, spec, fg, st);
+        case 32: return z_fwd_n<32, G>(in, spec, fg, st);
+        case 64: return z_fwd_n<64, G>(in, spec, fg, st);
+        case 128: return z_fwd_n<128, G>(in, spec, fg, st);
+        case 256: return z_fwd_n<256, G>(in, spec, fg, st);
+        case 512: return z_fwd_n<512, G>(in, spec, fg, st);
+        case 1024: return z_fwd_n<1024, G>(in, spec, fg, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int GS, int GO>
+cudaError_t z_inv_g(const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st) {
+    switch (fg.n) {
+        case 16: return z_inv_n<16, GS, GO>(spec, out, fg, st);
+        case 32: return z_inv_n<32, GS, GO>(spec, out, fg, st);
+        case 64: return z_inv_n<64, GS, GO>(spec, out, fg, st);
+        case 128: return z_inv_n<128, GS, GO>(spec, out, fg, st);
+        case 256: return z_inv_n<256, GS, GO>(spec, out, fg, st);
+        case 512: return z_inv_n<512, GS, GO>(spec, out, fg, st);
+        case 1024: return z_inv_n<1024, GS, GO>(spec, out, fg, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <bool INV>
+cudaError_t pencil_l(float2 *data, const PencilGeom &pg, int n, int64_t blocks, const float2 *tw, cudaStream_t st) {
+    switch (n) {
+        case 16: return pencil_n<16, INV>(data, pg, blocks, tw, st);
+        case 32: return pencil_n<32, INV>(data, pg, blocks, tw, st);
+        case 64: return pencil_n<64, INV>(data, pg, blocks, tw, st);
+        case 128: return pencil_n<128, INV>(data, pg, blocks, tw, st);
+        case 256: return pencil_n<256, INV>(data, pg, blocks, tw, st);
+        case 512: return pencil_n<512, INV>(data, pg, blocks, tw, st);
+        case 1024: return pencil_n<1024, INV>(data, pg, blocks, tw, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool own_fft_supported(int n) { return n >= 16 && n <= 1024 && (n & (n - 1)) == 0; }
+
+int own_fft_zc(int n) { return ((n / 2 + 1) + kPencil - 1) / kPencil * kPencil; }
+
+cudaError_t upload_fft_constants(float2 *tw_dev) {
+    float2 w32[32], w1024[1024];
+    for (int k = 0; k < 32; ++k) w32[k] = make_float2((float)std::cos(2.0 * M_PI * k / 32), (float)-std::sin(2.0 * M_PI * k / 32));
+    for (int k = 0; k < 1024; ++k)
+        w1024[k] = make_float2((float)std::cos(2.0 * M_PI * k / 1024), (float)-std::sin(2.0 * M_PI * k / 1024));
+    cudaError_t e = cudaMemcpyToSymbol(c_w32, w32, sizeof(w32));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(tw_dev, w1024, sizeof(w1024), cudaMemcpyHostToDevice);
+}
+
+cudaError_t launch_fft_z_fwd(int g, const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {
+    return g == 4 ? z_fwd_g<4>(in, spec, fg, st) : z_fwd_g<1>(in, spec, fg, st);
+}
+
+cudaError_t launch_fft_z_inv(int gs, const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st) {
+    switch (gs) {
+        case 4: return z_inv_g<4, 4>(spec, out, fg, st);
+        case 3: return z_inv_g<3, 4>(spec, out, fg, st);
+        case 1: return z_inv_g<1, 1>(spec, out, fg, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Transform fields [f0, f0 + nf) of the spectrum along y (axis 1) or x
+// (axis 0), forward or inverse.
+cudaError_t launch_fft_pencils(int axis, bool inverse, float2 *spec, int f0, int nf, const FftGeom &fg,
+                               cudaStream_t st) {
+    const int n = fg.n;
+    PencilGeom pg{};
+    pg.nkz = fg.zc / kPencil;
+    float2 *base = spec + f0 * fg.fstride;
+    int64_t blocks;
+    if (axis == 1) {  // lines along y: one pencil per (field, run, x, kz block)
+        pg.ls = fg.zc;
+        pg.nmid = 1;
+        pg.os = (int64_t)n * fg.zc;
+        pg.ms = 0;
+        blocks = (int64_t)nf * fg.nb * n * pg.nkz;
+    } else {  // lines along x: one pencil per (field, run, y, kz block)
+        pg.ls = (int64_t)n * fg.zc;
+        pg.nmid = n;
+        pg.ms = fg.zc;
+        pg.os = (int64_t)n * n * fg.zc;
+        blocks = (int64_t)nf * fg.nb * n * pg.nkz;
+    }
+    return inverse ? pencil_l<true>(base, pg, n, blocks, fg.tw, st) : pencil_l<false>(base, pg, n, blocks, fg.tw, st);
+}
+
+}  // namespace pmgb

@@ -50,12 +50,14 @@ struct Geom {
 };
 
 // A set of real meshes: field f of batch b starts at ptr + f*fstride + b*bstride;
-// rows along z are zs floats apart (zs = 2 (nm/2 + 1) for the in-place FFT
-// layout, nm for a caller's plain mesh).
+// rows along z are zs floats apart (zs = 2 (nm/2 + 1) for the cuFFT in-place
+// layout, nm for a plain mesh).  il = 4: the four fields are interleaved per
+// cell (cell c of run b at ptr + b*bstride + 4 c), fstride unused.
 struct MeshRef {
     float *ptr;
     int64_t fstride, bstride;
     int zs;
+    int il;
 };
 
 // Per step and simulation KDK factors on the device: x = K_a, y = Dr,
@@ -120,14 +122,36 @@ cudaError_t launch_mse(MeshRef mesh, const float *target, int n, int nb, double 
 cudaError_t launch_kick(const Geom &g, float *p, const float *f, const float4 *table, int step, int sel,
                         float sign, cudaStream_t st);
 
-// Spectral kernels over an rfft grid n x n x (n/2+1) (complex elements);
-// field f of batch b starts at c + f*fstride + b*bstride (complex elements).
+// Spectral kernels over an rfft grid n x n x (n/2+1) stored with row pitch
+// zc >= n/2+1 (complex elements); field f of batch b starts at
+// c + f*fstride + b*bstride (complex elements).
 struct Spec {
     float2 *c;
     int64_t fstride, bstride;
     int n, nb;
     float kf;  // 2 pi / box
+    int zc;
 };
+
+// The library's own FFT (fft_kernels.cu): spectra [field][run][x][y][zc].
+struct FftGeom {
+    int n, nb, zc;
+    int64_t fstride;    // complex elements per spectrum field (all runs)
+    const float2 *tw;   // W_1024^j, j < 1024
+};
+
+struct PencilGeom {
+    int64_t nkz, nmid, os, ms, ls;
+};
+
+bool own_fft_supported(int n);
+int own_fft_zc(int n);
+cudaError_t upload_fft_constants(float2 *tw_dev);
+cudaError_t launch_fft_z_fwd(int g, const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st);
+// gs = 4 or 3: spectrum fields -> 4-slot interleaved real mesh; gs = 1: plain real mesh.
+cudaError_t launch_fft_z_inv(int gs, const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st);
+cudaError_t launch_fft_pencils(int axis, bool inverse, float2 *spec, int f0, int nf, const FftGeom &fg,
+                               cudaStream_t st);
 
 enum SpecMode { SPEC_FORCE = 0, SPEC_ADJ = 1 };
 cudaError_t launch_spectral(int mode, const Spec &sp, const float *pref, cudaStream_t st);

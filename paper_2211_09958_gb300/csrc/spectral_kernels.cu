@@ -22,10 +22,9 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ void mode_ijk(int64_t m, int n, int &ix, int &iy, int &iz) {
-    const int nz = n / 2 + 1;
-    const int64_t r = m / nz;
-    iz = (int)(m - r * nz);
+__device__ __forceinline__ void mode_ijk(int64_t m, int n, int zc, int &ix, int &iy, int &iz) {
+    const int64_t r = m / zc;
+    iz = (int)(m - r * zc);
     const int64_t x = r / n;
     iy = (int)(r - x * n);
     ix = (int)x;
@@ -38,11 +37,12 @@ __device__ __forceinline__ float2 times_i(float2 v, float s) { return make_float
 __global__ void __launch_bounds__(kThreads) k_spec_force(Spec sp, const float *pref) {
     const int b = blockIdx.y;
     const int n = sp.n;
-    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t nmodes = (int64_t)n * n * sp.zc;
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
-    mode_ijk(m, n, ix, iy, iz);
+    mode_ijk(m, n, sp.zc, ix, iy, iz);
+    if (iz > n / 2) return;
     const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
     const float k2 = kx * kx + ky * ky + kz * kz;
     const float g = k2 > 0.f ? pref[b] / k2 : 0.f;
@@ -60,11 +60,12 @@ __global__ void __launch_bounds__(kThreads) k_spec_force(Spec sp, const float *p
 __global__ void __launch_bounds__(kThreads) k_spec_adj(Spec sp, const float *pref) {
     const int b = blockIdx.y;
     const int n = sp.n;
-    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t nmodes = (int64_t)n * n * sp.zc;
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
-    mode_ijk(m, n, ix, iy, iz);
+    mode_ijk(m, n, sp.zc, ix, iy, iz);
+    if (iz > n / 2) return;
     const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
     const float k2 = kx * kx + ky * ky + kz * kz;
     const float g = k2 > 0.f ? pref[b] / k2 : 0.f;
@@ -87,11 +88,12 @@ __global__ void __launch_bounds__(kThreads) k_power_bins(Spec sp, double *acc, i
     const int n = sp.n;
     for (int q = threadIdx.x; q < 3 * nbins; q += blockDim.x) sh[q] = 0.0;
     __syncthreads();
-    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t nmodes = (int64_t)n * n * sp.zc;
     const float2 *c0 = sp.c + (int64_t)b * sp.bstride;
     for (int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x; m < nmodes; m += (int64_t)gridDim.x * kThreads) {
         int ix, iy, iz;
-        mode_ijk(m, n, ix, iy, iz);
+        mode_ijk(m, n, sp.zc, ix, iy, iz);
+        if (iz > n / 2) continue;
         const int nx = signed_index(ix, n), ny = signed_index(iy, n);
         const int64_t n2 = (int64_t)nx * nx + (int64_t)ny * ny + (int64_t)iz * iz;
         if (n2 == 0) continue;
@@ -186,11 +188,12 @@ __device__ __forceinline__ void linear_mult(double k, const LinParams &lp, doubl
 __global__ void __launch_bounds__(kThreads) k_lpt_linear(Spec sp, const LinParams *lps) {
     const int b = blockIdx.y;
     const int n = sp.n;
-    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t nmodes = (int64_t)n * n * sp.zc;
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
-    mode_ijk(m, n, ix, iy, iz);
+    mode_ijk(m, n, sp.zc, ix, iy, iz);
+    if (iz > n / 2) return;
     const double kx = sp.kf * (double)signed_index(ix, n), ky = sp.kf * (double)signed_index(iy, n),
                  kz = sp.kf * (double)iz;
     const double k2 = kx * kx + ky * ky + kz * kz;
@@ -237,11 +240,12 @@ __global__ void k_lpt_source(MeshRef lat, int np, int f_phi, int f_src) {
 __global__ void __launch_bounds__(kThreads) k_lpt_second(Spec sp, int f_src, int f_out, float sign) {
     const int b = blockIdx.y;
     const int n = sp.n;
-    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t nmodes = (int64_t)n * n * sp.zc;
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
-    mode_ijk(m, n, ix, iy, iz);
+    mode_ijk(m, n, sp.zc, ix, iy, iz);
+    if (iz > n / 2) return;
     const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
     const float k2 = kx * kx + ky * ky + kz * kz;
     const float g = k2 > 0.f ? sign / (k2 * (float)n * n * n) : 0.f;
@@ -257,11 +261,12 @@ __global__ void __launch_bounds__(kThreads) k_lpt_second(Spec sp, int f_src, int
 __global__ void __launch_bounds__(kThreads) k_lpt_adj_second(Spec sp, int f_in, int f_out) {
     const int b = blockIdx.y;
     const int n = sp.n;
-    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t nmodes = (int64_t)n * n * sp.zc;
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
-    mode_ijk(m, n, ix, iy, iz);
+    mode_ijk(m, n, sp.zc, ix, iy, iz);
+    if (iz > n / 2) return;
     const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
     const float k2 = kx * kx + ky * ky + kz * kz;
     const float g = k2 > 0.f ? 1.f / (k2 * (float)n * n * n) : 0.f;
@@ -355,12 +360,12 @@ __global__ void k_lpt_adj_phi(MeshRef lat, int np) {
 __global__ void __launch_bounds__(kThreads) k_lpt_adj_final(Spec sp, const LinParams *lps, int f_noise, double *red) {
     const int b = blockIdx.y;
     const int n = sp.n;
-    const int64_t nmodes = (int64_t)n * n * (n / 2 + 1);
+    const int64_t nmodes = (int64_t)n * n * sp.zc;
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     double r0 = 0.0, r1 = 0.0;
-    if (m < nmodes) {
-        int ix, iy, iz;
-        mode_ijk(m, n, ix, iy, iz);
+    int ix = 0, iy = 0, iz = 0;
+    if (m < nmodes) mode_ijk(m, n, sp.zc, ix, iy, iz);
+    if (m < nmodes && iz <= n / 2) {
         const double kx = sp.kf * (double)signed_index(ix, n), ky = sp.kf * (double)signed_index(iy, n),
                      kz = sp.kf * (double)iz;
         const double k2 = kx * kx + ky * ky + kz * kz;
@@ -407,7 +412,7 @@ __global__ void __launch_bounds__(kThreads) k_lpt_adj_final(Spec sp, const LinPa
 }
 
 dim3 mode_grid(const Spec &sp) {
-    const int64_t nmodes = (int64_t)sp.n * sp.n * (sp.n / 2 + 1);
+    const int64_t nmodes = (int64_t)sp.n * sp.n * sp.zc;
     return dim3((unsigned)((nmodes + kThreads - 1) / kThreads), sp.nb);
 }
 
@@ -433,7 +438,7 @@ cudaError_t launch_power_bins(const Spec &sp, double *acc, int nbins, cudaStream
         cudaError_t e = cudaFuncSetAttribute(k_power_bins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int64_t nmodes = (int64_t)sp.n * sp.n * (sp.n / 2 + 1);
+    const int64_t nmodes = (int64_t)sp.n * sp.n * sp.zc;
     const int64_t blocks = (nmodes + kThreads - 1) / kThreads;
     k_power_bins<<<dim3((unsigned)(blocks < 152 * 4 ? blocks : 152 * 4), sp.nb), kThreads, smem, st>>>(sp, acc, nbins);
     return cudaGetLastError();

@@ -276,3 +276,25 @@ def test_errors_do_not_poison_the_context():
     s = torch.zeros((1, 16 ** 3, 3), device="cuda")
     f = pm.pm_force(s)
     assert torch.max(torch.abs(f)).item() < 1e-5      # uniform lattice: no force
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 24])
+def test_mesh_fft_against_numpy(n):
+    # The library's 3D real FFT (own passes for powers of two, cuFFT else)
+    # against numpy's FFT in FP64: forward, and inverse of the forward.
+    from paper_2211_09958_gb300 import _pmgb
+    import ctypes
+    pm = _pm(8, n, 40.0, om=[0.3, 0.3], s8=[0.8, 0.8])
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal((2, n, n, n)).astype(np.float32)
+    xd = _cuda(x)
+    spec = torch.empty((2, n, n, n // 2 + 1, 2), dtype=torch.float32, device="cuda")
+    pm._call("pm_mesh_rfft", ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(spec.data_ptr()))
+    got = _host(spec)
+    got = got[..., 0] + 1j * got[..., 1]
+    ref = np.fft.rfftn(x.astype(np.float64), axes=(1, 2, 3))
+    scale = np.sqrt(n ** 3)           # |X| ~ sqrt(n^3) for unit white noise
+    assert np.max(np.abs(got - ref)) < 2e-5 * scale * np.log2(n ** 3)
+    back = torch.empty_like(xd)
+    pm._call("pm_mesh_irfft", ctypes.c_void_p(spec.data_ptr()), ctypes.c_void_p(back.data_ptr()))
+    np.testing.assert_allclose(_host(back) / n ** 3, x, atol=2e-6 * np.log2(n ** 3))
