@@ -221,6 +221,12 @@ int pm_host_coefficients(const pm_config *cfg, double *kdk, double *dkdk, double
 /* Device-kernel launch counter since pm_create (for benchmarking). */
 int64_t pm_launch_count(const pm_ctx *ctx);
 
+/* pm_integrate and pm_adjoint_integrate capture their launch sequence in a
+ * CUDA graph on first use and replay it when called again with the same
+ * steps and buffers (up to 8 graphs per context; the default).  enable = 0
+ * runs every call as individual launches. */
+int pm_use_graphs(pm_ctx *ctx, int enable);
+
 /* Kernel timing.  pm_profile(ctx, 1) makes every later library kernel, cuFFT
  * call and scratch memset record a CUDA event pair on the context stream,
  * tagged with a kind name; pm_profile_read synchronises that stream and

@@ -62,6 +62,7 @@ _SIGNATURES = {
     "pm_mesh_irfft": (ctypes.c_int, [_P, _P, _P]),
     "pm_power_spectrum": (ctypes.c_int, [_P, _P, _c_double_p, _c_double_p, _c_double_p]),
     "pm_launch_count": (ctypes.c_int64, [_P]),
+    "pm_use_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
     "pm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pm_profile_kinds": (ctypes.c_int, [_P]),
     "pm_profile_name": (ctypes.c_char_p, [_P, ctypes.c_int]),

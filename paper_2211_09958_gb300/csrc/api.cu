@@ -5,6 +5,7 @@
 #include <cufft.h>
 
 #include <cmath>
+#include <functional>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -59,6 +60,18 @@ struct pm_ctx {
     std::vector<cudaEvent_t> pool;
     size_t pool_used = 0;
     std::vector<int> rec_kind;
+    // CUDA graphs of the integration loops, replayed when a call repeats
+    // with the same steps and buffers
+    bool graphs_on = true;
+    cudaStream_t cap_stream = nullptr;
+    struct GraphEntry {
+        int kind, b, e;
+        const void *q[5];
+        uint32_t flags;
+        cudaGraphExec_t exec;
+        int64_t launches;
+    };
+    std::vector<GraphEntry> graphs;
 };
 
 namespace {
@@ -380,6 +393,53 @@ int read_forces(pm_ctx *ctx, int mode, const ReadArgs &ra) {
     return PM_OK;
 }
 
+// Run `body` (a fixed sequence of launches on the context stream) through a
+// cached CUDA graph: the first call with a given key captures it on a
+// private stream, later calls replay it on the context stream.  Profiling
+// bypasses the graphs (its events are recorded per launch).
+int run_graphed(pm_ctx *ctx, int kind, int b, int e, const void *q0, const void *q1, const void *q2, const void *q3,
+                const void *q4, uint32_t flags, const std::function<int()> &body) {
+    if (!ctx->graphs_on || ctx->prof) return body();
+    const void *q[5] = {q0, q1, q2, q3, q4};
+    for (auto &g : ctx->graphs) {
+        if (g.kind == kind && g.b == b && g.e == e && g.flags == flags && std::equal(q, q + 5, g.q)) {
+            PM_CUDA(ctx, cudaGraphLaunch(g.exec, ctx->stream));
+            ctx->launches += g.launches;
+            return PM_OK;
+        }
+    }
+    if (!ctx->cap_stream) PM_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = ctx->stream;
+    PM_TRY(pm_set_stream(ctx, ctx->cap_stream));
+    cudaError_t ce = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess) {
+        pm_set_stream(ctx, user);
+        return fail(ctx, PM_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(ce));
+    }
+    const int64_t l0 = ctx->launches;
+    const int rc = body();
+    cudaGraph_t graph = nullptr;
+    ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    pm_set_stream(ctx, user);
+    if (rc != PM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(ctx, PM_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(ctx, PM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
+    if (ctx->graphs.size() >= 8) {
+        cudaGraphExecDestroy(ctx->graphs.front().exec);
+        ctx->graphs.erase(ctx->graphs.begin());
+    }
+    pm_ctx::GraphEntry ent{kind, b, e, {q0, q1, q2, q3, q4}, flags, exec, ctx->launches - l0};
+    ctx->graphs.push_back(ent);
+    PM_CUDA(ctx, cudaGraphLaunch(exec, user));
+    return PM_OK;
+}
+
 int check_ptr(pm_ctx *ctx, const void *p, const char *name) {
     if (!p) return fail(ctx, PM_EINVAL, std::string(name) + " must not be NULL");
     if ((uintptr_t)p % 4) return fail(ctx, PM_EINVAL, std::string(name) + " must be 4-byte aligned");
@@ -422,6 +482,12 @@ extern "C" {
 const char *pm_last_error(const pm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
 int64_t pm_launch_count(const pm_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int pm_use_graphs(pm_ctx *ctx, int enable) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    ctx->graphs_on = enable != 0;
+    return PM_OK;
+}
 
 int pm_profile(pm_ctx *ctx, int enable) {
     if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
@@ -576,6 +642,8 @@ int pm_destroy(pm_ctx *ctx) {
             if (h) cufftDestroy(h);
     }
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->spec, (void *)ctx->tw}) 
         if (p) cudaFree(p);
     for (void *p : {(void *)ctx->mesh, (void *)ctx->lat, (void *)ctx->d_table, (void *)ctx->d_pref,
@@ -699,21 +767,23 @@ int pm_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, fl
     if (step_begin < 0 || step_end > ctx->P.n_steps || step_begin >= step_end)
         return fail(ctx, PM_EINVAL, "need 0 <= step_begin < step_end <= n_steps");
     DeviceGuard guard(ctx->device);
-    ReadArgs ra = read_args(ctx, s);
-    ra.p = p;
-    ra.f = f;
-    for (int n = step_begin; n < step_end; ++n) {
+    return run_graphed(ctx, 1, step_begin, step_end, s, p, f, nullptr, nullptr, 0, [&]() -> int {
+        ReadArgs ra = read_args(ctx, s);
+        ra.p = p;
+        ra.f = f;
+        for (int n = step_begin; n < step_end; ++n) {
+            PM_TRY(force_meshes(ctx, s, nullptr));
+            ra.kick_step = n;
+            ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
+            ra.drift_step = n;
+            PM_TRY(read_forces(ctx, READ_KICK_DRIFT, ra));
+        }
         PM_TRY(force_meshes(ctx, s, nullptr));
-        ra.kick_step = n;
-        ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
-        ra.drift_step = n;
-        PM_TRY(read_forces(ctx, READ_KICK_DRIFT, ra));
-    }
-    PM_TRY(force_meshes(ctx, s, nullptr));
-    ra.kick_step = step_end - 1;
-    ra.kick_sel = KICK_B;
-    ra.drift_step = -1;
-    return read_forces(ctx, READ_HALF_KICK, ra);
+        ra.kick_step = step_end - 1;
+        ra.kick_sel = KICK_B;
+        ra.drift_step = -1;
+        return read_forces(ctx, READ_HALF_KICK, ra);
+    });
 }
 
 // Reverse time: the state enters at a[step_end].  Each iteration n paints at
@@ -732,46 +802,49 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
         return fail(ctx, PM_EINVAL, "need 0 <= step_begin < step_end <= n_steps");
     DeviceGuard guard(ctx->device);
     const int N = ctx->P.n_steps, B = ctx->P.n_batch;
-    PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * B * 2 * (N + 1), ctx->stream));
     const int last = step_end - 1;
-    if (flags & PM_ADJ_MU_ZERO) {
-        // undo the last half kick with the stored F(s_N) (mu = 0: no VJP)
-        PM_LAUNCH(ctx, "kick", launch_kick(ctx->g, p, f, ctx->d_table, last, KICK_B, -1.f, ctx->stream));
-        PreArgs pr = pre_args(ctx, s, p);
-        pr.lam = lam;
-        pr.mu = mu;
-        pr.step = last;
-        pr.red = ctx->d_red + 2 * last + 1;
-        PM_LAUNCH(ctx, "pre_rev_drift", launch_pre(PRE_REV_DRIFT, pr, ctx->stream));
-    } else {
-        // VJP of the last half kick at s_N, fused with the reverse drift of step `last`
-        PM_TRY(force_meshes(ctx, s, mu));
-        ReadArgs ra = read_args(ctx, s);
-        ra.p = p;
-        ra.lam = lam;
-        ra.mu = mu;
-        ra.kick_step = last;
-        ra.kick_sel = KICK_B;
-        ra.drift_step = last;
-        ra.red = ctx->d_red + 2 * N;
-        ra.red2_offset = (2 * last + 1) - 2 * N;
-        PM_TRY(read_forces(ctx, READ_ADJ, ra));
-    }
-    for (int n = last; n >= step_begin; --n) {
-        PM_TRY(force_meshes(ctx, s, mu));
-        ReadArgs ra = read_args(ctx, s);
-        ra.p = p;
-        ra.lam = lam;
-        ra.mu = mu;
-        ra.kick_step = n;
-        ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
-        ra.red = ctx->d_red + 2 * n;
-        if (n > step_begin) {
-            ra.drift_step = n - 1;
-            ra.red2_offset = (2 * (n - 1) + 1) - 2 * n;
+    PM_TRY(run_graphed(ctx, 2, step_begin, step_end, s, p, f, lam, mu, flags, [&]() -> int {
+        PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * B * 2 * (N + 1), ctx->stream));
+        if (flags & PM_ADJ_MU_ZERO) {
+            // undo the last half kick with the stored F(s_N) (mu = 0: no VJP)
+            PM_LAUNCH(ctx, "kick", launch_kick(ctx->g, p, f, ctx->d_table, last, KICK_B, -1.f, ctx->stream));
+            PreArgs pr = pre_args(ctx, s, p);
+            pr.lam = lam;
+            pr.mu = mu;
+            pr.step = last;
+            pr.red = ctx->d_red + 2 * last + 1;
+            PM_LAUNCH(ctx, "pre_rev_drift", launch_pre(PRE_REV_DRIFT, pr, ctx->stream));
+        } else {
+            // VJP of the last half kick at s_N, fused with the reverse drift of step `last`
+            PM_TRY(force_meshes(ctx, s, mu));
+            ReadArgs ra = read_args(ctx, s);
+            ra.p = p;
+            ra.lam = lam;
+            ra.mu = mu;
+            ra.kick_step = last;
+            ra.kick_sel = KICK_B;
+            ra.drift_step = last;
+            ra.red = ctx->d_red + 2 * N;
+            ra.red2_offset = (2 * last + 1) - 2 * N;
+            PM_TRY(read_forces(ctx, READ_ADJ, ra));
         }
-        PM_TRY(read_forces(ctx, READ_ADJ, ra));
-    }
+        for (int n = last; n >= step_begin; --n) {
+            PM_TRY(force_meshes(ctx, s, mu));
+            ReadArgs ra = read_args(ctx, s);
+            ra.p = p;
+            ra.lam = lam;
+            ra.mu = mu;
+            ra.kick_step = n;
+            ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
+            ra.red = ctx->d_red + 2 * n;
+            if (n > step_begin) {
+                ra.drift_step = n - 1;
+                ra.red2_offset = (2 * (n - 1) + 1) - 2 * n;
+            }
+            PM_TRY(read_forces(ctx, READ_ADJ, ra));
+        }
+        return PM_OK;
+    }));
     if (domega) {
         std::vector<double> red((size_t)B * 2 * (N + 1));
         PM_CUDA(ctx, cudaMemcpyAsync(red.data(), ctx->d_red, sizeof(double) * red.size(), cudaMemcpyDeviceToHost,

@@ -106,6 +106,34 @@ __device__ __forceinline__ void line_fft(float2 *line, int t, const float2 *__re
     __syncwarp();
 }
 
+// Same as line_fft, but step 1 starts from the M2 points v[n2] = line[t + M1 n2]
+// already in registers (loaded by the caller from global memory).
+template <int L, bool INV>
+__device__ __forceinline__ void line_fft_regs(float2 (&v)[L / split1(L)], float2 *line, int t,
+                                              const float2 *__restrict__ tw) {
+    constexpr int M1 = split1(L), M2 = L / M1;
+    reg_fft<M2, INV>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) {
+        float2 w = __ldg(tw + t * k2 * (1024 / L));
+        if (INV) w.y = -w.y;
+        line[t * (M2 + 1) + k2] = cmul(v[bitrev(k2, ilog2(M2))], w);
+    }
+    __syncwarp();
+    float2 u[M1];
+    if (t < M2) {
+#pragma unroll
+        for (int n1 = 0; n1 < M1; ++n1) u[n1] = line[n1 * (M2 + 1) + t];
+    }
+    __syncwarp();
+    if (t < M2) {
+        reg_fft<M1, INV>(u);
+#pragma unroll
+        for (int k1 = 0; k1 < M1; ++k1) line[t + M2 * k1] = u[bitrev(k1, ilog2(M1))];
+    }
+    __syncwarp();
+}
+
 // --------------------------------------------------------------- z pass ---
 
 template <int N, int G>
@@ -126,25 +154,23 @@ __global__ void __launch_bounds__(256) k_fft_z_fwd(const float *__restrict__ in,
     constexpr int NYB = N / Y;
     const int y0 = (int)(blockIdx.x % NYB) * Y;
     const int64_t bx = blockIdx.x / NYB;  // run * N + x
-    const float4 *src = reinterpret_cast<const float4 *>(in + (bx * N + y0) * (int64_t)N * G);
-    constexpr int NV = Y * N * G / 4;
-    for (int e = tid; e < NV; e += S::THREADS) {
-        const float4 q = src[e];
-        if (G == 1) {
-            const int yl = (4 * e) / N, z = (4 * e) % N;
-            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(sm + yl * LP) + z) = q;
-        } else {
-            const int yl = e / N, z = e % N;
-            float *l0 = reinterpret_cast<float *>(sm + yl * 4 * LP);
-            l0[z] = q.x;
-            l0[2 * LP + z] = q.y;
-            l0[4 * LP + z] = q.z;
-            l0[6 * LP + z] = q.w;
-        }
-    }
-    __syncthreads();
-    line_fft<M, false>(sm + line * LP, t, fg.tw);
     const int yl = line / G, g = line % G;
+    {
+        // point n of line (row y0 + yl, field g) is the complex pair of reals
+        // (2n, 2n + 1), i.e. floats G (2n) + g and G (2n + 1) + g of the row
+        constexpr int M1 = split1(M), M2 = M / M1;
+        const float *row = in + ((bx * N + y0 + yl) * (int64_t)N) * G + g;
+        float2 v[M2];
+#pragma unroll
+        for (int n2 = 0; n2 < M2; ++n2) {
+            const int n = t + M1 * n2;
+            if (G == 1)
+                v[n2] = __ldg(reinterpret_cast<const float2 *>(row) + n);
+            else
+                v[n2] = make_float2(__ldg(row + G * 2 * n), __ldg(row + G * (2 * n + 1)));
+        }
+        line_fft_regs<M, false>(v, sm + line * LP, t, fg.tw);
+    }
     const float2 *Lz = sm + line * LP;
     float2 *dst = spec + g * fg.fstride + (bx * N + y0 + yl) * (int64_t)fg.zc;
     for (int k = t; k <= M / 2; k += TL) {
@@ -174,33 +200,34 @@ __global__ void __launch_bounds__(256) k_fft_z_inv(const float2 *__restrict__ sp
     const int y0 = (int)(blockIdx.x % NYB) * Y;
     const int64_t bx = blockIdx.x / NYB;
     const int yl = line / GO, g = line % GO;
-    float2 *Lz = sm + line * LP;
-    if (g < GS) {
-        const float2 *src = spec + g * fg.fstride + (bx * N + y0 + yl) * (int64_t)fg.zc;
-        for (int k = t; k <= M / 2; k += TL) {
-            float2 xk = src[k], xm = src[M - k];
-            if (k == 0) {
-                xk.y = 0.f;
-                xm.y = 0.f;
+    {
+        // step 1 of the inverse M-point FFT starts from Z_k, k = t + M1 n2,
+        // built from the half-spectrum pair (X_k, X_{M-k}):
+        //   Z_k = (X_k + conj X_{M-k}) + i (X_k - conj X_{M-k}) W_N^{-k}
+        // (imaginary parts of X_0 and X_M taken as zero)
+        constexpr int M1 = split1(M), M2 = M / M1;
+        float2 v[M2];
+        if (g < GS) {
+            const float2 *src = spec + g * fg.fstride + (bx * N + y0 + yl) * (int64_t)fg.zc;
+#pragma unroll
+            for (int n2 = 0; n2 < M2; ++n2) {
+                const int k = t + M1 * n2;
+                float2 xk = __ldg(src + k), xm = __ldg(src + (M - k));
+                if (k == 0) {
+                    xk.y = 0.f;
+                    xm.y = 0.f;
+                }
+                const float2 wf = __ldg(fg.tw + k * (1024 / N));
+                const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);
+                const float2 Dw = cmul(make_float2(xk.x - xm.x, xk.y + xm.y), make_float2(wf.x, -wf.y));
+                v[n2] = make_float2(A.x - Dw.y, A.y + Dw.x);
             }
-            const float2 wf = __ldg(fg.tw + k * (1024 / N));
-            const float2 w = make_float2(wf.x, -wf.y);  // W_N^{-k}
-            // Z_k = (X_k + conj X_{M-k}) + i (X_k - conj X_{M-k}) W_N^{-k}
-            const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);
-            const float2 Dw = cmul(make_float2(xk.x - xm.x, xk.y + xm.y), w);
-            Lz[k] = make_float2(A.x - Dw.y, A.y + Dw.x);
-            if (k > 0 && k < M / 2) {
-                // Z_{M-k}: same with the pair swapped and W_N^{-(M-k)} = -conj(W_N^{-k})
-                const float2 A2 = make_float2(xm.x + xk.x, xm.y - xk.y);
-                const float2 Dw2 = cmul(make_float2(xm.x - xk.x, xm.y + xk.y), make_float2(-w.x, w.y));
-                Lz[M - k] = make_float2(A2.x - Dw2.y, A2.y + Dw2.x);
-            }
+        } else {
+#pragma unroll
+            for (int n2 = 0; n2 < M2; ++n2) v[n2] = make_float2(0.f, 0.f);
         }
-    } else {
-        for (int k = t; k < M; k += TL) Lz[k] = make_float2(0.f, 0.f);
+        line_fft_regs<M, true>(v, sm + line * LP, t, fg.tw);
     }
-    __syncwarp();
-    line_fft<M, true>(Lz, t, fg.tw);
     __syncthreads();
     float4 *dst = reinterpret_cast<float4 *>(out + (bx * N + y0) * (int64_t)N * GO);
     if (GO == 4) {
@@ -221,26 +248,53 @@ __global__ void __launch_bounds__(256) k_fft_z_inv(const float2 *__restrict__ sp
 
 constexpr int kPencil = 8;
 
+// Pencil of 8 adjacent columns (64 contiguous bytes per row), lines of L
+// points along a strided axis.  Step 1: thread (n1, w) loads its M2 points of
+// column w straight into registers (a warp covers 4 rows x 64 bytes per
+// load), transforms them and writes the twiddled result to the exchange
+// buffer [n1][k2][w] (n1 pitch M2*8 + 8 keeps half-warps on distinct banks);
+// step 3: thread (k2, w) transforms over n1 and stores straight to global.
+template <int L>
+struct PencilShape {
+    static constexpr int M1 = split1(L), M2 = L / M1, THREADS = M1 * kPencil, YP = M2 * kPencil + kPencil;
+    static constexpr int SMEM = M1 * YP;  // complex elements
+};
+
 template <int L, bool INV>
-__global__ void __launch_bounds__(256) k_fft_pencil(float2 *data, PencilGeom pg, const float2 *__restrict__ tw) {
-    constexpr int TL = split1(L), LP = line_pitch(L), THREADS = kPencil * TL;
+__global__ void __launch_bounds__(PencilShape<L>::THREADS, 2) k_fft_pencil(float2 *data, PencilGeom pg,
+                                                                            const float2 *__restrict__ tw) {
+    using S = PencilShape<L>;
+    constexpr int M1 = S::M1, M2 = S::M2, YP = S::YP, W = kPencil;
     extern __shared__ float4 smraw[];
-    float2 *sm = reinterpret_cast<float2 *>(smraw);
-    const int tid = threadIdx.x, line = tid / TL, t = tid % TL;
+    float2 *ys = reinterpret_cast<float2 *>(smraw);
+    const int tid = threadIdx.x, w = tid % W, r = tid / W;
     const int64_t p = blockIdx.x;
     const int64_t kzp = p % pg.nkz, rest = p / pg.nkz;
     const int64_t mid = rest % pg.nmid, outer = rest / pg.nmid;
-    float2 *base = data + outer * pg.os + mid * pg.ms + kzp * kPencil;
-    for (int e = tid; e < L * kPencil; e += THREADS) {
-        const int n = e / kPencil, w = e % kPencil;
-        sm[w * LP + n] = base[(int64_t)n * pg.ls + w];
+    float2 *base = data + outer * pg.os + mid * pg.ms + kzp * W + w;
+    const int ls = (int)pg.ls;  // offsets within one pencil fit in 32 bits (n * ls < 2^31)
+    {
+        const int n1 = r;
+        float2 v[M2];
+#pragma unroll
+        for (int n2 = 0; n2 < M2; ++n2) v[n2] = base[(n1 + M1 * n2) * ls];
+        reg_fft<M2, INV>(v);
+#pragma unroll
+        for (int k2 = 0; k2 < M2; ++k2) {
+            float2 t = __ldg(tw + n1 * k2 * (1024 / L));
+            if (INV) t.y = -t.y;
+            ys[n1 * YP + k2 * W + w] = cmul(v[bitrev(k2, ilog2(M2))], t);
+        }
     }
     __syncthreads();
-    line_fft<L, INV>(sm + line * LP, t, tw);
-    __syncthreads();
-    for (int e = tid; e < L * kPencil; e += THREADS) {
-        const int n = e / kPencil, w = e % kPencil;
-        base[(int64_t)n * pg.ls + w] = sm[w * LP + n];
+    const int k2 = r;
+    if (k2 < M2) {
+        float2 u[M1];
+#pragma unroll
+        for (int n1 = 0; n1 < M1; ++n1) u[n1] = ys[n1 * YP + k2 * W + w];
+        reg_fft<M1, INV>(u);
+#pragma unroll
+        for (int k1 = 0; k1 < M1; ++k1) base[(k2 + M2 * k1) * ls] = u[bitrev(k1, ilog2(M1))];
     }
 }
 
@@ -269,11 +323,11 @@ cudaError_t z_inv_n(const float2 *spec, float *out, const FftGeom &fg, cudaStrea
 
 template <int L, bool INV>
 cudaError_t pencil_n(float2 *data, const PencilGeom &pg, int64_t blocks, const float2 *tw, cudaStream_t st) {
-    constexpr int TL = split1(L);
-    const size_t smem = sizeof(float2) * kPencil * line_pitch(L);
+    using S = PencilShape<L>;
+    const size_t smem = sizeof(float2) * S::SMEM;
     cudaError_t e = cudaFuncSetAttribute(k_fft_pencil<L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fft_pencil<L, INV><<<(unsigned)blocks, kPencil * TL, smem, st>>>(data, pg, tw);
+    k_fft_pencil<L, INV><<<(unsigned)blocks, S::THREADS, smem, st>>>(data, pg, tw);
     return cudaGetLastError();
 }
 

@@ -176,6 +176,10 @@ class ParticleMesh:
         self._call("pm_power_spectrum", _ptr(s), _pmgb._dptr(k), _pmgb._dptr(pk), _pmgb._dptr(nm))
         return k, pk, nm
 
+    def use_graphs(self, enable=True):
+        """Replay pm_integrate / pm_adjoint_integrate from captured CUDA graphs."""
+        self._call("pm_use_graphs", int(bool(enable)))
+
     def launch_count(self):
         return int(self._lib.pm_launch_count(self._ctx))
 
