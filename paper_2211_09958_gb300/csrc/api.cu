@@ -261,10 +261,10 @@ Spec mesh_spec(pm_ctx *ctx) {
     const int n = ctx->P.n_m;
     if (ctx->own) {
         const int64_t per = (int64_t)n * n * ctx->fg.zc;
-        return Spec{ctx->spec, per * ctx->P.n_batch, per, n, ctx->P.n_batch, kf, ctx->fg.zc};
+        return Spec{ctx->spec, per * ctx->P.n_batch, per, n, ctx->P.n_batch, kf, ctx->fg.zc, 1};
     }
     const int64_t modes = ctx->mesh_pad / 2;
-    return Spec{reinterpret_cast<float2 *>(ctx->mesh), modes * ctx->P.n_batch, modes, n, ctx->P.n_batch, kf, n / 2 + 1};
+    return Spec{reinterpret_cast<float2 *>(ctx->mesh), modes * ctx->P.n_batch, modes, n, ctx->P.n_batch, kf, n / 2 + 1, 0};
 }
 
 MeshRef lat_ref(pm_ctx *ctx) {
@@ -274,7 +274,7 @@ MeshRef lat_ref(pm_ctx *ctx) {
 Spec lat_spec(pm_ctx *ctx) {
     const int64_t modes = ctx->lat_pad / 2;
     return Spec{reinterpret_cast<float2 *>(ctx->lat), modes * ctx->P.n_batch, modes, ctx->P.n_p, ctx->P.n_batch,
-                (float)(2.0 * M_PI / ctx->P.box), ctx->P.n_p / 2 + 1};
+                (float)(2.0 * M_PI / ctx->P.box), ctx->P.n_p / 2 + 1, 0};
 }
 
 float *lat_field(pm_ctx *ctx, int f) { return ctx->lat + (int64_t)f * ctx->lat_pad * ctx->P.n_batch; }
@@ -987,11 +987,10 @@ int pm_mesh_rfft(pm_ctx *ctx, const float *real, float *spec) {
     PM_TRY(check_ptr(ctx, spec, "spec"));
     DeviceGuard guard(ctx->device);
     const int n = ctx->P.n_m, B = ctx->P.n_batch;
-    const size_t row = sizeof(float2) * (n / 2 + 1);
     if (ctx->own) {
         PM_TRY(own_forward(ctx, real, 1));
-        PM_CUDA(ctx, cudaMemcpy2DAsync(spec, row, ctx->spec, sizeof(float2) * ctx->fg.zc, row, (size_t)B * n * n,
-                                       cudaMemcpyDeviceToDevice, ctx->stream));
+        PM_LAUNCH(ctx, "spec_copy", launch_spec_copy(ctx->spec, reinterpret_cast<float2 *>(spec), ctx->fg, true,
+                                                     ctx->stream));
         return PM_OK;
     }
     const int zs = 2 * (n / 2 + 1);
@@ -1009,10 +1008,9 @@ int pm_mesh_irfft(pm_ctx *ctx, const float *spec, float *real) {
     PM_TRY(check_ptr(ctx, real, "real"));
     DeviceGuard guard(ctx->device);
     const int n = ctx->P.n_m, B = ctx->P.n_batch;
-    const size_t row = sizeof(float2) * (n / 2 + 1);
     if (ctx->own) {
-        PM_CUDA(ctx, cudaMemcpy2DAsync(ctx->spec, sizeof(float2) * ctx->fg.zc, spec, row, row, (size_t)B * n * n,
-                                       cudaMemcpyDeviceToDevice, ctx->stream));
+        PM_LAUNCH(ctx, "spec_copy", launch_spec_copy(ctx->spec, reinterpret_cast<float2 *>(const_cast<float *>(spec)),
+                                                     ctx->fg, false, ctx->stream));
         return own_inverse(ctx, real, 1);
     }
     const int zs = 2 * (n / 2 + 1);

@@ -3,14 +3,15 @@
 //
 //   real meshes     [run][x][y][z][G] floats, G = 1 (density) or 4
 //                   (interleaved adjoint sources / force components)
-//   spectra         [field][run][x][y][zc] complex, kz = 0 .. n/2 valid,
-//                   row pitch zc = n/2 + 1 rounded up to 8 (pad kept at 0)
+//   spectra         [field][run][kz / 8][x][y][kz % 8] complex ("blocked":
+//                   8 consecutive kz per 64-byte block), kz = 0 .. n/2 valid
+//                   out of zc = n/2 + 1 rounded up to 8 (pad kept at 0)
 //
 //   z pass  (R2C / C2R)  rows of n reals as n/2-point complex FFTs with the
 //                        even/odd packing; reads or writes the interleaved
 //                        real mesh and the spectrum rows
-//   pencil  (y and x)    8 adjacent kz columns (64 contiguous bytes per
-//                        row) transformed along y or x
+//   pencil  (y and x)    one kz block transformed along y (a contiguous
+//                        64 KB slab at n = 1024) or x (rows 64 KB apart)
 //
 // Conventions match cuFFT's unnormalised R2C / C2R: forward
 // X_k = sum_n x_n e^{-2 pi i k n / n}, inverse without 1/n.  The spectral
@@ -172,18 +173,22 @@ __global__ void __launch_bounds__(256) k_fft_z_fwd(const float *__restrict__ in,
         line_fft_regs<M, false>(v, sm + line * LP, t, fg.tw);
     }
     const float2 *Lz = sm + line * LP;
-    float2 *dst = spec + g * fg.fstride + (bx * N + y0 + yl) * (int64_t)fg.zc;
+    // element kz of this row sits at dst + (kz / 8) * N^2 * 8 + kz % 8
+    const int64_t run = bx / N, xx = bx % N;
+    float2 *dst = spec + g * fg.fstride + (run * (fg.zc / 8) * N * N + xx * N + y0 + yl) * 8;
+    constexpr int64_t KB = (int64_t)N * N * 8;
+    auto at = [&](int kz) -> float2 & { return dst[(kz >> 3) * KB + (kz & 7)]; };
     for (int k = t; k <= M / 2; k += TL) {
         const float2 zk = Lz[k], zm = Lz[(M - k) & (M - 1)];
         const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
         const float2 WO = cmul(__ldg(fg.tw + k * (1024 / N)), O);
-        dst[k] = cadd(E, WO);
+        at(k) = cadd(E, WO);
         const float2 r = csub(E, WO);
         if (k == 0)
-            dst[M] = make_float2(r.x, -r.y);
+            at(M) = make_float2(r.x, -r.y);
         else if (k < M / 2)
-            dst[M - k] = make_float2(r.x, -r.y);
+            at(M - k) = make_float2(r.x, -r.y);
     }
 }
 
@@ -208,11 +213,13 @@ __global__ void __launch_bounds__(256) k_fft_z_inv(const float2 *__restrict__ sp
         constexpr int M1 = split1(M), M2 = M / M1;
         float2 v[M2];
         if (g < GS) {
-            const float2 *src = spec + g * fg.fstride + (bx * N + y0 + yl) * (int64_t)fg.zc;
+            const int64_t run = bx / N, xx = bx % N;
+            const float2 *src = spec + g * fg.fstride + (run * (fg.zc / 8) * N * N + xx * N + y0 + yl) * 8;
+            constexpr int64_t KB = (int64_t)N * N * 8;
 #pragma unroll
             for (int n2 = 0; n2 < M2; ++n2) {
-                const int k = t + M1 * n2;
-                float2 xk = __ldg(src + k), xm = __ldg(src + (M - k));
+                const int k = t + M1 * n2, km = M - k;
+                float2 xk = __ldg(src + (k >> 3) * KB + (k & 7)), xm = __ldg(src + (km >> 3) * KB + (km & 7));
                 if (k == 0) {
                     xk.y = 0.f;
                     xm.y = 0.f;
@@ -269,9 +276,8 @@ __global__ void __launch_bounds__(PencilShape<L>::THREADS, 2) k_fft_pencil(float
     float2 *ys = reinterpret_cast<float2 *>(smraw);
     const int tid = threadIdx.x, w = tid % W, r = tid / W;
     const int64_t p = blockIdx.x;
-    const int64_t kzp = p % pg.nkz, rest = p / pg.nkz;
-    const int64_t mid = rest % pg.nmid, outer = rest / pg.nmid;
-    float2 *base = data + outer * pg.os + mid * pg.ms + kzp * W + w;
+    const int64_t mid = p % pg.nmid, outer = p / pg.nmid;
+    float2 *base = data + outer * pg.os + mid * pg.ms + w;
     const int ls = (int)pg.ls;  // offsets within one pencil fit in 32 bits (n * ls < 2^31)
     {
         const int n1 = r;
@@ -373,7 +379,31 @@ cudaError_t pencil_l(float2 *data, const PencilGeom &pg, int n, int64_t blocks, 
     }
 }
 
+// Copy between the blocked spectrum (field 0) and a plain
+// [run][x][y][n/2 + 1] half spectrum.
+__global__ void k_spec_copy(float2 *blocked, float2 *plain, FftGeom fg, bool to_plain) {
+    const int n = fg.n, h = n / 2 + 1;
+    const int64_t total = (int64_t)fg.nb * n * n * h;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int kz = (int)(i % h);
+        const int64_t row = i / h;  // (run * n + x) * n + y
+        const int64_t run = row / ((int64_t)n * n), xy = row % ((int64_t)n * n);
+        const int64_t b = ((run * (fg.zc / 8) + kz / 8) * n * n + xy) * 8 + kz % 8;
+        if (to_plain)
+            plain[i] = blocked[b];
+        else
+            blocked[b] = plain[i];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_spec_copy(float2 *blocked, float2 *plain, const FftGeom &fg, bool to_plain, cudaStream_t st) {
+    const int64_t total = (int64_t)fg.nb * fg.n * fg.n * (fg.n / 2 + 1);
+    const int64_t blocks = (total + 255) / 256;
+    k_spec_copy<<<(unsigned)(blocks < 152 * 32 ? blocks : 152 * 32), 256, 0, st>>>(blocked, plain, fg, to_plain);
+    return cudaGetLastError();
+}
 
 bool own_fft_supported(int n) { return n >= 16 && n <= 1024 && (n & (n - 1)) == 0; }
 
@@ -403,27 +433,24 @@ cudaError_t launch_fft_z_inv(int gs, const float2 *spec, float *out, const FftGe
 }
 
 // Transform fields [f0, f0 + nf) of the spectrum along y (axis 1) or x
-// (axis 0), forward or inverse.
+// (axis 0), forward or inverse.  One pencil per (field, run, kz block) and
+// x (y pass) or y (x pass); consecutive blocks take neighbouring pencils.
 cudaError_t launch_fft_pencils(int axis, bool inverse, float2 *spec, int f0, int nf, const FftGeom &fg,
                                cudaStream_t st) {
     const int n = fg.n;
     PencilGeom pg{};
-    pg.nkz = fg.zc / kPencil;
+    pg.nkz = 1;
+    pg.nmid = n;
+    pg.os = (int64_t)n * n * kPencil;
     float2 *base = spec + f0 * fg.fstride;
-    int64_t blocks;
-    if (axis == 1) {  // lines along y: one pencil per (field, run, x, kz block)
-        pg.ls = fg.zc;
-        pg.nmid = 1;
-        pg.os = (int64_t)n * fg.zc;
-        pg.ms = 0;
-        blocks = (int64_t)nf * fg.nb * n * pg.nkz;
-    } else {  // lines along x: one pencil per (field, run, y, kz block)
-        pg.ls = (int64_t)n * fg.zc;
-        pg.nmid = n;
-        pg.ms = fg.zc;
-        pg.os = (int64_t)n * n * fg.zc;
-        blocks = (int64_t)nf * fg.nb * n * pg.nkz;
+    if (axis == 1) {  // lines along y: a contiguous n x 8 slab
+        pg.ls = kPencil;
+        pg.ms = (int64_t)n * kPencil;
+    } else {          // lines along x: rows n * 8 complex apart
+        pg.ls = (int64_t)n * kPencil;
+        pg.ms = kPencil;
     }
+    const int64_t blocks = (int64_t)nf * fg.nb * (fg.zc / kPencil) * n;
     return inverse ? pencil_l<true>(base, pg, n, blocks, fg.tw, st) : pencil_l<false>(base, pg, n, blocks, fg.tw, st);
 }
 

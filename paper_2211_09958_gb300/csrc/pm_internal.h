@@ -122,18 +122,20 @@ cudaError_t launch_mse(MeshRef mesh, const float *target, int n, int nb, double 
 cudaError_t launch_kick(const Geom &g, float *p, const float *f, const float4 *table, int step, int sel,
                         float sign, cudaStream_t st);
 
-// Spectral kernels over an rfft grid n x n x (n/2+1) stored with row pitch
-// zc >= n/2+1 (complex elements); field f of batch b starts at
-// c + f*fstride + b*bstride (complex elements).
+// Spectral kernels over an rfft grid n x n x (n/2+1) (complex elements);
+// field f of batch b starts at c + f*fstride + b*bstride.  blk = 0: rows
+// [x][y][zc] with zc >= n/2+1; blk = 1: the own FFT's blocked layout
+// [kz/8][x][y][kz%8] with zc/8 blocks.
 struct Spec {
     float2 *c;
     int64_t fstride, bstride;
     int n, nb;
     float kf;  // 2 pi / box
     int zc;
+    int blk;
 };
 
-// The library's own FFT (fft_kernels.cu): spectra [field][run][x][y][zc].
+// The library's own FFT (fft_kernels.cu): spectra [field][run][kz/8][x][y][kz%8].
 struct FftGeom {
     int n, nb, zc;
     int64_t fstride;    // complex elements per spectrum field (all runs)
@@ -152,6 +154,7 @@ cudaError_t launch_fft_z_fwd(int g, const float *in, float2 *spec, const FftGeom
 cudaError_t launch_fft_z_inv(int gs, const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st);
 cudaError_t launch_fft_pencils(int axis, bool inverse, float2 *spec, int f0, int nf, const FftGeom &fg,
                                cudaStream_t st);
+cudaError_t launch_spec_copy(float2 *blocked, float2 *plain, const FftGeom &fg, bool to_plain, cudaStream_t st);
 
 enum SpecMode { SPEC_FORCE = 0, SPEC_ADJ = 1 };
 cudaError_t launch_spectral(int mode, const Spec &sp, const float *pref, cudaStream_t st);

@@ -22,7 +22,16 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ void mode_ijk(int64_t m, int n, int zc, int &ix, int &iy, int &iz) {
+__device__ __forceinline__ void mode_ijk(int64_t m, int n, int zc, int blk, int &ix, int &iy, int &iz) {
+    if (blk) {  // [kz/8][x][y][kz%8]
+        const int j = (int)(m & 7);
+        int64_t r = m >> 3;
+        iy = (int)(r % n);
+        r /= n;
+        ix = (int)(r % n);
+        iz = (int)(r / n) * 8 + j;
+        return;
+    }
     const int64_t r = m / zc;
     iz = (int)(m - r * zc);
     const int64_t x = r / n;
@@ -41,7 +50,7 @@ __global__ void __launch_bounds__(kThreads) k_spec_force(Spec sp, const float *p
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
-    mode_ijk(m, n, sp.zc, ix, iy, iz);
+    mode_ijk(m, n, sp.zc, sp.blk, ix, iy, iz);
     if (iz > n / 2) return;
     const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
     const float k2 = kx * kx + ky * ky + kz * kz;
@@ -64,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_spec_adj(Spec sp, const float *pre
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
-    mode_ijk(m, n, sp.zc, ix, iy, iz);
+    mode_ijk(m, n, sp.zc, sp.blk, ix, iy, iz);
     if (iz > n / 2) return;
     const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
     const float k2 = kx * kx + ky * ky + kz * kz;
@@ -92,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_power_bins(Spec sp, double *acc, i
     const float2 *c0 = sp.c + (int64_t)b * sp.bstride;
     for (int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x; m < nmodes; m += (int64_t)gridDim.x * kThreads) {
         int ix, iy, iz;
-        mode_ijk(m, n, sp.zc, ix, iy, iz);
+        mode_ijk(m, n, sp.zc, sp.blk, ix, iy, iz);
         if (iz > n / 2) continue;
         const int nx = signed_index(ix, n), ny = signed_index(iy, n);
         const int64_t n2 = (int64_t)nx * nx + (int64_t)ny * ny + (int64_t)iz * iz;
@@ -192,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_lpt_linear(Spec sp, const LinParam
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
-    mode_ijk(m, n, sp.zc, ix, iy, iz);
+    mode_ijk(m, n, sp.zc, sp.blk, ix, iy, iz);
     if (iz > n / 2) return;
     const double kx = sp.kf * (double)signed_index(ix, n), ky = sp.kf * (double)signed_index(iy, n),
                  kz = sp.kf * (double)iz;
@@ -244,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) k_lpt_second(Spec sp, int f_src, int
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
-    mode_ijk(m, n, sp.zc, ix, iy, iz);
+    mode_ijk(m, n, sp.zc, sp.blk, ix, iy, iz);
     if (iz > n / 2) return;
     const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
     const float k2 = kx * kx + ky * ky + kz * kz;
@@ -265,7 +274,7 @@ __global__ void __launch_bounds__(kThreads) k_lpt_adj_second(Spec sp, int f_in, 
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
-    mode_ijk(m, n, sp.zc, ix, iy, iz);
+    mode_ijk(m, n, sp.zc, sp.blk, ix, iy, iz);
     if (iz > n / 2) return;
     const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
     const float k2 = kx * kx + ky * ky + kz * kz;
@@ -364,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) k_lpt_adj_final(Spec sp, const LinPa
     const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     double r0 = 0.0, r1 = 0.0;
     int ix = 0, iy = 0, iz = 0;
-    if (m < nmodes) mode_ijk(m, n, sp.zc, ix, iy, iz);
+    if (m < nmodes) mode_ijk(m, n, sp.zc, sp.blk, ix, iy, iz);
     if (m < nmodes && iz <= n / 2) {
         const double kx = sp.kf * (double)signed_index(ix, n), ky = sp.kf * (double)signed_index(iy, n),
                      kz = sp.kf * (double)iz;

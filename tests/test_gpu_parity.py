@@ -308,14 +308,15 @@ def test_graph_replay_matches_direct_launches():
     s0, p0 = pm.init_lpt(_cuda(inputs.white_noise(n_p, 8))[None])
     s, p = s0.clone(), p0.clone()
     f = pm.new_particles()
-    lam, mu = torch.ones_like(s), torch.zeros_like(p)
+    lam0 = _cuda(np.random.default_rng(9).standard_normal((n_p ** 3, 3)))[None]
+    lam, mu = lam0.clone(), torch.zeros_like(p)
 
     def run():
         s.copy_(s0)
         p.copy_(p0)
         pm.integrate(s, p, f=f)
         fwd = s.clone()
-        lam.fill_(1.0)
+        lam.copy_(lam0)
         mu.zero_()
         dom = pm.adjoint_integrate(s, p, f, lam, mu)
         return fwd, lam.clone(), dom[0]
