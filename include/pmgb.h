@@ -218,6 +218,37 @@ int pm_power_spectrum(pm_ctx *ctx, const float *s, double *k_mean,
  *   amp   [n_batch][2]  P(k) amplitude A and d ln A / dOm      (may be NULL) */
 int pm_host_coefficients(const pm_config *cfg, double *kdk, double *dkdk, double *lpt, double *amp);
 
+/* Learned force correction (requires a power-of-two n_m).  The paper names
+ * a learned optimisation of the PM gravity solver as ongoing work (Statement
+ * of Need) without describing it; this library's network is a per-cell MLP
+ * on the coarse CIC density: features asinh(delta) at the cell and its 26
+ * periodic neighbours plus the scale factor a (32 inputs), layers
+ * 32 -> 128 -> 128 -> 3 with ReLU, BF16 weights and activations on tensor
+ * cores with FP32 accumulation; the output times 3/2 Om h (h = cell size) is
+ * added to the force meshes before the CIC read.  Parameters are one flat
+ * FP32 vector [W1 32x128, b1 128, W2 128x128, b2 128, W3 128x3, b3 3]
+ * (row-major, inputs first) of pm_nn_param_count() values.
+ *
+ * pm_nn_set_params   upload theta (host), reset the Adam moments
+ * pm_nn_get_params   download theta and/or the last gradient (host; NULL skips)
+ * pm_nn_enable       apply the correction in pm_integrate and pm_kdk_step at
+ *                    each evaluation's scale factor (pm_force stays the plain
+ *                    PM force; pm_adjoint_integrate refuses with PM_ESTATE)
+ * pm_nn_predict      dF device [n_batch][n_p^3][3]: the correction read at
+ *                    the particles s for scale factor a
+ * pm_nn_train_step   force matching at particles s: loss = mean over
+ *                    particles of |pm_nn_predict - target|^2 (target device,
+ *                    same layout), gradient into the context, then one Adam
+ *                    step (lr, beta 0.9 / 0.999, eps 1e-8, bias correction for
+ *                    step >= 1) when apply != 0; loss host, may be NULL. */
+int pm_nn_param_count(void);
+int pm_nn_set_params(pm_ctx *ctx, const float *theta);
+int pm_nn_get_params(pm_ctx *ctx, float *theta, float *grad);
+int pm_nn_enable(pm_ctx *ctx, int enable);
+int pm_nn_predict(pm_ctx *ctx, const float *s, double a, float *dF);
+int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a, double lr, int64_t step,
+                     int apply, double *loss);
+
 /* Device-kernel launch counter since pm_create (for benchmarking). */
 int64_t pm_launch_count(const pm_ctx *ctx);
 

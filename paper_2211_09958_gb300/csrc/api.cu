@@ -72,6 +72,13 @@ struct pm_ctx {
         int64_t launches;
     };
     std::vector<GraphEntry> graphs;
+    // learned force correction (own-FFT meshes only)
+    bool nn_on = false;
+    void *nn_packed = nullptr;
+    NNWeightsMut nnw{};
+    float *nn_theta = nullptr, *nn_grad = nullptr, *nn_m = nullptr, *nn_v = nullptr, *nn_part = nullptr;
+    __nv_bfloat16 *nn_act = nullptr;
+    double *nn_loss = nullptr;
 };
 
 namespace {
@@ -363,7 +370,9 @@ int own_inverse(pm_ctx *ctx, float *real, int g) {
 // multiply and inverse transforms; leaves F_x, F_y, F_z (and psi for the
 // adjoint) in the scratch fields.  mu != NULL selects the 4-field adjoint
 // paint.
-int force_meshes(pm_ctx *ctx, const float *s, const float *mu) {
+int apply_correction(pm_ctx *ctx, double a);
+
+int force_meshes(pm_ctx *ctx, const float *s, const float *mu, double a = -1.0) {
     const bool adj = mu != nullptr;
     const int nf = adj ? 4 : 1;
     const int mode = adj ? PAINT_ADJ : PAINT_DENSITY;
@@ -377,7 +386,9 @@ int force_meshes(pm_ctx *ctx, const float *s, const float *mu) {
         PM_TRY(own_forward(ctx, real, nf));
         PM_LAUNCH(ctx, (adj ? "spectral_adj" : "spectral_force"),
                   launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream));
-        return own_inverse(ctx, ctx->r4, adj ? 4 : 3);
+        PM_TRY(own_inverse(ctx, ctx->r4, adj ? 4 : 3));
+        if (!adj && ctx->nn_on && a > 0.0) PM_TRY(apply_correction(ctx, a));
+        return PM_OK;
     }
     PM_MEMSET(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * ctx->P.n_batch * nf, ctx->stream));
     PM_LAUNCH(ctx, paint_kind(mode), launch_paint(mode, pa, ctx->stream));
@@ -440,6 +451,10 @@ int run_graphed(pm_ctx *ctx, int kind, int b, int e, const void *q0, const void 
     return PM_OK;
 }
 
+double a_of(pm_ctx *ctx, int n) {
+    return ctx->P.a_init + (ctx->P.a_final - ctx->P.a_init) * n / ctx->P.n_steps;
+}
+
 int check_ptr(pm_ctx *ctx, const void *p, const char *name) {
     if (!p) return fail(ctx, PM_EINVAL, std::string(name) + " must not be NULL");
     if ((uintptr_t)p % 4) return fail(ctx, PM_EINVAL, std::string(name) + " must be 4-byte aligned");
@@ -470,6 +485,79 @@ int lpt_forward_fields(pm_ctx *ctx, const float *noise, uint64_t seed) {
     PM_TRY(lat_r2c(ctx, 9, 1));
     PM_LAUNCH(ctx, "lpt_second", launch_lpt_second(lat_spec(ctx), 9, 10, -1.f, ctx->stream));
     PM_TRY(lat_c2r(ctx, 10, 3));
+    return PM_OK;
+}
+
+// ---------------------------------------------------- learned correction --
+
+int64_t nn_cells(pm_ctx *ctx) { return (int64_t)ctx->P.n_batch * ctx->P.n_m * ctx->P.n_m * ctx->P.n_m; }
+
+int ensure_nn(pm_ctx *ctx) {
+    if (ctx->nn_theta) return PM_OK;
+    if (!ctx->own) return fail(ctx, PM_ESTATE, "the learned correction needs a power-of-two mesh (own FFT path)");
+    const int np = nn_param_count();
+    const int64_t cells = nn_cells(ctx);
+    const int64_t parts = ctx->g.npart * ctx->P.n_batch;
+    const size_t act = (size_t)cells * (NN_IN + 4 * NN_HID + 8);
+    if (cudaMalloc(&ctx->nn_theta, sizeof(float) * np) != cudaSuccess ||
+        cudaMalloc(&ctx->nn_grad, sizeof(float) * np) != cudaSuccess ||
+        cudaMalloc(&ctx->nn_m, sizeof(float) * np) != cudaSuccess ||
+        cudaMalloc(&ctx->nn_v, sizeof(float) * np) != cudaSuccess ||
+        cudaMalloc(&ctx->nn_packed, nn_packed_bytes()) != cudaSuccess ||
+        cudaMalloc(&ctx->nn_act, sizeof(__nv_bfloat16) * act) != cudaSuccess ||
+        cudaMalloc(&ctx->nn_part, sizeof(float) * 3 * parts) != cudaSuccess ||
+        cudaMalloc(&ctx->nn_loss, sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, PM_ENOMEM, "cannot allocate the learned-correction buffers");
+    }
+    ctx->nnw = nn_carve(ctx->nn_packed);
+    PM_CUDA(ctx, nn_prepare());
+    return PM_OK;
+}
+
+NNArgs nn_args(pm_ctx *ctx, double a) {
+    NNArgs na{};
+    na.w = NNWeights{ctx->nnw.w1t, ctx->nnw.w2t, ctx->nnw.w2n, ctx->nnw.w3t, ctx->nnw.w3n,
+                     ctx->nnw.b1, ctx->nnw.b2, ctx->nnw.b3};
+    na.n = ctx->P.n_m;
+    na.rho = ctx->r1;
+    na.afeat = (float)a;
+    na.pref = ctx->d_pref;
+    na.s_scale = (float)((double)ctx->P.n_m * ctx->P.n_m * ctx->P.box);
+    na.out = ctx->r4;
+    const int64_t cells = nn_cells(ctx);
+    na.xg = ctx->nn_act;
+    na.h1g = na.xg + cells * NN_IN;
+    na.h2g = na.h1g + cells * NN_HID;
+    na.g1g = na.h2g + cells * NN_HID;
+    na.g2g = na.g1g + cells * NN_HID;
+    na.g3g = na.g2g + cells * NN_HID;
+    na.grad = ctx->nn_grad;
+    na.gb1 = ctx->nn_grad + NN_IN * NN_HID;
+    na.gb2 = na.gb1 + NN_HID + NN_HID * NN_HID;
+    na.gb3 = na.gb2 + NN_HID + NN_HID * NN_OUT;
+    return na;
+}
+
+// Add the network's correction to the force meshes (r4) from the density in
+// r1 at scale factor a.
+int apply_correction(pm_ctx *ctx, double a) {
+    NNArgs na = nn_args(ctx, a);
+    na.accumulate = 1;
+    PM_LAUNCH(ctx, "nn_fwd", launch_nn_fwd(na, nn_cells(ctx), false, ctx->stream));
+    return PM_OK;
+}
+
+// Paint the density of s into r1 and evaluate the network into r4 (slots
+// 0..2 overwritten); train = also keep the activations.
+int nn_forward_at(pm_ctx *ctx, const float *s, double a, bool train) {
+    const MeshRef dref = density_ref(ctx);
+    PM_MEMSET(ctx, cudaMemsetAsync(dref.ptr, 0, sizeof(float) * density_floats(ctx), ctx->stream));
+    PaintArgs pa = paint_args(ctx, s);
+    pa.mesh = dref;
+    PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
+    NNArgs na = nn_args(ctx, a);
+    PM_LAUNCH(ctx, train ? "nn_fwd_train" : "nn_fwd", launch_nn_fwd(na, nn_cells(ctx), train, ctx->stream));
     return PM_OK;
 }
 
@@ -643,6 +731,9 @@ int pm_destroy(pm_ctx *ctx) {
     }
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    for (void *p : {(void *)ctx->nn_packed, (void *)ctx->nn_theta, (void *)ctx->nn_grad, (void *)ctx->nn_m,
+                    (void *)ctx->nn_v, (void *)ctx->nn_part, (void *)ctx->nn_act, (void *)ctx->nn_loss})
+        if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->spec, (void *)ctx->tw}) 
         if (p) cudaFree(p);
@@ -750,7 +841,7 @@ int pm_kdk_step(pm_ctx *ctx, int32_t step, float *s, float *p, float *f) {
     pr.f = f;
     pr.step = step;
     PM_LAUNCH(ctx, "pre_kick_drift", launch_pre(PRE_KICK_DRIFT, pr, ctx->stream));
-    PM_TRY(force_meshes(ctx, s, nullptr));
+    PM_TRY(force_meshes(ctx, s, nullptr, a_of(ctx, step + 1)));
     ReadArgs ra = read_args(ctx, s);
     ra.p = p;
     ra.f = f;
@@ -772,13 +863,13 @@ int pm_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, fl
         ra.p = p;
         ra.f = f;
         for (int n = step_begin; n < step_end; ++n) {
-            PM_TRY(force_meshes(ctx, s, nullptr));
+            PM_TRY(force_meshes(ctx, s, nullptr, a_of(ctx, n)));
             ra.kick_step = n;
             ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
             ra.drift_step = n;
             PM_TRY(read_forces(ctx, READ_KICK_DRIFT, ra));
         }
-        PM_TRY(force_meshes(ctx, s, nullptr));
+        PM_TRY(force_meshes(ctx, s, nullptr, a_of(ctx, step_end)));
         ra.kick_step = step_end - 1;
         ra.kick_sel = KICK_B;
         ra.drift_step = -1;
@@ -800,6 +891,7 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
     PM_TRY(check_ptr(ctx, mu, "mu"));
     if (step_begin < 0 || step_end > ctx->P.n_steps || step_begin >= step_end)
         return fail(ctx, PM_EINVAL, "need 0 <= step_begin < step_end <= n_steps");
+    if (ctx->nn_on) return fail(ctx, PM_ESTATE, "the learned correction has no reverse-time adjoint; disable it first");
     DeviceGuard guard(ctx->device);
     const int N = ctx->P.n_steps, B = ctx->P.n_batch;
     const int last = step_end - 1;
@@ -1053,6 +1145,98 @@ int pm_power_spectrum(pm_ctx *ctx, const float *s, double *k_mean, double *power
             k_mean[(size_t)b * nb + i] = a[1] / cnt * (2.0 * M_PI / ctx->P.box);
             power[(size_t)b * nb + i] = vol / n6 * a[2] / cnt;
         }
+    return PM_OK;
+}
+
+int pm_nn_param_count(void) { return nn_param_count(); }
+
+int pm_nn_set_params(pm_ctx *ctx, const float *theta) {
+    if (!ctx || !theta) return fail(ctx, PM_EINVAL, "ctx and theta must not be NULL");
+    DeviceGuard guard(ctx->device);
+    PM_TRY(ensure_nn(ctx));
+    const int np = nn_param_count();
+    PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    PM_CUDA(ctx, cudaMemcpy(ctx->nn_theta, theta, sizeof(float) * np, cudaMemcpyHostToDevice));
+    for (float *p : {ctx->nn_grad, ctx->nn_m, ctx->nn_v}) PM_CUDA(ctx, cudaMemset(p, 0, sizeof(float) * np));
+    PM_LAUNCH(ctx, "nn_pack", launch_nn_pack(ctx->nn_theta, ctx->nnw, ctx->stream));
+    return PM_OK;
+}
+
+int pm_nn_get_params(pm_ctx *ctx, float *theta, float *grad) {
+    if (!ctx || (!theta && !grad)) return fail(ctx, PM_EINVAL, "nothing to copy");
+    if (!ctx->nn_theta) return fail(ctx, PM_ESTATE, "no network parameters set");
+    DeviceGuard guard(ctx->device);
+    const int np = nn_param_count();
+    PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (theta) PM_CUDA(ctx, cudaMemcpy(theta, ctx->nn_theta, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    if (grad) PM_CUDA(ctx, cudaMemcpy(grad, ctx->nn_grad, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    return PM_OK;
+}
+
+int pm_nn_enable(pm_ctx *ctx, int enable) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    if (enable && !ctx->nn_theta) return fail(ctx, PM_ESTATE, "set the network parameters first");
+    ctx->nn_on = enable != 0;
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+    return PM_OK;
+}
+
+int pm_nn_predict(pm_ctx *ctx, const float *s, double a, float *dF) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    PM_TRY(check_ptr(ctx, dF, "dF"));
+    if (!ctx->nn_theta) return fail(ctx, PM_ESTATE, "no network parameters set");
+    DeviceGuard guard(ctx->device);
+    PM_TRY(nn_forward_at(ctx, s, a, false));
+    ReadArgs ra = read_args(ctx, const_cast<float *>(s));
+    ra.f = dF;
+    return read_forces(ctx, READ_FORCE, ra);
+}
+
+int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a, double lr, int64_t step, int apply,
+                     double *loss) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    PM_TRY(check_ptr(ctx, target, "target"));
+    if (!ctx->nn_theta) return fail(ctx, PM_ESTATE, "no network parameters set");
+    if (apply && step < 1) return fail(ctx, PM_EINVAL, "Adam step count starts at 1");
+    DeviceGuard guard(ctx->device);
+    const int np = nn_param_count();
+    const int64_t parts = ctx->g.npart * ctx->P.n_batch;
+    PM_MEMSET(ctx, cudaMemsetAsync(ctx->nn_grad, 0, sizeof(float) * np, ctx->stream));
+    PM_MEMSET(ctx, cudaMemsetAsync(ctx->nn_loss, 0, sizeof(double), ctx->stream));
+    PM_TRY(nn_forward_at(ctx, s, a, true));
+    // per-particle prediction, residual against the target, its cotangent
+    ReadArgs ra = read_args(ctx, const_cast<float *>(s));
+    ra.f = ctx->nn_part;
+    PM_TRY(read_forces(ctx, READ_FORCE, ra));
+    PM_LAUNCH(ctx, "nn_residual", launch_nn_residual(ctx->nn_part, target, 3 * parts, 1.f / (float)parts,
+                                                      ctx->nn_loss, ctx->stream));
+    // adjoint of the read: paint the cotangent into slots 1..3 of a gradient mesh
+    float *gmesh = reinterpret_cast<float *>(ctx->spec);
+    const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
+    PM_MEMSET(ctx, cudaMemsetAsync(gmesh, 0, sizeof(float) * 4 * n3 * ctx->P.n_batch, ctx->stream));
+    PaintArgs pa = paint_args(ctx, s, ctx->nn_part);
+    pa.mesh = MeshRef{gmesh, 0, 4 * n3, ctx->P.n_m, 4};
+    PM_LAUNCH(ctx, paint_kind(PAINT_ADJ), launch_paint(PAINT_ADJ, pa, ctx->stream));
+    NNArgs na = nn_args(ctx, a);
+    na.gmesh = gmesh;
+    PM_LAUNCH(ctx, "nn_bwd", launch_nn_bwd(na, nn_cells(ctx), ctx->stream));
+    if (apply) {
+        const double b1 = 0.9, b2 = 0.999;
+        const float c1 = (float)(1.0 / (1.0 - std::pow(b1, (double)step)));
+        const float c2 = (float)(1.0 / (1.0 - std::pow(b2, (double)step)));
+        PM_LAUNCH(ctx, "adam", launch_adam(ctx->nn_theta, ctx->nn_grad, ctx->nn_m, ctx->nn_v, np, (float)lr,
+                                           (float)b1, (float)b2, 1e-8f, c1, c2, ctx->stream));
+        PM_LAUNCH(ctx, "nn_pack", launch_nn_pack(ctx->nn_theta, ctx->nnw, ctx->stream));
+    }
+    if (loss) {
+        double l = 0.0;
+        PM_CUDA(ctx, cudaMemcpyAsync(&l, ctx->nn_loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        *loss = l / (double)parts;
+    }
     return PM_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 PM library (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -174,5 +175,43 @@ cudaError_t launch_lpt_adj_seed(MeshRef lat, int np, int nb, const float4 *fac, 
                                 double *red, cudaStream_t st);
 cudaError_t launch_lpt_adj_phi(MeshRef lat, int np, int nb, cudaStream_t st);
 cudaError_t launch_lpt_adj_final(const Spec &sp, const LinParams *lp, int f_noise, double *red, cudaStream_t st);
+
+// ------------------------------------------------- learned correction ---
+
+constexpr int NN_IN = 32, NN_HID = 128, NN_OUT = 3;
+
+struct NNWeights {  // packed bf16 operands and FP32 biases (learned.cu)
+    const __nv_bfloat16 *w1t, *w2t, *w2n, *w3t, *w3n;
+    const float *b1, *b2, *b3;
+};
+struct NNWeightsMut {
+    __nv_bfloat16 *w1t, *w2t, *w2n, *w3t, *w3n;
+    float *b1, *b2, *b3;
+};
+struct NNArgs {
+    NNWeights w;
+    int n;               // mesh cells per side
+    const float *rho;    // painted density [run][n^3] (alpha sum W)
+    float afeat;         // scale-factor feature
+    const float *pref;   // per run 3/2 Om / n^3; output scale = pref * s_scale
+    float s_scale;       // n^3 h, so that the output scale is 3/2 Om h
+    float *out;          // interleaved 4-slot mesh [run][n^3][4], slots 0..2
+    int accumulate;      // add to out instead of overwriting
+    __nv_bfloat16 *xg, *h1g, *h2g, *g1g, *g2g, *g3g;  // training activations
+    const float *gmesh;  // interleaved gradient mesh, slots 1..3
+    float *grad, *gb1, *gb2, *gb3;
+};
+
+int nn_param_count();
+cudaError_t nn_prepare();  // kernel attributes; call once before any capture
+size_t nn_packed_bytes();
+NNWeightsMut nn_carve(void *base);
+cudaError_t launch_nn_pack(const float *theta, const NNWeightsMut &w, cudaStream_t st);
+cudaError_t launch_nn_fwd(const NNArgs &a, int64_t cells, bool train, cudaStream_t st);
+cudaError_t launch_nn_bwd(const NNArgs &a, int64_t cells, cudaStream_t st);
+cudaError_t launch_nn_residual(float *pred, const float *target, int64_t n, float inv_total, double *loss,
+                               cudaStream_t st);
+cudaError_t launch_adam(float *theta, float *grad, float *m, float *v, int np, float lr, float b1, float b2, float eps,
+                        float c1, float c2, cudaStream_t st);
 
 }  // namespace pmgb

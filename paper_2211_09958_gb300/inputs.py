@@ -37,3 +37,15 @@ def random_displacements(n_p, box, seed, scale=0.3):
     single operations."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return (rng.standard_normal((n_p ** 3, 3)) * scale * box / n_p).astype(np.float32)
+
+
+def mlp_params(sizes, seed, bias_scale=0.1):
+    """Flat float32 parameters of a dense network with layer widths
+    ``sizes``: per layer a weight matrix [fan_in][fan_out] drawn N(0, 2 /
+    fan_in), then a bias vector drawn N(0, bias_scale^2)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for fi, fo in zip(sizes[:-1], sizes[1:]):
+        out.append(rng.standard_normal(fi * fo) * np.sqrt(2.0 / fi))
+        out.append(rng.standard_normal(fo) * bias_scale)
+    return np.concatenate(out).astype(np.float32)

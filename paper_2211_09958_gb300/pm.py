@@ -176,6 +176,43 @@ class ParticleMesh:
         self._call("pm_power_spectrum", _ptr(s), _pmgb._dptr(k), _pmgb._dptr(pk), _pmgb._dptr(nm))
         return k, pk, nm
 
+    # ------------------------------------------- learned force correction --
+    def nn_param_count(self):
+        return int(self._lib.pm_nn_param_count())
+
+    def nn_set_params(self, theta):
+        """Upload the flat FP32 parameter vector (host) and reset Adam."""
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+        if th.shape != (self.nn_param_count(),):
+            raise PMError(f"theta must have {self.nn_param_count()} values, got {th.shape}")
+        self._call("pm_nn_set_params", th.ctypes.data_as(ctypes.c_void_p))
+
+    def nn_get_params(self):
+        """(theta, last gradient) as float32 host arrays."""
+        th = np.zeros(self.nn_param_count(), np.float32)
+        g = np.zeros_like(th)
+        self._call("pm_nn_get_params", th.ctypes.data_as(ctypes.c_void_p), g.ctypes.data_as(ctypes.c_void_p))
+        return th, g
+
+    def nn_enable(self, enable=True):
+        """Add the network's correction to every force of pm_integrate / pm_kdk_step."""
+        self._call("pm_nn_enable", int(bool(enable)))
+
+    def nn_predict(self, s, a):
+        self._particles(s, "s")
+        df = self.new_particles()
+        self._call("pm_nn_predict", _ptr(s), ctypes.c_double(a), _ptr(df))
+        return df
+
+    def nn_train_step(self, s, target, a, lr=1e-3, step=1, apply=True):
+        """Force-matching loss at (s, a) against target; one Adam step when apply."""
+        self._particles(s, "s")
+        self._particles(target, "target")
+        loss = ctypes.c_double(0.0)
+        self._call("pm_nn_train_step", _ptr(s), _ptr(target), ctypes.c_double(a), ctypes.c_double(lr),
+                   ctypes.c_int64(step), int(bool(apply)), ctypes.byref(loss))
+        return loss.value
+
     def use_graphs(self, enable=True):
         """Replay pm_integrate / pm_adjoint_integrate from captured CUDA graphs."""
         self._call("pm_use_graphs", int(bool(enable)))
