@@ -18,8 +18,17 @@ displacement s = x - q and momentum p = a^3 E dx/da.
   CIC weights   W(x - c) = prod_d w(u_d - c_d), u = x / h, i0 = floor(u),
                 f = u - i0, w = 1 - f at i0 and f at i0 + 1.
   density       rho(c) = alpha sum_i W(x_i - c) - 1, alpha = (n_m / n_p)^3
-  force         F_j(k) = i k_j (3/2) Om rho(k) / k^2, zero at k = 0 and where
-                n_j is the Nyquist index; F_j(c) = IDFT; F_i = sum_c W F(c)
+  force         F_j(k) = i D_j(k) (3/2) Om rho(k) / k^2, zero at k = 0 and
+                where n_j is the Nyquist index; F_j(c) = IDFT; F_i = sum_c W F(c)
+  gradient      D_j(k) = (8 sin(k_j h) - sin(2 k_j h)) / (6 h), the 4-point
+                central difference in Fourier space [reading]: it vanishes
+                smoothly at the Nyquist frequency.  With a mesh finer than the
+                particle lattice (n_m > n_p) the perturbed lattice puts
+                density at the lattice harmonics near the mesh Nyquist; the
+                exact spectral gradient i k_j jumps there and makes the
+                linear force on a long plane wave too strong by an amount
+                linear in k (+6 % at n_m = 2 n_p, k = k_Nyquist(particles)/8),
+                while D_j keeps the error O(k^2) at every mesh ratio
   step n        p <- p + K_a F(s);  s <- s + Dr p;  p <- p + K_b F(s)
 
 Every routine below is written as the definition it implements; FFTs are
@@ -158,15 +167,23 @@ def density(s, setup):
 
 # -------------------------------------------------------------- force ----
 
+def gradient_operator(k, h):
+    """Fourier multiplier of the 4-point central difference d/dx on a mesh of
+    spacing h (times i): (8 sin(k h) - sin(2 k h)) / (6 h)."""
+    return (8.0 * np.sin(k * h) - np.sin(2.0 * k * h)) / (6.0 * h)
+
+
 def gradient_green_multipliers(n, box, omega_m):
-    """i k_j (3/2) Om / k^2 on the rfft grid, zero at k = 0 and where n_j is
-    the Nyquist index (so each inverse transform is exactly real) [reading]."""
+    """i D_j (3/2) Om / k^2 on the rfft grid (D_j the 4-point difference
+    gradient, k^2 exact), zero at k = 0 and where n_j is the Nyquist index
+    (so each inverse transform is exactly real) [reading]."""
     (kx, ky, kz), nyq = rfft_wavenumbers(n, box)
     k2 = kx ** 2 + ky ** 2 + kz ** 2
     k2s = np.where(k2 > 0, k2, 1.0)
+    h = box / n
     out = []
     for kj, mj in zip((kx, ky, kz), nyq):
-        m = 1j * kj * (1.5 * omega_m) / k2s
+        m = 1j * gradient_operator(kj, h) * (1.5 * omega_m) / k2s
         m = np.where((k2 > 0) & ~mj, m, 0.0)
         out.append(m)
     return out

@@ -38,6 +38,7 @@ struct pm_ctx {
     float *lat = nullptr;
     float4 *d_table = nullptr;
     float *d_pref = nullptr;
+    float *d_grad = nullptr;  // [n_m] difference-gradient multiplier per axis index
     float4 *d_fac = nullptr;
     LinParams *d_lin = nullptr;
     double *d_red = nullptr;
@@ -268,10 +269,11 @@ Spec mesh_spec(pm_ctx *ctx) {
     const int n = ctx->P.n_m;
     if (ctx->own) {
         const int64_t per = (int64_t)n * n * ctx->fg.zc;
-        return Spec{ctx->spec, per * ctx->P.n_batch, per, n, ctx->P.n_batch, kf, ctx->fg.zc, 1};
+        return Spec{ctx->spec, per * ctx->P.n_batch, per, n, ctx->P.n_batch, kf, ctx->fg.zc, 1, ctx->d_grad};
     }
     const int64_t modes = ctx->mesh_pad / 2;
-    return Spec{reinterpret_cast<float2 *>(ctx->mesh), modes * ctx->P.n_batch, modes, n, ctx->P.n_batch, kf, n / 2 + 1, 0};
+    return Spec{reinterpret_cast<float2 *>(ctx->mesh), modes * ctx->P.n_batch, modes, n, ctx->P.n_batch, kf, n / 2 + 1, 0,
+                ctx->d_grad};
 }
 
 MeshRef lat_ref(pm_ctx *ctx) {
@@ -683,6 +685,7 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
     }
     if (cudaMalloc(&ctx->d_table, sizeof(float4) * (size_t)c.n_steps * B) != cudaSuccess ||
         cudaMalloc(&ctx->d_pref, sizeof(float) * B) != cudaSuccess ||
+        cudaMalloc(&ctx->d_grad, sizeof(float) * ctx->P.n_m) != cudaSuccess ||
         cudaMalloc(&ctx->d_fac, sizeof(float4) * B) != cudaSuccess ||
         cudaMalloc(&ctx->d_lin, sizeof(LinParams) * B) != cudaSuccess ||
         cudaMalloc(&ctx->d_red, sizeof(double) * B * 2 * (c.n_steps + 1)) != cudaSuccess ||
@@ -691,6 +694,21 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
         cudaGetLastError();
         fail(ctx, PM_ENOMEM, "device allocation failed in pm_create");
         return bail(PM_ENOMEM);
+    }
+    {
+        // D(k) = (8 sin(k h) - sin(2 k h)) / (6 h) per axis index, k = 2 pi n_j / L
+        std::vector<float> grad(c.n_m);
+        const double h = c.box / c.n_m;
+        for (int j = 0; j < c.n_m; ++j) {
+            const int nj = j < c.n_m / 2 ? j : j - c.n_m;
+            const double kh = 2.0 * M_PI * nj / c.n_m;
+            grad[j] = 2 * j == c.n_m ? 0.f : (float)((8.0 * std::sin(kh) - std::sin(2.0 * kh)) / (6.0 * h));
+        }
+        if (cudaMemcpy(ctx->d_grad, grad.data(), sizeof(float) * c.n_m, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            fail(ctx, PM_ECUDA, "cannot upload the gradient table");
+            return bail(PM_ECUDA);
+        }
     }
     int rc = upload_tables(ctx);
     if (rc) return bail(rc);
@@ -737,7 +755,7 @@ int pm_destroy(pm_ctx *ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->spec, (void *)ctx->tw}) 
         if (p) cudaFree(p);
-    for (void *p : {(void *)ctx->mesh, (void *)ctx->lat, (void *)ctx->d_table, (void *)ctx->d_pref,
+    for (void *p : {(void *)ctx->mesh, (void *)ctx->lat, (void *)ctx->d_table, (void *)ctx->d_pref, (void *)ctx->d_grad,
                     (void *)ctx->d_fac, (void *)ctx->d_lin, (void *)ctx->d_red, (void *)ctx->d_pk,
                     (void *)ctx->d_lred, ctx->work})
         if (p) cudaFree(p);

@@ -134,6 +134,7 @@ struct Spec {
     float kf;  // 2 pi / box
     int zc;
     int blk;
+    const float *grad;  // [n] 4-point difference gradient D(k) per axis index (force kernels)
 };
 
 // The library's own FFT (fft_kernels.cu): spectra [field][run][kz/8][x][y][kz%8].

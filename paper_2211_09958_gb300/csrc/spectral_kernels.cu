@@ -8,9 +8,11 @@
 // (n/2 + 1) complex entries; wavenumber index j maps to n_j = j for
 // j < n/2 and j - n otherwise (the Nyquist index n/2 maps to -n/2 on the
 // full axes and +n/2 on the half axis).
-//   force    F_j(k) = i k_j (3/2) Om delta(k) / k^2 / n^3, zero at k = 0 and
-//            where index j is the Nyquist index (inverse transforms real)
-//   adjoint  psi(k) = sum_j conj(i k_j (3/2) Om / k^2 / n^3) u_j(k)
+//   force    F_j(k) = i D_j (3/2) Om delta(k) / k^2 / n^3, zero at k = 0;
+//            D_j = (8 sin(k_j h) - sin(2 k_j h)) / (6 h), the 4-point central
+//            difference gradient, from a per-axis table that is exactly zero
+//            at the Nyquist index (inverse transforms real)
+//   adjoint  psi(k) = sum_j conj(i D_j (3/2) Om / k^2 / n^3) u_j(k)
 //   2LPT     s1_j = i k_j / k^2 delta_L, phi_ij = k_i k_j / k^2 delta_L,
 //            s2_j = -i k_j / k^2 S, delta_L = noise(k) sqrt(P(k) / V_c)
 
@@ -57,13 +59,9 @@ __global__ void __launch_bounds__(kThreads) k_spec_force(Spec sp, const float *p
     const float g = k2 > 0.f ? pref[b] / k2 : 0.f;
     float2 *c0 = sp.c + (int64_t)b * sp.bstride + m;
     const float2 d = *c0;
-    const int h = n / 2;
-    const float2 fx = times_i(d, ix == h ? 0.f : kx * g);
-    const float2 fy = times_i(d, iy == h ? 0.f : ky * g);
-    const float2 fz = times_i(d, iz == h ? 0.f : kz * g);
-    c0[0] = fx;
-    c0[sp.fstride] = fy;
-    c0[2 * sp.fstride] = fz;
+    c0[0] = times_i(d, __ldg(sp.grad + ix) * g);
+    c0[sp.fstride] = times_i(d, __ldg(sp.grad + iy) * g);
+    c0[2 * sp.fstride] = times_i(d, __ldg(sp.grad + iz) * g);
 }
 
 __global__ void __launch_bounds__(kThreads) k_spec_adj(Spec sp, const float *pref) {
@@ -81,8 +79,7 @@ __global__ void __launch_bounds__(kThreads) k_spec_adj(Spec sp, const float *pre
     float2 *c0 = sp.c + (int64_t)b * sp.bstride + m;
     const int64_t fs = sp.fstride;
     const float2 d = c0[0], ux = c0[fs], uy = c0[2 * fs], uz = c0[3 * fs];
-    const int h = n / 2;
-    const float ax = ix == h ? 0.f : kx * g, ay = iy == h ? 0.f : ky * g, az = iz == h ? 0.f : kz * g;
+    const float ax = __ldg(sp.grad + ix) * g, ay = __ldg(sp.grad + iy) * g, az = __ldg(sp.grad + iz) * g;
     c0[0] = times_i(d, ax);
     c0[fs] = times_i(d, ay);
     c0[2 * fs] = times_i(d, az);

@@ -82,7 +82,9 @@ def test_cic_read_grad_matches_finite_difference():
 @pytest.mark.parametrize("n", [4, 6, 8])
 def test_force_mesh_against_direct_dft(n):
     # Green's function x gradient via explicit O(N^6) complex DFT sums on the
-    # full k grid, with the same k = 0 and Nyquist (index n/2) zeroing.
+    # full k grid, with the same k = 0 and Nyquist (index n/2) zeroing; the
+    # gradient is the 4-point central difference, here applied in real space
+    # to the DFT potential (so this also pins its Fourier multiplier).
     rng = np.random.default_rng(n)
     box, om = 10.0, 0.3
     st = Setup(n, n, box, pm.Cosmology(om))
@@ -97,12 +99,15 @@ def test_force_mesh_against_direct_dft(n):
     rho_k = dft @ rho.ravel()
     k2 = np.sum(kvec ** 2, axis=1)
     got = pm.force_meshes(x, st)
+    green = np.where(k2 > 0, -1.5 * om / np.where(k2 > 0, k2, 1.0), 0.0)
     for j in range(3):
-        mult = np.where((k2 > 0) & (idx[:, j] != n // 2),
-                        1j * kvec[:, j] * 1.5 * om / np.where(k2 > 0, k2, 1.0), 0.0)
-        fj = (np.conj(dft).T @ (mult * rho_k)) / n ** 3
-        assert np.max(np.abs(fj.imag)) < 1e-12
-        np.testing.assert_allclose(got[j].ravel(), fj.real, atol=1e-12)
+        # potential with the Nyquist plane of axis j removed, then
+        # F_j = -(8 (phi(c+e) - phi(c-e)) - (phi(c+2e) - phi(c-2e))) / (12 h)
+        keep = idx[:, j] != n // 2
+        phi = ((np.conj(dft).T @ (np.where(keep, green, 0.0) * rho_k)) / n ** 3).real.reshape(n, n, n)
+        sh = lambda d: np.roll(phi, -d, axis=j)
+        fj = -(8.0 * (sh(1) - sh(-1)) - (sh(2) - sh(-2))) / (12.0 * h)
+        np.testing.assert_allclose(got[j], fj, atol=1e-12)
 
 
 def _force_at(x, setup, mass_x):
@@ -130,6 +135,26 @@ def test_total_force_vanishes():
     s = rng.normal(0, 3.0, (8 ** 3, 3))
     f = pm.force(s, st)
     assert np.max(np.abs(f.sum(0))) < 1e-10 * np.abs(f).sum()
+
+
+@pytest.mark.parametrize("ratio", [1, 2, 4])
+def test_plane_wave_force_converges_at_every_mesh_ratio(ratio):
+    # F -> 3/2 Om s for a small longitudinal plane wave on the particle
+    # lattice, with an error that falls as k^2 (halving k quarters it) at
+    # every mesh-to-lattice ratio.  An exact spectral gradient i k fails
+    # this for ratio >= 2 (error linear in k, +6 % at n_m = 2 n_p, k =
+    # k_Nyquist / 8).
+    errs = []
+    for n_p in (16, 32):
+        box = 8.0 * n_p
+        st = Setup(n_p, ratio * n_p, box, pm.Cosmology(0.3))
+        q = pm.lattice(n_p, box, ratio * n_p)
+        k = 2 * np.pi / box
+        s = np.zeros_like(q)
+        s[:, 0] = 1e-4 * np.sin(k * q[:, 0])
+        f = pm.force(s, st)[:, 0]
+        errs.append(abs(f @ s[:, 0] / (s[:, 0] @ s[:, 0]) / (1.5 * 0.3) - 1.0))
+    assert errs[0] < 3e-2 and errs[1] < errs[0] / 3.0, errs
 
 
 def test_linear_force_prefactor():
