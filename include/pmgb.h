@@ -238,16 +238,18 @@ int pm_host_coefficients(const pm_config *cfg, double *kdk, double *dkdk, double
  *                    the particles s for scale factor a
  * pm_nn_train_step   force matching at particles s: loss = mean over
  *                    particles of |pm_nn_predict - target|^2 (target device,
- *                    same layout), gradient into the context, then one Adam
- *                    step (lr, beta 0.9 / 0.999, eps 1e-8, bias correction for
- *                    step >= 1) when apply != 0; loss host, may be NULL. */
+ *                    same layout), gradient of weight * loss into the context
+ *                    (weight > 0 balances samples of different force scale),
+ *                    then one Adam step (lr, beta 0.9 / 0.999, eps 1e-8, bias
+ *                    correction for step >= 1) when apply != 0; loss (host,
+ *                    unweighted) may be NULL. */
 int pm_nn_param_count(void);
 int pm_nn_set_params(pm_ctx *ctx, const float *theta);
 int pm_nn_get_params(pm_ctx *ctx, float *theta, float *grad);
 int pm_nn_enable(pm_ctx *ctx, int enable);
 int pm_nn_predict(pm_ctx *ctx, const float *s, double a, float *dF);
-int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a, double lr, int64_t step,
-                     int apply, double *loss);
+int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a, double weight, double lr,
+                     int64_t step, int apply, double *loss);
 
 /* Device-kernel launch counter since pm_create (for benchmarking). */
 int64_t pm_launch_count(const pm_ctx *ctx);

@@ -1212,13 +1212,14 @@ int pm_nn_predict(pm_ctx *ctx, const float *s, double a, float *dF) {
     return read_forces(ctx, READ_FORCE, ra);
 }
 
-int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a, double lr, int64_t step, int apply,
-                     double *loss) {
+int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a, double weight, double lr,
+                     int64_t step, int apply, double *loss) {
     if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
     PM_TRY(check_ptr(ctx, s, "s"));
     PM_TRY(check_ptr(ctx, target, "target"));
     if (!ctx->nn_theta) return fail(ctx, PM_ESTATE, "no network parameters set");
     if (apply && step < 1) return fail(ctx, PM_EINVAL, "Adam step count starts at 1");
+    if (!(weight > 0.0) || !std::isfinite(weight)) return fail(ctx, PM_EINVAL, "weight must be finite and > 0");
     DeviceGuard guard(ctx->device);
     const int np = nn_param_count();
     const int64_t parts = ctx->g.npart * ctx->P.n_batch;
@@ -1229,7 +1230,7 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
     ReadArgs ra = read_args(ctx, const_cast<float *>(s));
     ra.f = ctx->nn_part;
     PM_TRY(read_forces(ctx, READ_FORCE, ra));
-    PM_LAUNCH(ctx, "nn_residual", launch_nn_residual(ctx->nn_part, target, 3 * parts, 1.f / (float)parts,
+    PM_LAUNCH(ctx, "nn_residual", launch_nn_residual(ctx->nn_part, target, 3 * parts, (float)(weight / parts),
                                                       ctx->nn_loss, ctx->stream));
     // adjoint of the read: paint the cotangent into slots 1..3 of a gradient mesh
     float *gmesh = reinterpret_cast<float *>(ctx->spec);

@@ -394,13 +394,14 @@ __global__ void k_adam(float *theta, float *grad, float *m, float *v, int np, fl
 }
 
 // Residual of the predicted per-particle correction against the target:
-// loss += sum |pred - T|^2, pred <- 2 (pred - T) / n_total (cotangent).
-__global__ void k_nn_residual(float *pred, const float *target, int64_t n, float inv_total, double *loss) {
+// loss += sum |pred - T|^2, pred <- 2 (pred - T) * scale (cotangent of
+// weight * mean, scale = weight / n_particles).
+__global__ void k_nn_residual(float *pred, const float *target, int64_t n, float scale, double *loss) {
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float d = pred[i] - target[i];
         acc += (double)d * d;
-        pred[i] = 2.f * d * inv_total;
+        pred[i] = 2.f * d * scale;
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
@@ -489,10 +490,10 @@ cudaError_t launch_nn_bwd(const NNArgs &a, int64_t cells, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_nn_residual(float *pred, const float *target, int64_t n, float inv_total, double *loss,
+cudaError_t launch_nn_residual(float *pred, const float *target, int64_t n, float scale, double *loss,
                                cudaStream_t st) {
     const int64_t blocks = (n + 255) / 256;
-    k_nn_residual<<<(unsigned)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(pred, target, n, inv_total, loss);
+    k_nn_residual<<<(unsigned)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(pred, target, n, scale, loss);
     return cudaGetLastError();
 }
 

@@ -210,7 +210,7 @@ NNWeightsMut nn_carve(void *base);
 cudaError_t launch_nn_pack(const float *theta, const NNWeightsMut &w, cudaStream_t st);
 cudaError_t launch_nn_fwd(const NNArgs &a, int64_t cells, bool train, cudaStream_t st);
 cudaError_t launch_nn_bwd(const NNArgs &a, int64_t cells, cudaStream_t st);
-cudaError_t launch_nn_residual(float *pred, const float *target, int64_t n, float inv_total, double *loss,
+cudaError_t launch_nn_residual(float *pred, const float *target, int64_t n, float scale, double *loss,
                                cudaStream_t st);
 cudaError_t launch_adam(float *theta, float *grad, float *m, float *v, int np, float lr, float b1, float b2, float eps,
                         float c1, float c2, cudaStream_t st);

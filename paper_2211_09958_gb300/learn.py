@@ -85,7 +85,8 @@ def snapshots(setup, fine, coarse, seed):
 
 @dataclass
 class TrainLog:
-    losses: list = field(default_factory=list)      # per Adam step
+    losses: list = field(default_factory=list)      # per Adam step, relative to the sample's |T|^2
+    samples: list = field(default_factory=list)     # snapshot index of each step
     base: list = field(default_factory=list)        # |T|^2 of each sample
     seconds_data: float = 0.0
     seconds_train: float = 0.0
@@ -106,11 +107,12 @@ def _init_theta(count, seed):
     return theta
 
 
-def train(setup, seeds, epochs=3, lr=1e-3, lr_final=1e-4, init_seed=0, theta=None, log=None):
+def train(setup, seeds, epochs=3, lr=1e-3, lr_final=1e-4, init_seed=0, theta=None, log=None, weighted=True):
     """Train the correction on the reference runs of ``seeds`` (consumed
     ``setup.group`` at a time, each group's samples visited ``epochs`` times
     in a seeded random order, learning rate decaying geometrically from lr to
-    lr_final); returns (theta, log)."""
+    lr_final; with ``weighted`` each sample's loss counts relative to its
+    |T|^2); returns (theta, log)."""
     log = log or TrainLog()
     coarse, fine = setup.coarse(), setup.fine()
     if theta is None:
@@ -128,11 +130,16 @@ def train(setup, seeds, epochs=3, lr=1e-3, lr_final=1e-4, init_seed=0, theta=Non
         log.base += [float((T[k] ** 2).sum(-1).mean()) for k in range(len(a))]
         torch.cuda.synchronize()
         t1 = time.perf_counter()
+        # each sample's loss relative to its own |T|^2, so that early times
+        # (forces ~1e-5 of the late ones) weigh as much as late ones
+        scale = [1.0 / max(b, 1e-30) for b in log.base[-len(a):]]
         for _ in range(epochs):
             for k in rng.permutation(len(a)):
                 step += 1
                 rate = lr * (lr_final / lr) ** ((step - 1) / max(total - 1, 1))
-                log.losses.append(coarse.nn_train_step(S[k], T[k], float(a[k]), lr=rate, step=step))
+                log.losses.append(coarse.nn_train_step(S[k], T[k], float(a[k]), lr=rate, step=step,
+                                                       weight=scale[k] if weighted else 1.0) * scale[k])
+                log.samples.append(int(k))
         t2 = time.perf_counter()
         log.seconds_data += t1 - t0
         log.seconds_train += t2 - t1

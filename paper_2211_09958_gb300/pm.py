@@ -204,12 +204,14 @@ class ParticleMesh:
         self._call("pm_nn_predict", _ptr(s), ctypes.c_double(a), _ptr(df))
         return df
 
-    def nn_train_step(self, s, target, a, lr=1e-3, step=1, apply=True):
-        """Force-matching loss at (s, a) against target; one Adam step when apply."""
+    def nn_train_step(self, s, target, a, lr=1e-3, step=1, apply=True, weight=1.0):
+        """Force-matching loss at (s, a) against target (returned unweighted);
+        the gradient of weight * loss, then one Adam step when apply."""
         self._particles(s, "s")
         self._particles(target, "target")
         loss = ctypes.c_double(0.0)
-        self._call("pm_nn_train_step", _ptr(s), _ptr(target), ctypes.c_double(a), ctypes.c_double(lr),
+        self._call("pm_nn_train_step", _ptr(s), _ptr(target), ctypes.c_double(a), ctypes.c_double(weight),
+                   ctypes.c_double(lr),
                    ctypes.c_int64(step), int(bool(apply)), ctypes.byref(loss))
         return loss.value
 

@@ -90,6 +90,12 @@ def test_gradient_parity(n_p, n_m, box):
     g = grad.astype(np.float64)
     assert _rel(g, rg) < 5e-3, _rel(g, rg)
     assert g @ rg / np.linalg.norm(g) / np.linalg.norm(rg) > 0.9999
+    # the sample weight scales the gradient, not the reported loss (a power
+    # of two, so that the bf16 roundings scale exactly; FP32 atomics remain)
+    loss4 = pm.nn_train_step(_cuda(s)[None], _cuda(target)[None], 0.7, apply=False, weight=4.0)
+    _, grad4 = pm.nn_get_params()
+    assert abs(loss4 - loss) <= 1e-6 * abs(loss)
+    assert _rel(grad4.astype(np.float64), 4.0 * g) < 1e-4
     # every parameter block carries gradient
     k = 0
     for name, shape in olearned.param_shapes():
@@ -191,7 +197,9 @@ def test_training_reduces_force_error():
     fine = ParticleMesh(32, 128, 64.0, 0.3, 0.8, 10)
     s, p = coarse.init_lpt(seed=31)
     coarse.integrate(s, p)
-    target = fine.pm_force(s) - coarse.pm_force(s)
+    # the lattice sits half a mesh cell off the nodes: same positions, shifted s
+    from paper_2211_09958_gb300.learn import lattice_shift
+    target = fine.pm_force(s + lattice_shift(coarse, fine)) - coarse.pm_force(s)
     base = float((target ** 2).sum(-1).mean())
     coarse.nn_set_params(olearned.init_params(2).astype(np.float32))
     first = coarse.nn_train_step(s, target, 1.0, lr=2e-3, step=1)
