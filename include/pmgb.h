@@ -233,7 +233,9 @@ int pm_host_coefficients(const pm_config *cfg, double *kdk, double *dkdk, double
  * pm_nn_get_params   download theta and/or the last gradient (host; NULL skips)
  * pm_nn_enable       apply the correction in pm_integrate and pm_kdk_step at
  *                    each evaluation's scale factor (pm_force stays the plain
- *                    PM force; pm_adjoint_integrate refuses with PM_ESTATE)
+ *                    PM force; pm_adjoint_integrate refuses with PM_ESTATE);
+ *                    synchronises the stream and returns PM_ECUDA if a
+ *                    tensor-core wait of an earlier correction timed out
  * pm_nn_predict      dF device [n_batch][n_p^3][3]: the correction read at
  *                    the particles s for scale factor a
  * pm_nn_train_step   force matching at particles s: loss = mean over

@@ -80,6 +80,8 @@ struct pm_ctx {
     float *nn_theta = nullptr, *nn_grad = nullptr, *nn_m = nullptr, *nn_v = nullptr, *nn_part = nullptr;
     __nv_bfloat16 *nn_act = nullptr;
     double *nn_loss = nullptr;
+    int *nn_err = nullptr;  // tensor-core kernel time-out flag
+    __nv_bfloat16 *nn_feat = nullptr;  // feature mesh [run][n^3]
 };
 
 namespace {
@@ -508,19 +510,24 @@ int ensure_nn(pm_ctx *ctx) {
         cudaMalloc(&ctx->nn_packed, nn_packed_bytes()) != cudaSuccess ||
         cudaMalloc(&ctx->nn_act, sizeof(__nv_bfloat16) * act) != cudaSuccess ||
         cudaMalloc(&ctx->nn_part, sizeof(float) * 3 * parts) != cudaSuccess ||
-        cudaMalloc(&ctx->nn_loss, sizeof(double)) != cudaSuccess) {
+        cudaMalloc(&ctx->nn_loss, sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ctx->nn_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->nn_err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&ctx->nn_feat, sizeof(__nv_bfloat16) * cells) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, PM_ENOMEM, "cannot allocate the learned-correction buffers");
     }
     ctx->nnw = nn_carve(ctx->nn_packed);
     PM_CUDA(ctx, nn_prepare());
+    PM_CUDA(ctx, nn_tc_prepare());
     return PM_OK;
 }
 
 NNArgs nn_args(pm_ctx *ctx, double a) {
     NNArgs na{};
     na.w = NNWeights{ctx->nnw.w1t, ctx->nnw.w2t, ctx->nnw.w2n, ctx->nnw.w3t, ctx->nnw.w3n,
-                     ctx->nnw.b1, ctx->nnw.b2, ctx->nnw.b3};
+                     ctx->nnw.b1, ctx->nnw.b2, ctx->nnw.b3, ctx->nnw.w1c, ctx->nnw.w2c, ctx->nnw.w3c};
+    na.err = ctx->nn_err;
+    na.feat = ctx->nn_feat;
     na.n = ctx->P.n_m;
     na.rho = ctx->r1;
     na.afeat = (float)a;
@@ -541,12 +548,25 @@ NNArgs nn_args(pm_ctx *ctx, double a) {
     return na;
 }
 
+// Report (and clear) a time-out of the tensor-core kernel's MMA waits.
+int nn_check(pm_ctx *ctx) {
+    int flag = 0;
+    PM_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->nn_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (flag) {
+        PM_CUDA(ctx, cudaMemset(ctx->nn_err, 0, sizeof(int)));
+        return fail(ctx, PM_ECUDA, "tensor-core MMA wait timed out in the learned correction");
+    }
+    return PM_OK;
+}
+
 // Add the network's correction to the force meshes (r4) from the density in
 // r1 at scale factor a.
 int apply_correction(pm_ctx *ctx, double a) {
     NNArgs na = nn_args(ctx, a);
     na.accumulate = 1;
-    PM_LAUNCH(ctx, "nn_fwd", launch_nn_fwd(na, nn_cells(ctx), false, ctx->stream));
+    PM_LAUNCH(ctx, "nn_feat", launch_nn_feat(ctx->r1, ctx->nn_feat, nn_cells(ctx), ctx->stream));
+    PM_LAUNCH(ctx, "nn_fwd_tc", launch_nn_fwd_tc(na, nn_cells(ctx), ctx->stream));
     return PM_OK;
 }
 
@@ -559,7 +579,12 @@ int nn_forward_at(pm_ctx *ctx, const float *s, double a, bool train) {
     pa.mesh = dref;
     PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
     NNArgs na = nn_args(ctx, a);
-    PM_LAUNCH(ctx, train ? "nn_fwd_train" : "nn_fwd", launch_nn_fwd(na, nn_cells(ctx), train, ctx->stream));
+    if (train)
+        PM_LAUNCH(ctx, "nn_fwd_train", launch_nn_fwd(na, nn_cells(ctx), true, ctx->stream));
+    else {
+        PM_LAUNCH(ctx, "nn_feat", launch_nn_feat(ctx->r1, ctx->nn_feat, nn_cells(ctx), ctx->stream));
+        PM_LAUNCH(ctx, "nn_fwd_tc", launch_nn_fwd_tc(na, nn_cells(ctx), ctx->stream));
+    }
     return PM_OK;
 }
 
@@ -750,7 +775,8 @@ int pm_destroy(pm_ctx *ctx) {
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     for (void *p : {(void *)ctx->nn_packed, (void *)ctx->nn_theta, (void *)ctx->nn_grad, (void *)ctx->nn_m,
-                    (void *)ctx->nn_v, (void *)ctx->nn_part, (void *)ctx->nn_act, (void *)ctx->nn_loss})
+                    (void *)ctx->nn_v, (void *)ctx->nn_part, (void *)ctx->nn_act, (void *)ctx->nn_loss,
+                    (void *)ctx->nn_err, (void *)ctx->nn_feat})
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->spec, (void *)ctx->tw}) 
@@ -1194,6 +1220,10 @@ int pm_nn_get_params(pm_ctx *ctx, float *theta, float *grad) {
 int pm_nn_enable(pm_ctx *ctx, int enable) {
     if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
     if (enable && !ctx->nn_theta) return fail(ctx, PM_ESTATE, "set the network parameters first");
+    if (ctx->nn_err) {
+        DeviceGuard guard(ctx->device);
+        PM_TRY(nn_check(ctx));  // a time-out in the corrected integrations so far
+    }
     ctx->nn_on = enable != 0;
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
@@ -1209,7 +1239,8 @@ int pm_nn_predict(pm_ctx *ctx, const float *s, double a, float *dF) {
     PM_TRY(nn_forward_at(ctx, s, a, false));
     ReadArgs ra = read_args(ctx, const_cast<float *>(s));
     ra.f = dF;
-    return read_forces(ctx, READ_FORCE, ra);
+    PM_TRY(read_forces(ctx, READ_FORCE, ra));
+    return nn_check(ctx);
 }
 
 int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a, double weight, double lr,

@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(THREADS) k_wgrad(const bf16 *__restrict__ A, c
 __global__ void k_nn_pack(const float *theta, NNWeightsMut w) {
     const float *W1 = theta, *b1 = W1 + NI * NH, *W2 = b1 + NH, *b2 = W2 + NH * NH, *W3 = b2 + NH, *b3 = W3 + NH * NO;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < NH * KP2; k += gridDim.x * blockDim.x) {
-        const int r = k / KP2, c = k % KP2;
+        const int r = k / KP2, c = k % KP2;  // NH * KP2 > NH * NH: every index below is reached
         w.w2t[k] = __float2bfloat16_rn(c < NH ? W2[c * NH + r] : 0.f);  // [out][in]
         w.w2n[k] = __float2bfloat16_rn(c < NH ? W2[r * NH + c] : 0.f);  // [in][out]
         if (k < NH * KP1) {
@@ -378,6 +378,19 @@ __global__ void k_nn_pack(const float *theta, NNWeightsMut w) {
             w.b2[k] = b2[k];
         }
         if (k < 8) w.b3[k] = k < NO ? b3[k] : 0.f;
+        // tcgen05 operands: rows = outputs, K = inputs, core-matrix layout
+        {
+            const int r = k / NH, c = k % NH;  // k < NH * NH covers W2
+            if (k < NH * NH) w.w2c[nn_cm_index(r, c, NH)] = __float2bfloat16_rn(W2[c * NH + r]);
+            if (k < NH * NI) {
+                const int r1 = k / NI, c1 = k % NI;
+                w.w1c[nn_cm_index(r1, c1, NH)] = __float2bfloat16_rn(W1[c1 * NH + r1]);
+            }
+            if (k < 16 * NH) {
+                const int r3 = k / NH, c3 = k % NH;
+                w.w3c[nn_cm_index(r3, c3, 16)] = __float2bfloat16_rn(r3 < NO ? W3[c3 * NO + r3] : 0.f);
+            }
+        }
     }
 }
 
@@ -412,7 +425,8 @@ __global__ void k_nn_residual(float *pred, const float *target, int64_t n, float
 int nn_param_count() { return NI * NH + NH + NH * NH + NH + NH * NO + NO; }
 
 size_t nn_packed_bytes() {
-    return sizeof(bf16) * (NH * KP1 + 2 * NH * KP2 + 8 * KP2 + NH * KP3) + sizeof(float) * (NH + NH + 8) + 256;
+    return sizeof(bf16) * (NH * KP1 + 2 * NH * KP2 + 8 * KP2 + NH * KP3) + sizeof(float) * (NH + NH + 8) +
+           sizeof(bf16) * (NH * NI + NH * NH + 16 * NH) + 512;
 }
 
 NNWeightsMut nn_carve(void *base) {
@@ -431,6 +445,9 @@ NNWeightsMut nn_carve(void *base) {
     w.b1 = reinterpret_cast<float *>(take(sizeof(float) * NH));
     w.b2 = reinterpret_cast<float *>(take(sizeof(float) * NH));
     w.b3 = reinterpret_cast<float *>(take(sizeof(float) * 8));
+    w.w1c = reinterpret_cast<bf16 *>(take(sizeof(bf16) * NH * NI));
+    w.w2c = reinterpret_cast<bf16 *>(take(sizeof(bf16) * NH * NH));
+    w.w3c = reinterpret_cast<bf16 *>(take(sizeof(bf16) * 16 * NH));
     return w;
 }
 

@@ -1,0 +1,359 @@
+// Learned-correction inference on the 5th-generation tensor cores: the same
+// per-cell MLP as learned.cu (features asinh(rho - 1) of the 27 periodic
+// neighbours and a; 32 -> 128 -> 128 -> 3, ReLU; BF16 operands, FP32
+// accumulation; output times 3/2 Om h added to the force meshes), with each
+// layer one M = 128 tcgen05.mma chain whose accumulator lives in tensor
+// memory.
+//
+// Per 128-cell tile (one row of A per cell, one TMEM lane per row):
+//   features -> smem A1 (128 x 32, bf16)             all threads, gathered
+//               from the feature mesh bf16(asinh(rho - 1)) (k_nn_feat)
+//   D1 = A1 W1^T  (N = 128, 2 MMAs of K = 16)         one thread, TMEM cols [0,128)
+//   h1 = relu(D1 + b1) -> smem A2 (128 x 128, bf16)  tcgen05.ld, all threads
+//   D2 = A2 W2^T  (N = 128, 8 MMAs)                   TMEM cols [128,256)
+//   h2 = relu(D2 + b2) -> smem A2
+//   D3 = A2 W3^T  (N = 16, rows 3..15 of W3^T zero)   TMEM cols [0,16)
+//   out[cell][j] (+)= s_out (D3[j] + b3[j]), j < 3
+// Operands sit in shared memory in the no-swizzle K-major core-matrix layout
+// (nn_cm_index); weights are staged once per persistent block.  Warp w reads
+// TMEM lanes 32 (w % 4) .. + 31 (the cells of those rows) and columns
+// 64 (w / 4) .. + 63 of each 128-wide accumulator.
+//
+// Every wait on the MMA-completion mbarrier is bounded: on time-out the
+// kernel sets *err, stops issuing work, frees its tensor memory and returns.
+
+#include <cuda_bf16.h>
+
+#include "pm_internal.h"
+
+namespace pmgb {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int M = 128;          // cells per tile = TMEM lanes
+constexpr int THREADS = 256;    // 8 warps: lane quarter w % 4, column half w / 4
+constexpr int NI = NN_IN, NH = NN_HID, NO = NN_OUT;
+constexpr int N3 = 16;          // padded width of the last layer (M = 128 needs N % 16 == 0)
+constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+// shared-memory carve-up (bytes); every operand base is 128-byte aligned
+constexpr int OFF_W1 = 0;
+constexpr int OFF_W2 = OFF_W1 + NH * NI * 2;
+constexpr int OFF_W3 = OFF_W2 + NH * NH * 2;
+constexpr int OFF_A1 = OFF_W3 + N3 * NH * 2;
+constexpr int OFF_A2 = OFF_A1 + M * NI * 2;
+constexpr int OFF_B = OFF_A2 + M * NH * 2;           // b1[128], b2[128], b3[16] (FP32)
+constexpr int OFF_BAR = OFF_B + (2 * NH + N3) * 4;   // mbarrier (8 B)
+constexpr int OFF_TMEM = OFF_BAR + 8;                // TMEM base address slot
+constexpr int SMEM_BYTES = OFF_TMEM + 8;
+static_assert(OFF_W2 % 128 == 0 && OFF_W3 % 128 == 0 && OFF_A1 % 128 == 0 && OFF_A2 % 128 == 0, "alignment");
+static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address >> 4 (bits
+// 0-13), leading byte offset >> 4 (16-29), stride byte offset >> 4 (32-45),
+// descriptor version 1 (bits 46-47); base offset, LBO mode and layout 0.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_before();
+__device__ __forceinline__ void fence_after();
+
+// Thread 0 waits for the barrier phase, the block learns the outcome at a
+// thread barrier (so every thread takes the same branch), then orders its
+// tensor-memory reads after the MMAs.
+__device__ __forceinline__ bool wait_all(uint32_t bar, uint32_t &phase, int tid) {
+    const int ok = tid == 0 ? (int)bar_wait(bar, phase) : 1;
+    const bool all = __syncthreads_and(ok) != 0;
+    fence_after();
+    phase ^= 1;
+    return all;
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// Columns 16 HALF .. 16 HALF + 15 of one cell's feature row (offsets
+// q = 9 (ox + 1) + 3 (oy + 1) + (oz + 1) < 27, then a, then zeros), written
+// as two 16-byte core-matrix rows at dst and dst + M * 16.
+template <int HALF>
+__device__ __forceinline__ void feature_rows(const unsigned short *f, int64_t c, int n, unsigned short afeat,
+                                             char *dst) {
+    const int x = (int)(c / ((int64_t)n * n)), y = (int)((c / n) % n), z = (int)(c % n);
+    const int xs[3] = {x == 0 ? n - 1 : x - 1, x, x == n - 1 ? 0 : x + 1};
+    const int ys[3] = {y == 0 ? n - 1 : y - 1, y, y == n - 1 ? 0 : y + 1};
+    const int zs[3] = {z == 0 ? n - 1 : z - 1, z, z == n - 1 ? 0 : z + 1};
+#pragma unroll
+    for (int chunk = 0; chunk < 2; ++chunk) {
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            uint32_t v2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = 16 * HALF + 8 * chunk + 2 * e + h;
+                if (q < 27)
+                    v2[h] = __ldg(f + ((int64_t)xs[q / 9] * n + ys[(q / 3) % 3]) * n + zs[q % 3]);
+                else
+                    v2[h] = q == 27 ? afeat : 0u;
+            }
+            w[e] = v2[0] | (v2[1] << 16);
+        }
+        // the next 8 columns are the next K-direction core matrix, M * 16 bytes on
+        *reinterpret_cast<uint4 *>(dst + chunk * M * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// One K-chain of MMAs: D[128 x n] (=|+=) A[128 x k] B[n x k]^T.
+__device__ __forceinline__ void mma_chain(uint32_t d_tmem, uint32_t a_base, uint32_t b_base, int k, int n) {
+    const uint32_t lbo_a = (M / 8) * 128, lbo_b = (uint32_t)(n / 8) * 128;
+    for (int kk = 0; kk < k / 16; ++kk)
+        mma_f16(d_tmem, sdesc(a_base + 2 * kk * lbo_a, lbo_a, 128), sdesc(b_base + 2 * kk * lbo_b, lbo_b, 128),
+                idesc(n), kk > 0);
+}
+
+// 64 columns [c0, c0 + 64) of a 128-wide accumulator for this thread's row:
+// + bias, ReLU, bf16, into the A2 operand (row `row`, columns c0 ..).
+__device__ __forceinline__ void relu_to_a2(uint32_t taddr, const float *bias, int c0, int row, char *a2) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float v[32];
+        tmem_ld32(taddr + c0 + 32 * h, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {  // 8 columns = one 16-byte core-matrix row
+            const int c = c0 + 32 * h + 8 * q;
+            uint4 u;
+            u.x = pack2(fmaxf(v[8 * q + 0] + bias[c + 0], 0.f), fmaxf(v[8 * q + 1] + bias[c + 1], 0.f));
+            u.y = pack2(fmaxf(v[8 * q + 2] + bias[c + 2], 0.f), fmaxf(v[8 * q + 3] + bias[c + 3], 0.f));
+            u.z = pack2(fmaxf(v[8 * q + 4] + bias[c + 4], 0.f), fmaxf(v[8 * q + 5] + bias[c + 5], 0.f));
+            u.w = pack2(fmaxf(v[8 * q + 6] + bias[c + 6], 0.f), fmaxf(v[8 * q + 7] + bias[c + 7], 0.f));
+            *reinterpret_cast<uint4 *>(a2 + 2 * nn_cm_index(row, c, M)) = u;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t tiles) {
+    extern __shared__ __align__(1024) char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, colhalf = warp >> 2;
+    const int row = 32 * quarter + lane;  // this thread's accumulator row (cell of the tile)
+    float *bias = reinterpret_cast<float *>(sm + OFF_B);
+    const uint32_t bar = smem_u32(sm + OFF_BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_TMEM);
+
+    // stage weights and biases; init the barrier; allocate tensor memory
+    {
+        const int4 *src[3] = {reinterpret_cast<const int4 *>(a.w.w1c), reinterpret_cast<const int4 *>(a.w.w2c),
+                              reinterpret_cast<const int4 *>(a.w.w3c)};
+        const int off[3] = {OFF_W1, OFF_W2, OFF_W3}, n16[3] = {NH * NI / 8, NH * NH / 8, N3 * NH / 8};
+        for (int m = 0; m < 3; ++m)
+            for (int k = tid; k < n16[m]; k += THREADS) reinterpret_cast<int4 *>(sm + off[m])[k] = src[m][k];
+        for (int k = tid; k < 2 * NH + N3; k += THREADS)
+            bias[k] = k < NH ? a.w.b1[k] : (k < 2 * NH ? a.w.b2[k - NH] : (k - 2 * NH < NO ? a.w.b3[k - 2 * NH] : 0.f));
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+    const uint32_t sA1 = smem_u32(sm + OFF_A1), sA2 = smem_u32(sm + OFF_A2);
+    const uint32_t sW1 = smem_u32(sm + OFF_W1), sW2 = smem_u32(sm + OFF_W2), sW3 = smem_u32(sm + OFF_W3);
+    char *a1 = sm + OFF_A1, *a2 = sm + OFF_A2;
+
+    const int n = a.n;
+    const int64_t n3 = (int64_t)n * n * n;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const int64_t cell0 = tile * M;
+        const int64_t run = cell0 / n3;
+        const float *rho = a.rho + run * n3;
+        // features of cell `cl` from the bf16 feature mesh: threads 0..127
+        // build columns 0..15 (offsets 0..15), threads 128..255 columns
+        // 16..31 (offsets 16..26, a, zeros), as two 16-byte core-matrix rows
+        {
+            const int cl = tid & (M - 1);
+            const int64_t c = cell0 - run * n3 + cl;
+            const unsigned short *f = reinterpret_cast<const unsigned short *>(a.feat) + run * n3;
+            const unsigned short afeat = __bfloat16_as_ushort(__float2bfloat16_rn(a.afeat));
+            if (tid < M)
+                feature_rows<0>(f, c, n, afeat, a1 + 2 * nn_cm_index(cl, 0, M));
+            else
+                feature_rows<1>(f, c, n, afeat, a1 + 2 * nn_cm_index(cl, 16, M));
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        // layer 1
+        if (tid == 0) {
+            fence_after();
+            mma_chain(tmem, sA1, sW1, NI, NH);
+            mma_commit(bar);
+        }
+        ok = wait_all(bar, phase, tid);
+        if (!ok) break;
+        relu_to_a2(lane_base, bias, 64 * colhalf, row, a2);
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        // layer 2
+        if (tid == 0) {
+            fence_after();
+            mma_chain(tmem + NH, sA2, sW2, NH, NH);
+            mma_commit(bar);
+        }
+        ok = wait_all(bar, phase, tid);
+        if (!ok) break;
+        relu_to_a2(lane_base + NH, bias + NH, 64 * colhalf, row, a2);
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        // layer 3
+        if (tid == 0) {
+            fence_after();
+            mma_chain(tmem, sA2, sW3, NH, N3);
+            mma_commit(bar);
+        }
+        ok = wait_all(bar, phase, tid);
+        if (!ok) break;
+        if (colhalf == 0) {
+            float y[4];
+            tmem_ld4(lane_base, y);
+            const float s_out = a.pref[run] * a.s_scale;
+            float *dst = a.out + (cell0 + row) * 4;
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+                const float v = s_out * (y[j] + bias[2 * NH + j]);
+                dst[j] = a.accumulate ? dst[j] + v : v;
+            }
+        }
+        fence_before();
+        __syncthreads();  // A1 / A2 and the accumulators are free for the next tile
+        fence_after();
+    }
+    if (!ok && tid == 0) {
+        atomicExch(a.err, 1);
+        bar_wait(bar, phase ^ 1);  // the phase that timed out: let its MMAs finish (bounded)
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// Feature mesh: bf16(asinh(rho - 1)) per cell, four cells a thread.
+__global__ void k_nn_feat(const float4 *__restrict__ rho, uint2 *__restrict__ feat, int64_t n4) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 r = rho[i];
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(asinhf(r.x - 1.f), asinhf(r.y - 1.f));
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(asinhf(r.z - 1.f), asinhf(r.w - 1.f));
+        feat[i] = make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_nn_feat(const float *rho, __nv_bfloat16 *feat, int64_t cells, cudaStream_t st) {
+    const int64_t n4 = cells / 4, blocks = (n4 + 255) / 256;
+    k_nn_feat<<<(unsigned)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(
+        reinterpret_cast<const float4 *>(rho), reinterpret_cast<uint2 *>(feat), n4);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_tc_prepare() {
+    return cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+}
+
+cudaError_t launch_nn_fwd_tc(const NNArgs &a, int64_t cells, cudaStream_t st) {
+    const int64_t tiles = cells / M;
+    const int64_t cap = 2 * 152;  // two blocks per SM: 2 x 256 TMEM columns, 2 x ~87 KB shared memory
+    k_mlp_fwd_tc<<<(unsigned)(tiles < cap ? tiles : cap), THREADS, SMEM_BYTES, st>>>(a, tiles);
+    return cudaGetLastError();
+}
+
+}  // namespace pmgb

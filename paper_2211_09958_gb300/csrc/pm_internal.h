@@ -184,11 +184,22 @@ constexpr int NN_IN = 32, NN_HID = 128, NN_OUT = 3;
 struct NNWeights {  // packed bf16 operands and FP32 biases (learned.cu)
     const __nv_bfloat16 *w1t, *w2t, *w2n, *w3t, *w3n;
     const float *b1, *b2, *b3;
+    const __nv_bfloat16 *w1c, *w2c, *w3c;  // tensor-core (tcgen05) operand layouts
 };
 struct NNWeightsMut {
     __nv_bfloat16 *w1t, *w2t, *w2n, *w3t, *w3n;
     float *b1, *b2, *b3;
+    __nv_bfloat16 *w1c, *w2c, *w3c;
 };
+
+// Element index of (row r, column k) of an R x K bf16 operand stored as
+// 8 x 8 "core matrices" (8 rows of 16 contiguous bytes), K-direction core
+// matrices R/8 * 128 bytes apart and row-direction ones 128 bytes apart: the
+// no-swizzle K-major shared-memory layout the tcgen05 matrix descriptors
+// address (leading byte offset R * 16, stride byte offset 128).
+__host__ __device__ constexpr int nn_cm_index(int r, int k, int R) {
+    return (((k >> 3) * (R >> 3) + (r >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
 struct NNArgs {
     NNWeights w;
     int n;               // mesh cells per side
@@ -201,6 +212,8 @@ struct NNArgs {
     __nv_bfloat16 *xg, *h1g, *h2g, *g1g, *g2g, *g3g;  // training activations
     const float *gmesh;  // interleaved gradient mesh, slots 1..3
     float *grad, *gb1, *gb2, *gb3;
+    int *err;            // set by the tensor-core kernel when a wait times out
+    const __nv_bfloat16 *feat;  // [run][n^3] bf16(asinh(rho - 1)) (tensor-core path)
 };
 
 int nn_param_count();
@@ -210,6 +223,9 @@ NNWeightsMut nn_carve(void *base);
 cudaError_t launch_nn_pack(const float *theta, const NNWeightsMut &w, cudaStream_t st);
 cudaError_t launch_nn_fwd(const NNArgs &a, int64_t cells, bool train, cudaStream_t st);
 cudaError_t launch_nn_bwd(const NNArgs &a, int64_t cells, cudaStream_t st);
+cudaError_t nn_tc_prepare();
+cudaError_t launch_nn_feat(const float *rho, __nv_bfloat16 *feat, int64_t cells, cudaStream_t st);
+cudaError_t launch_nn_fwd_tc(const NNArgs &a, int64_t cells, cudaStream_t st);
 cudaError_t launch_nn_residual(float *pred, const float *target, int64_t n, float scale, double *loss,
                                cudaStream_t st);
 cudaError_t launch_adam(float *theta, float *grad, float *m, float *v, int np, float lr, float b1, float b2, float eps,
