@@ -8,16 +8,22 @@
 // Per 128-cell tile (one row of A per cell, one TMEM lane per row):
 //   features -> smem A1 (128 x 32, bf16)             all threads, gathered
 //               from the feature mesh bf16(asinh(rho - 1)) (k_nn_feat)
-//   D1 = A1 W1^T  (N = 128, 2 MMAs of K = 16)         one thread, TMEM cols [0,128)
+//   D1 = A1 W1^T  (N = 128, 2 MMAs of K = 16)         one thread
 //   h1 = relu(D1 + b1) -> smem A2 (128 x 128, bf16)  tcgen05.ld, all threads
-//   D2 = A2 W2^T  (N = 128, 8 MMAs)                   TMEM cols [128,256)
+//   D2 = A2 W2^T  (N = 128, 8 MMAs)
 //   h2 = relu(D2 + b2) -> smem A2
-//   D3 = A2 W3^T  (N = 16, rows 3..15 of W3^T zero)   TMEM cols [0,16)
+//   D3 = A2 W3^T  (N = 16, rows 3..15 of W3^T zero)
+// (A1 is the first 8 KB of A2: the L1 MMAs have finished reading it before
+// the h1 epilogue writes there.)
 //   out[cell][j] (+)= s_out (D3[j] + b3[j]), j < 3
 // Operands sit in shared memory in the no-swizzle K-major core-matrix layout
-// (nn_cm_index); weights are staged once per persistent block.  Warp w reads
-// TMEM lanes 32 (w % 4) .. + 31 (the cells of those rows) and columns
-// 64 (w / 4) .. + 63 of each 128-wide accumulator.
+// (nn_cm_index).  A persistent block stages the weights once and runs PIPES
+// independent tile pipelines of 8 warps (own A buffer, TMEM columns,
+// mbarrier and named barrier), so that while one pipeline waits for its
+// MMAs another runs its epilogue; two blocks share an SM (4 pipelines).
+// Warp w of a pipeline reads TMEM lanes 32 (w % 4) .. + 31 (the cells of
+// those rows) and columns 64 (w / 4) .. + 63 of each 128-wide accumulator;
+// D1, D2 and D3 of a pipeline reuse its 128 columns in turn.
 //
 // Every wait on the MMA-completion mbarrier is bounded: on time-out the
 // kernel sets *err, stops issuing work, frees its tensor memory and returns.
@@ -33,24 +39,28 @@ namespace {
 using bf16 = __nv_bfloat16;
 
 constexpr int M = 128;          // cells per tile = TMEM lanes
-constexpr int THREADS = 256;    // 8 warps: lane quarter w % 4, column half w / 4
+constexpr int PIPES = 2;        // tile pipelines per block
+constexpr int PT = 256;         // threads per pipeline: 8 warps, lane quarter w % 4, column half w / 4
+constexpr int THREADS = PIPES * PT;
 constexpr int NI = NN_IN, NH = NN_HID, NO = NN_OUT;
 constexpr int N3 = 16;          // padded width of the last layer (M = 128 needs N % 16 == 0)
-constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t TMEM_COLS = 128 * PIPES;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
 // shared-memory carve-up (bytes); every operand base is 128-byte aligned
 constexpr int OFF_W1 = 0;
 constexpr int OFF_W2 = OFF_W1 + NH * NI * 2;
 constexpr int OFF_W3 = OFF_W2 + NH * NH * 2;
-constexpr int OFF_A1 = OFF_W3 + N3 * NH * 2;
-constexpr int OFF_A2 = OFF_A1 + M * NI * 2;
-constexpr int OFF_B = OFF_A2 + M * NH * 2;           // b1[128], b2[128], b3[16] (FP32)
-constexpr int OFF_BAR = OFF_B + (2 * NH + N3) * 4;   // mbarrier (8 B)
-constexpr int OFF_TMEM = OFF_BAR + 8;                // TMEM base address slot
+constexpr int OFF_A = OFF_W3 + N3 * NH * 2;           // PIPES x A2 (128 x 128 bf16), A1 aliased at its start
+constexpr int A_BYTES = M * NH * 2;
+constexpr int OFF_B = OFF_A + PIPES * A_BYTES;        // b1[128], b2[128], b3[16] (FP32)
+constexpr int OFF_BAR = OFF_B + (2 * NH + N3) * 4;    // PIPES mbarriers (8 B each)
+constexpr int OFF_TMEM = OFF_BAR + 8 * PIPES;         // TMEM base address slot
 constexpr int SMEM_BYTES = OFF_TMEM + 8;
-static_assert(OFF_W2 % 128 == 0 && OFF_W3 % 128 == 0 && OFF_A1 % 128 == 0 && OFF_A2 % 128 == 0, "alignment");
+static_assert(OFF_W2 % 128 == 0 && OFF_W3 % 128 == 0 && OFF_A % 128 == 0 && A_BYTES % 128 == 0, "alignment");
 static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
+static_assert(M * NI * 2 <= A_BYTES, "A1 fits in A2");
+static_assert(2 * (SMEM_BYTES + 1024) <= 228 * 1024, "two blocks per SM");
 
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
@@ -99,12 +109,28 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
 __device__ __forceinline__ void fence_before();
 __device__ __forceinline__ void fence_after();
 
-// Thread 0 waits for the barrier phase, the block learns the outcome at a
-// thread barrier (so every thread takes the same branch), then orders its
-// tensor-memory reads after the MMAs.
-__device__ __forceinline__ bool wait_all(uint32_t bar, uint32_t &phase, int tid) {
-    const int ok = tid == 0 ? (int)bar_wait(bar, phase) : 1;
-    const bool all = __syncthreads_and(ok) != 0;
+// Named barrier of pipeline p (ids 1..PIPES; 0 is __syncthreads).
+__device__ __forceinline__ void pipe_sync(int p) {
+    asm volatile("bar.sync %0, %1;" ::"r"(p + 1), "r"(PT) : "memory");
+}
+
+__device__ __forceinline__ int pipe_and(int p, int pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred q, o;\n\tsetp.ne.b32 q, %1, 0;\n\tbar.red.and.pred o, %2, %3, q;\n\t"
+        "selp.b32 %0, 1, 0, o;\n\t}\n"
+        : "=r"(r)
+        : "r"(pred), "r"(p + 1), "r"(PT)
+        : "memory");
+    return r;
+}
+
+// The pipeline's thread 0 waits for the barrier phase, the pipeline learns
+// the outcome at its named barrier (so every thread takes the same branch),
+// then orders its tensor-memory reads after the MMAs.
+__device__ __forceinline__ bool wait_all(uint32_t bar, uint32_t &phase, int tp, int p) {
+    const int ok = tp == 0 ? (int)bar_wait(bar, phase) : 1;
+    const bool all = pipe_and(p, ok) != 0;
     fence_after();
     phase ^= 1;
     return all;
@@ -140,9 +166,11 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
     for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&v);
+// bf16x2 of (relu(lo), relu(hi)), round to nearest even (lo in the low half).
+__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 // Columns 16 HALF .. 16 HALF + 15 of one cell's feature row (offsets
@@ -195,10 +223,10 @@ __device__ __forceinline__ void relu_to_a2(uint32_t taddr, const float *bias, in
         for (int q = 0; q < 4; ++q) {  // 8 columns = one 16-byte core-matrix row
             const int c = c0 + 32 * h + 8 * q;
             uint4 u;
-            u.x = pack2(fmaxf(v[8 * q + 0] + bias[c + 0], 0.f), fmaxf(v[8 * q + 1] + bias[c + 1], 0.f));
-            u.y = pack2(fmaxf(v[8 * q + 2] + bias[c + 2], 0.f), fmaxf(v[8 * q + 3] + bias[c + 3], 0.f));
-            u.z = pack2(fmaxf(v[8 * q + 4] + bias[c + 4], 0.f), fmaxf(v[8 * q + 5] + bias[c + 5], 0.f));
-            u.w = pack2(fmaxf(v[8 * q + 6] + bias[c + 6], 0.f), fmaxf(v[8 * q + 7] + bias[c + 7], 0.f));
+            u.x = pack2_relu(v[8 * q + 0] + bias[c + 0], v[8 * q + 1] + bias[c + 1]);
+            u.y = pack2_relu(v[8 * q + 2] + bias[c + 2], v[8 * q + 3] + bias[c + 3]);
+            u.z = pack2_relu(v[8 * q + 4] + bias[c + 4], v[8 * q + 5] + bias[c + 5]);
+            u.w = pack2_relu(v[8 * q + 6] + bias[c + 6], v[8 * q + 7] + bias[c + 7]);
             *reinterpret_cast<uint4 *>(a2 + 2 * nn_cm_index(row, c, M)) = u;
         }
     }
@@ -207,13 +235,14 @@ __device__ __forceinline__ void relu_to_a2(uint32_t taddr, const float *bias, in
 __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t tiles) {
     extern __shared__ __align__(1024) char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, colhalf = warp >> 2;
-    const int row = 32 * quarter + lane;  // this thread's accumulator row (cell of the tile)
+    const int pipe = tid / PT, tp = tid % PT;           // pipeline and thread within it
+    const int quarter = warp & 3, colhalf = (warp >> 2) & 1;
+    const int row = 32 * quarter + lane;                // this thread's accumulator row (cell of the tile)
     float *bias = reinterpret_cast<float *>(sm + OFF_B);
-    const uint32_t bar = smem_u32(sm + OFF_BAR);
+    const uint32_t bar = smem_u32(sm + OFF_BAR + 8 * pipe);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_TMEM);
 
-    // stage weights and biases; init the barrier; allocate tensor memory
+    // stage weights and biases; init the barriers; allocate tensor memory
     {
         const int4 *src[3] = {reinterpret_cast<const int4 *>(a.w.w1c), reinterpret_cast<const int4 *>(a.w.w2c),
                               reinterpret_cast<const int4 *>(a.w.w3c)};
@@ -223,7 +252,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t til
         for (int k = tid; k < 2 * NH + N3; k += THREADS)
             bias[k] = k < NH ? a.w.b1[k] : (k < 2 * NH ? a.w.b2[k - NH] : (k - 2 * NH < NO ? a.w.b3[k - 2 * NH] : 0.f));
     }
-    if (tid == 0) {
+    if (tp == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -237,67 +266,66 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t til
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t tmem = *tslot;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
-    const uint32_t sA1 = smem_u32(sm + OFF_A1), sA2 = smem_u32(sm + OFF_A2);
+    const uint32_t tcol = *tslot + 128 * pipe;                     // this pipeline's 128 columns
+    const uint32_t lane_base = tcol + ((uint32_t)(32 * quarter) << 16);
+    char *abuf = sm + OFF_A + pipe * A_BYTES;
+    const uint32_t sA = smem_u32(abuf);
     const uint32_t sW1 = smem_u32(sm + OFF_W1), sW2 = smem_u32(sm + OFF_W2), sW3 = smem_u32(sm + OFF_W3);
-    char *a1 = sm + OFF_A1, *a2 = sm + OFF_A2;
 
     const int n = a.n;
     const int64_t n3 = (int64_t)n * n * n;
     uint32_t phase = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+    for (int64_t tile = (int64_t)blockIdx.x * PIPES + pipe; tile < tiles && ok; tile += (int64_t)gridDim.x * PIPES) {
         const int64_t cell0 = tile * M;
         const int64_t run = cell0 / n3;
-        const float *rho = a.rho + run * n3;
-        // features of cell `cl` from the bf16 feature mesh: threads 0..127
-        // build columns 0..15 (offsets 0..15), threads 128..255 columns
-        // 16..31 (offsets 16..26, a, zeros), as two 16-byte core-matrix rows
+        // features of cell `cl` from the bf16 feature mesh: threads 0..127 of
+        // the pipeline build columns 0..15 (offsets 0..15), threads 128..255
+        // columns 16..31 (offsets 16..26, a, zeros)
         {
-            const int cl = tid & (M - 1);
+            const int cl = tp & (M - 1);
             const int64_t c = cell0 - run * n3 + cl;
             const unsigned short *f = reinterpret_cast<const unsigned short *>(a.feat) + run * n3;
             const unsigned short afeat = __bfloat16_as_ushort(__float2bfloat16_rn(a.afeat));
-            if (tid < M)
-                feature_rows<0>(f, c, n, afeat, a1 + 2 * nn_cm_index(cl, 0, M));
+            if (tp < M)
+                feature_rows<0>(f, c, n, afeat, abuf + 2 * nn_cm_index(cl, 0, M));
             else
-                feature_rows<1>(f, c, n, afeat, a1 + 2 * nn_cm_index(cl, 16, M));
+                feature_rows<1>(f, c, n, afeat, abuf + 2 * nn_cm_index(cl, 16, M));
         }
         fence_async_smem();
         fence_before();
-        __syncthreads();
-        // layer 1
-        if (tid == 0) {
+        pipe_sync(pipe);
+        // layer 1 (A1 = features, 128 x 32)
+        if (tp == 0) {
             fence_after();
-            mma_chain(tmem, sA1, sW1, NI, NH);
+            mma_chain(tcol, sA, sW1, NI, NH);
             mma_commit(bar);
         }
-        ok = wait_all(bar, phase, tid);
+        ok = wait_all(bar, phase, tp, pipe);
         if (!ok) break;
-        relu_to_a2(lane_base, bias, 64 * colhalf, row, a2);
+        relu_to_a2(lane_base, bias, 64 * colhalf, row, abuf);
         fence_async_smem();
         fence_before();
-        __syncthreads();
+        pipe_sync(pipe);
         // layer 2
-        if (tid == 0) {
+        if (tp == 0) {
             fence_after();
-            mma_chain(tmem + NH, sA2, sW2, NH, NH);
+            mma_chain(tcol, sA, sW2, NH, NH);
             mma_commit(bar);
         }
-        ok = wait_all(bar, phase, tid);
+        ok = wait_all(bar, phase, tp, pipe);
         if (!ok) break;
-        relu_to_a2(lane_base + NH, bias + NH, 64 * colhalf, row, a2);
+        relu_to_a2(lane_base, bias + NH, 64 * colhalf, row, abuf);
         fence_async_smem();
         fence_before();
-        __syncthreads();
+        pipe_sync(pipe);
         // layer 3
-        if (tid == 0) {
+        if (tp == 0) {
             fence_after();
-            mma_chain(tmem, sA2, sW3, NH, N3);
+            mma_chain(tcol, sA, sW3, NH, N3);
             mma_commit(bar);
         }
-        ok = wait_all(bar, phase, tid);
+        ok = wait_all(bar, phase, tp, pipe);
         if (!ok) break;
         if (colhalf == 0) {
             float y[4];
@@ -311,10 +339,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t til
             }
         }
         fence_before();
-        __syncthreads();  // A1 / A2 and the accumulators are free for the next tile
+        pipe_sync(pipe);  // the A buffer and the accumulator columns are free for the next tile
         fence_after();
     }
-    if (!ok && tid == 0) {
+    if (!ok && tp == 0) {
         atomicExch(a.err, 1);
         bar_wait(bar, phase ^ 1);  // the phase that timed out: let its MMAs finish (bounded)
     }
@@ -322,7 +350,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t til
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(TMEM_COLS)
+                     : "memory");
     }
 }
 
@@ -351,8 +380,9 @@ cudaError_t nn_tc_prepare() {
 
 cudaError_t launch_nn_fwd_tc(const NNArgs &a, int64_t cells, cudaStream_t st) {
     const int64_t tiles = cells / M;
-    const int64_t cap = 2 * 152;  // two blocks per SM: 2 x 256 TMEM columns, 2 x ~87 KB shared memory
-    k_mlp_fwd_tc<<<(unsigned)(tiles < cap ? tiles : cap), THREADS, SMEM_BYTES, st>>>(a, tiles);
+    const int64_t want = (tiles + PIPES - 1) / PIPES;
+    const int64_t cap = 2 * 152;  // two blocks per SM: 2 x 256 TMEM columns, 2 x ~109 KB shared memory
+    k_mlp_fwd_tc<<<(unsigned)(want < cap ? want : cap), THREADS, SMEM_BYTES, st>>>(a, tiles);
     return cudaGetLastError();
 }
 
