@@ -62,6 +62,9 @@ _SIGNATURES = {
     "pm_mesh_irfft": (ctypes.c_int, [_P, _P, _P]),
     "pm_power_spectrum": (ctypes.c_int, [_P, _P, _c_double_p, _c_double_p, _c_double_p]),
     "pm_launch_count": (ctypes.c_int64, [_P]),
+    "pm_autotune": (ctypes.c_int, [_P, _P, _P]),
+    "pm_set_tuning": (ctypes.c_int, [_P, _P]),
+    "pm_get_tuning": (ctypes.c_int, [_P, _P]),
     "pm_nn_param_count": (ctypes.c_int, []),
     "pm_nn_set_params": (ctypes.c_int, [_P, _P]),
     "pm_nn_get_params": (ctypes.c_int, [_P, _P, _P]),

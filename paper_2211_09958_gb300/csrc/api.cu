@@ -73,6 +73,9 @@ struct pm_ctx {
         int64_t launches;
     };
     std::vector<GraphEntry> graphs;
+    // launch shapes (block sizes) of the tunable kernel families:
+    // paint, read, spectral force/adjoint, z-pass FFT (n >= 256)
+    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256};
     // learned force correction (own-FFT meshes only)
     bool nn_on = false;
     void *nn_packed = nullptr;
@@ -271,11 +274,12 @@ Spec mesh_spec(pm_ctx *ctx) {
     const int n = ctx->P.n_m;
     if (ctx->own) {
         const int64_t per = (int64_t)n * n * ctx->fg.zc;
-        return Spec{ctx->spec, per * ctx->P.n_batch, per, n, ctx->P.n_batch, kf, ctx->fg.zc, 1, ctx->d_grad};
+        return Spec{ctx->spec, per * ctx->P.n_batch, per, n, ctx->P.n_batch, kf, ctx->fg.zc, 1, ctx->d_grad,
+                    ctx->tune[2]};
     }
     const int64_t modes = ctx->mesh_pad / 2;
     return Spec{reinterpret_cast<float2 *>(ctx->mesh), modes * ctx->P.n_batch, modes, n, ctx->P.n_batch, kf, n / 2 + 1, 0,
-                ctx->d_grad};
+                ctx->d_grad, ctx->tune[2]};
 }
 
 MeshRef lat_ref(pm_ctx *ctx) {
@@ -321,6 +325,7 @@ PaintArgs paint_args(pm_ctx *ctx, const float *s, const float *mu = nullptr) {
     a.s = s;
     a.mu = mu;
     a.mesh = mesh_ref(ctx);
+    a.threads = ctx->tune[0];
     return a;
 }
 
@@ -332,6 +337,7 @@ ReadArgs read_args(pm_ctx *ctx, float *s) {
     a.table = ctx->d_table;
     a.red_bstride = 2 * (ctx->P.n_steps + 1);
     a.drift_step = -1;
+    a.threads = ctx->tune[1];
     return a;
 }
 
@@ -597,6 +603,111 @@ extern "C" {
 const char *pm_last_error(const pm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
 int64_t pm_launch_count(const pm_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+static int set_tuning(pm_ctx *ctx, const int *t) {
+    for (int k = 0; k < PM_TUNE_KINDS; ++k)
+        if (t[k] != 128 && t[k] != 256 && t[k] != 512) return fail(ctx, PM_EINVAL, "block sizes must be 128, 256 or 512");
+    for (int k = 0; k < PM_TUNE_KINDS; ++k) ctx->tune[k] = t[k];
+    ctx->fg.zthreads = ctx->tune[3];
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);  // captured with the old shapes
+    ctx->graphs.clear();
+    return PM_OK;
+}
+
+int pm_set_tuning(pm_ctx *ctx, const int *threads) {
+    if (!ctx || !threads) return fail(ctx, PM_EINVAL, "ctx and threads must not be NULL");
+    return set_tuning(ctx, threads);
+}
+
+int pm_get_tuning(pm_ctx *ctx, int *threads) {
+    if (!ctx || !threads) return fail(ctx, PM_EINVAL, "ctx and threads must not be NULL");
+    for (int k = 0; k < PM_TUNE_KINDS; ++k) threads[k] = ctx->tune[k];
+    return PM_OK;
+}
+
+int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    PM_TRY(check_ptr(ctx, s, "s"));
+    DeviceGuard guard(ctx->device);
+    const int B = ctx->P.n_batch;
+    const int64_t npart = ctx->g.npart * B;
+    float *f = nullptr;
+    if (cudaMalloc(&f, sizeof(float) * 3 * npart) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, PM_ENOMEM, "cannot allocate the autotuner's scratch force");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    int rc = PM_OK;
+    // one representative launch sequence per family, on the context's own
+    // scratch meshes filled by a real force evaluation of s
+    auto body = [&](int kind) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (kind == 0) {
+            PaintArgs pa = paint_args(ctx, s);
+            pa.mesh = density_ref(ctx);
+            if ((e = launch_paint(PAINT_DENSITY, pa, ctx->stream)) != cudaSuccess) return e;
+            pa = paint_args(ctx, s, s);
+            return launch_paint(PAINT_ADJ, pa, ctx->stream);
+        }
+        if (kind == 1) {
+            ReadArgs ra = read_args(ctx, const_cast<float *>(s));
+            ra.f = f;
+            return launch_read(READ_FORCE, ra, ctx->stream);
+        }
+        if (kind == 2) {
+            if ((e = launch_spectral(SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream)) != cudaSuccess) return e;
+            return launch_spectral(SPEC_ADJ, mesh_spec(ctx), ctx->d_pref, ctx->stream);
+        }
+        if ((e = launch_fft_z_fwd(1, ctx->r1, ctx->spec, ctx->fg, ctx->stream)) != cudaSuccess) return e;
+        if ((e = launch_fft_z_fwd(4, ctx->r4, ctx->spec, ctx->fg, ctx->stream)) != cudaSuccess) return e;
+        if ((e = launch_fft_z_inv(3, ctx->spec, ctx->r4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
+        return launch_fft_z_inv(4, ctx->spec, ctx->r4, ctx->fg, ctx->stream);
+    };
+    const int cand[3] = {128, 256, 512};
+    int best[PM_TUNE_KINDS];
+    for (int k = 0; k < PM_TUNE_KINDS; ++k) best[k] = ctx->tune[k];
+    rc = force_meshes(ctx, s, nullptr);
+    for (int kind = 0; kind < PM_TUNE_KINDS && rc == PM_OK; ++kind) {
+        if (kind == 3 && !(ctx->own && ctx->P.n_m >= 256)) {
+            if (ms) ms[3 * kind] = ms[3 * kind + 1] = ms[3 * kind + 2] = 0.f;
+            continue;
+        }
+        float best_ms = 0.f;
+        for (int c = 0; c < 3 && rc == PM_OK; ++c) {
+            int t[PM_TUNE_KINDS];
+            for (int k = 0; k < PM_TUNE_KINDS; ++k) t[k] = best[k];
+            t[kind] = cand[c];
+            if ((rc = set_tuning(ctx, t)) != PM_OK) break;
+            cudaError_t e = body(kind);  // warm-up (first use of this variant)
+            cudaEventRecord(e0, ctx->stream);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = body(kind);
+            cudaEventRecord(e1, ctx->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                rc = fail(ctx, PM_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+                break;
+            }
+            float t_ms = 0.f;
+            cudaEventElapsedTime(&t_ms, e0, e1);
+            t_ms /= 3.f;
+            if (ms) ms[3 * kind + c] = t_ms;
+            if (c == 0 || t_ms < best_ms) {
+                best_ms = t_ms;
+                best[kind] = cand[c];
+            }
+        }
+    }
+    if (rc == PM_OK) rc = set_tuning(ctx, best);
+    ctx->prof = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(f);
+    return rc;
+}
 
 int pm_use_graphs(pm_ctx *ctx, int enable) {
     if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");

@@ -26,10 +26,10 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
                  : "memory");
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_paint(PaintArgs a) {
+template <int MODE, int T>
+__global__ void __launch_bounds__(T) k_paint(PaintArgs a) {
     const int b = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * T + threadIdx.x;
     if (i >= a.g.npart) return;
     const int64_t gi = ((int64_t)b * a.g.npart + i) * 3;
     const float sx = a.s[gi], sy = a.s[gi + 1], sz = a.s[gi + 2];
@@ -69,10 +69,10 @@ __global__ void __launch_bounds__(kThreads) k_paint(PaintArgs a) {
         }
 }
 
-template <int MODE, bool IL>
-__global__ void __launch_bounds__(kThreads) k_read(ReadArgs a) {
+template <int MODE, bool IL, int T>
+__global__ void __launch_bounds__(T) k_read(ReadArgs a) {
     const int b = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * T + threadIdx.x;
     float red[2] = {0.f, 0.f};
     if (i < a.g.npart) {
         const int64_t gi = ((int64_t)b * a.g.npart + i) * 3;
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kThreads) k_read(ReadArgs a) {
         float s3[3] = {sx, sy, sz};
         finish_read<MODE>(a, b, gi, s3, F, G, mu, red);
     }
-    if (MODE == READ_ADJ) block_sum_to<kThreads, 2>(red, a.red + (int64_t)b * a.red_bstride, a.red2_offset);
+    if (MODE == READ_ADJ) block_sum_to<T, 2>(red, a.red + (int64_t)b * a.red_bstride, a.red2_offset);
 }
 
 // p += K_a f; s += Dr p (the pre-force half of a KDK step), or the reverse
@@ -225,40 +225,58 @@ __global__ void __launch_bounds__(kThreads) k_mse(MeshRef mesh, const float *tar
     }
 }
 
-dim3 particle_grid(const Geom &g) { return dim3((unsigned)((g.npart + kThreads - 1) / kThreads), g.nb); }
+dim3 particle_grid(const Geom &g, int t = kThreads) { return dim3((unsigned)((g.npart + t - 1) / t), g.nb); }
 
-}  // namespace
-
-cudaError_t launch_paint(int mode, const PaintArgs &a, cudaStream_t st) {
-    const dim3 grid = particle_grid(a.g);
-    switch (mode) {
-        case PAINT_DENSITY: k_paint<PAINT_DENSITY><<<grid, kThreads, 0, st>>>(a); break;
-        case PAINT_ADJ: k_paint<PAINT_ADJ><<<grid, kThreads, 0, st>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+template <int T>
+void paint_t(int mode, const PaintArgs &a, cudaStream_t st) {
+    const dim3 grid = particle_grid(a.g, T);
+    if (mode == PAINT_DENSITY)
+        k_paint<PAINT_DENSITY, T><<<grid, T, 0, st>>>(a);
+    else
+        k_paint<PAINT_ADJ, T><<<grid, T, 0, st>>>(a);
 }
 
-template <bool IL>
-void read_il(int mode, const ReadArgs &a, dim3 grid, cudaStream_t st) {
+template <bool IL, int T>
+void read_il(int mode, const ReadArgs &a, cudaStream_t st) {
+    const dim3 grid = particle_grid(a.g, T);
     switch (mode) {
-        case READ_FORCE: k_read<READ_FORCE, IL><<<grid, kThreads, 0, st>>>(a); break;
-        case READ_KICK_DRIFT: k_read<READ_KICK_DRIFT, IL><<<grid, kThreads, 0, st>>>(a); break;
-        case READ_HALF_KICK: k_read<READ_HALF_KICK, IL><<<grid, kThreads, 0, st>>>(a); break;
-        case READ_ADJ: k_read<READ_ADJ, IL><<<grid, kThreads, 0, st>>>(a); break;
+        case READ_FORCE: k_read<READ_FORCE, IL, T><<<grid, T, 0, st>>>(a); break;
+        case READ_KICK_DRIFT: k_read<READ_KICK_DRIFT, IL, T><<<grid, T, 0, st>>>(a); break;
+        case READ_HALF_KICK: k_read<READ_HALF_KICK, IL, T><<<grid, T, 0, st>>>(a); break;
+        case READ_ADJ: k_read<READ_ADJ, IL, T><<<grid, T, 0, st>>>(a); break;
         default: break;
     }
 }
 
+template <int T>
+void read_t(int mode, const ReadArgs &a, cudaStream_t st) {
+    if (a.mesh.il == 4)
+        read_il<true, T>(mode, a, st);
+    else
+        read_il<false, T>(mode, a, st);
+}
+
+}  // namespace
+
+cudaError_t launch_paint(int mode, const PaintArgs &a, cudaStream_t st) {
+    if (mode != PAINT_DENSITY && mode != PAINT_ADJ) return cudaErrorInvalidValue;
+    switch (a.threads) {
+        case 128: paint_t<128>(mode, a, st); break;
+        case 512: paint_t<512>(mode, a, st); break;
+        default: paint_t<256>(mode, a, st); break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_read(int mode, const ReadArgs &a, cudaStream_t st) {
-    const dim3 grid = particle_grid(a.g);
     if (mode == READ_GRAD) {
-        k_read<READ_GRAD, false><<<grid, kThreads, 0, st>>>(a);
+        k_read<READ_GRAD, false, kThreads><<<particle_grid(a.g), kThreads, 0, st>>>(a);
     } else if (mode >= READ_FORCE && mode <= READ_ADJ) {
-        if (a.mesh.il == 4)
-            read_il<true>(mode, a, grid, st);
-        else
-            read_il<false>(mode, a, grid, st);
+        switch (a.threads) {
+            case 128: read_t<128>(mode, a, st); break;
+            case 512: read_t<512>(mode, a, st); break;
+            default: read_t<256>(mode, a, st); break;
+        }
     } else {
         return cudaErrorInvalidValue;
     }

@@ -137,17 +137,18 @@ __device__ __forceinline__ void line_fft_regs(float2 (&v)[L / split1(L)], float2
 
 // --------------------------------------------------------------- z pass ---
 
-template <int N, int G>
+// Z pass of n-point rows, G lines per row, about T threads per block.
+template <int N, int G, int T = 256>
 struct ZShape {
     static constexpr int M = N / 2, TL = split1(M), LP = line_pitch(M);
-    static constexpr int Y = (256 / TL / G) < N ? (256 / TL / G) : N;  // rows per block
+    static constexpr int Y = (T / TL / G) < N ? (T / TL / G) : N;  // rows per block
     static constexpr int LINES = Y * G, THREADS = LINES * TL;
 };
 
 // Forward: G interleaved real fields -> spectrum fields 0 .. G-1.
-template <int N, int G>
-__global__ void __launch_bounds__(256) k_fft_z_fwd(const float *__restrict__ in, float2 *spec, FftGeom fg) {
-    using S = ZShape<N, G>;
+template <int N, int G, int T>
+__global__ void __launch_bounds__(T) k_fft_z_fwd(const float *__restrict__ in, float2 *spec, FftGeom fg) {
+    using S = ZShape<N, G, T>;
     constexpr int M = S::M, TL = S::TL, Y = S::Y, LP = S::LP;
     extern __shared__ float4 smraw[];
     float2 *sm = reinterpret_cast<float2 *>(smraw);
@@ -194,9 +195,9 @@ __global__ void __launch_bounds__(256) k_fft_z_fwd(const float *__restrict__ in,
 
 // Inverse: spectrum fields 0 .. GS-1 -> real mesh with GO interleaved
 // slots per cell (GO = 4: slots >= GS written as 0; GO = 1: plain rows).
-template <int N, int GS, int GO>
-__global__ void __launch_bounds__(256) k_fft_z_inv(const float2 *__restrict__ spec, float *out, FftGeom fg) {
-    using S = ZShape<N, GO>;
+template <int N, int GS, int GO, int T>
+__global__ void __launch_bounds__(T) k_fft_z_inv(const float2 *__restrict__ spec, float *out, FftGeom fg) {
+    using S = ZShape<N, GO, T>;
     constexpr int M = S::M, TL = S::TL, Y = S::Y, LP = S::LP;
     extern __shared__ float4 smraw[];
     float2 *sm = reinterpret_cast<float2 *>(smraw);
@@ -304,27 +305,44 @@ __global__ void __launch_bounds__(PencilShape<L>::THREADS, 2) k_fft_pencil(float
     }
 }
 
-template <int N, int G>
-cudaError_t z_fwd_n(const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {
-    using S = ZShape<N, G>;
+template <int N, int G, int T>
+cudaError_t z_fwd_t(const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {
+    using S = ZShape<N, G, T>;
     const size_t smem = sizeof(float2) * S::LINES * S::LP;
-    cudaError_t e = cudaFuncSetAttribute(k_fft_z_fwd<N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fft_z_fwd<N, G, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)fg.nb * N * (N / S::Y);
-    k_fft_z_fwd<N, G><<<(unsigned)blocks, S::THREADS, smem, st>>>(in, spec, fg);
+    k_fft_z_fwd<N, G, T><<<(unsigned)blocks, S::THREADS, smem, st>>>(in, spec, fg);
     return cudaGetLastError();
+}
+
+template <int N, int GS, int GO, int T>
+cudaError_t z_inv_t(const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st) {
+    using S = ZShape<N, GO, T>;
+    const size_t smem = sizeof(float2) * S::LINES * S::LP;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fft_z_inv<N, GS, GO, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (int64_t)fg.nb * N * (N / S::Y);
+    k_fft_z_inv<N, GS, GO, T><<<(unsigned)blocks, S::THREADS, smem, st>>>(spec, out, fg);
+    return cudaGetLastError();
+}
+
+// Block-size variants (the autotuner's choice) only where rows are long
+// enough for them to differ: n >= 256.
+template <int N, int G>
+cudaError_t z_fwd_n(const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {
+    if (N >= 256 && fg.zthreads == 128) return z_fwd_t<N, G, (N >= 256 ? 128 : 256)>(in, spec, fg, st);
+    if (N >= 256 && fg.zthreads == 512) return z_fwd_t<N, G, (N >= 256 ? 512 : 256)>(in, spec, fg, st);
+    return z_fwd_t<N, G, 256>(in, spec, fg, st);
 }
 
 template <int N, int GS, int GO>
 cudaError_t z_inv_n(const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st) {
-    using S = ZShape<N, GO>;
-    const size_t smem = sizeof(float2) * S::LINES * S::LP;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_fft_z_inv<N, GS, GO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = (int64_t)fg.nb * N * (N / S::Y);
-    k_fft_z_inv<N, GS, GO><<<(unsigned)blocks, S::THREADS, smem, st>>>(spec, out, fg);
-    return cudaGetLastError();
+    if (N >= 256 && fg.zthreads == 128) return z_inv_t<N, GS, GO, (N >= 256 ? 128 : 256)>(spec, out, fg, st);
+    if (N >= 256 && fg.zthreads == 512) return z_inv_t<N, GS, GO, (N >= 256 ? 512 : 256)>(spec, out, fg, st);
+    return z_inv_t<N, GS, GO, 256>(spec, out, fg, st);
 }
 
 template <int L, bool INV>

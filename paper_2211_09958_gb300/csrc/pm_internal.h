@@ -75,6 +75,7 @@ struct PaintArgs {
     const float *s;
     const float *mu;
     MeshRef mesh;
+    int threads;  // block size: 128, 256 (also for 0) or 512 (autotuned)
 };
 
 // Particle-local work that precedes a force evaluation.
@@ -112,6 +113,7 @@ struct ReadArgs {
     double *red;          // kick reduction (batch stride red_bstride)
     int red_bstride;
     int red2_offset;      // drift reduction at red + red2_offset (0 when no drift)
+    int threads;          // block size: 128, 256 (also for 0) or 512 (autotuned)
 };
 
 cudaError_t launch_paint(int mode, const PaintArgs &a, cudaStream_t st);
@@ -135,6 +137,7 @@ struct Spec {
     int zc;
     int blk;
     const float *grad;  // [n] 4-point difference gradient D(k) per axis index (force kernels)
+    int threads;        // force-kernel block size: 128, 256 (also for 0) or 512 (autotuned)
 };
 
 // The library's own FFT (fft_kernels.cu): spectra [field][run][kz/8][x][y][kz%8].
@@ -142,6 +145,7 @@ struct FftGeom {
     int n, nb, zc;
     int64_t fstride;    // complex elements per spectrum field (all runs)
     const float2 *tw;   // W_1024^j, j < 1024
+    int zthreads;       // z-pass block size for n >= 256: 128, 256 (also for 0) or 512 (autotuned)
 };
 
 struct PencilGeom {

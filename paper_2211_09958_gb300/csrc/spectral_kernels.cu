@@ -45,11 +45,12 @@ __device__ __forceinline__ int signed_index(int j, int n) { return j < n / 2 ? j
 
 __device__ __forceinline__ float2 times_i(float2 v, float s) { return make_float2(-s * v.y, s * v.x); }
 
-__global__ void __launch_bounds__(kThreads) k_spec_force(Spec sp, const float *pref) {
+template <int T>
+__global__ void __launch_bounds__(T) k_spec_force(Spec sp, const float *pref) {
     const int b = blockIdx.y;
     const int n = sp.n;
     const int64_t nmodes = (int64_t)n * n * sp.zc;
-    const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t m = (int64_t)blockIdx.x * T + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
     mode_ijk(m, n, sp.zc, sp.blk, ix, iy, iz);
@@ -64,11 +65,12 @@ __global__ void __launch_bounds__(kThreads) k_spec_force(Spec sp, const float *p
     c0[2 * sp.fstride] = times_i(d, __ldg(sp.grad + iz) * g);
 }
 
-__global__ void __launch_bounds__(kThreads) k_spec_adj(Spec sp, const float *pref) {
+template <int T>
+__global__ void __launch_bounds__(T) k_spec_adj(Spec sp, const float *pref) {
     const int b = blockIdx.y;
     const int n = sp.n;
     const int64_t nmodes = (int64_t)n * n * sp.zc;
-    const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t m = (int64_t)blockIdx.x * T + threadIdx.x;
     if (m >= nmodes) return;
     int ix, iy, iz;
     mode_ijk(m, n, sp.zc, sp.blk, ix, iy, iz);
@@ -417,6 +419,16 @@ __global__ void __launch_bounds__(kThreads) k_lpt_adj_final(Spec sp, const LinPa
     }
 }
 
+template <int T>
+void spectral_t(int mode, const Spec &sp, const float *pref, cudaStream_t st) {
+    const int64_t nmodes = (int64_t)sp.n * sp.n * sp.zc;
+    const dim3 grid((unsigned)((nmodes + T - 1) / T), sp.nb);
+    if (mode == SPEC_FORCE)
+        k_spec_force<T><<<grid, T, 0, st>>>(sp, pref);
+    else
+        k_spec_adj<T><<<grid, T, 0, st>>>(sp, pref);
+}
+
 dim3 mode_grid(const Spec &sp) {
     const int64_t nmodes = (int64_t)sp.n * sp.n * sp.zc;
     return dim3((unsigned)((nmodes + kThreads - 1) / kThreads), sp.nb);
@@ -431,10 +443,11 @@ dim3 site_grid(int np, int nb) {
 }  // namespace
 
 cudaError_t launch_spectral(int mode, const Spec &sp, const float *pref, cudaStream_t st) {
-    if (mode == SPEC_FORCE)
-        k_spec_force<<<mode_grid(sp), kThreads, 0, st>>>(sp, pref);
-    else
-        k_spec_adj<<<mode_grid(sp), kThreads, 0, st>>>(sp, pref);
+    switch (sp.threads) {
+        case 128: spectral_t<128>(mode, sp, pref, st); break;
+        case 512: spectral_t<512>(mode, sp, pref, st); break;
+        default: spectral_t<256>(mode, sp, pref, st); break;
+    }
     return cudaGetLastError();
 }
 

@@ -215,6 +215,26 @@ class ParticleMesh:
                    ctypes.c_int64(step), int(bool(apply)), ctypes.byref(loss))
         return loss.value
 
+    # ------------------------------------------------------- autotuner --
+    TUNE_FAMILIES = ("paint", "read", "spectral", "fft_z")
+
+    def autotune(self, s):
+        """Pick the fastest block size per kernel family on particles s;
+        returns (chosen {family: threads}, times [family][128, 256, 512] ms)."""
+        self._particles(s, "s")
+        ms = np.zeros((4, 3), np.float32)
+        self._call("pm_autotune", _ptr(s), ms.ctypes.data_as(ctypes.c_void_p))
+        return self.get_tuning(), ms
+
+    def get_tuning(self):
+        t = np.zeros(4, np.int32)
+        self._call("pm_get_tuning", t.ctypes.data_as(ctypes.c_void_p))
+        return dict(zip(self.TUNE_FAMILIES, (int(v) for v in t)))
+
+    def set_tuning(self, paint=256, read=256, spectral=256, fft_z=256):
+        t = np.array([paint, read, spectral, fft_z], np.int32)
+        self._call("pm_set_tuning", t.ctypes.data_as(ctypes.c_void_p))
+
     def use_graphs(self, enable=True):
         """Replay pm_integrate / pm_adjoint_integrate from captured CUDA graphs."""
         self._call("pm_use_graphs", int(bool(enable)))

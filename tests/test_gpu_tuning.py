@@ -1,0 +1,65 @@
+"""Launch-shape autotuner (include/pmgb.h pm_autotune / pm_set_tuning):
+every candidate block size gives the same results (up to the order of FP32
+atomics), and the tuner keeps the fastest candidate it measured."""
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2211_09958_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FAMILIES = ("paint", "read", "spectral", "fft_z")
+
+
+def _pm(n_p=32, n_m=256, box=128.0, steps=3):
+    from paper_2211_09958_gb300.pm import ParticleMesh
+    return ParticleMesh(n_p, n_m, box, 0.3, 0.8, steps)
+
+
+def test_every_block_size_gives_the_same_force_and_trajectory():
+    pm = _pm()
+    s0 = torch.from_numpy(inputs.random_displacements(32, 128.0, seed=2, scale=0.5)).cuda()[None]
+    ref_f = pm.pm_force(s0)
+    s, p = pm.init_lpt(seed=5)
+    ref_s, ref_p = s.clone(), p.clone()
+    pm.integrate(ref_s, ref_p)
+    scale_f = ref_f.abs().max().item()
+    for fam in FAMILIES:
+        for t in (128, 512):
+            pm.set_tuning(**{fam: t})
+            f = pm.pm_force(s0)
+            assert (f - ref_f).abs().max().item() <= 2e-5 * scale_f, (fam, t)
+            s2, p2 = s.clone(), p.clone()
+            pm.integrate(s2, p2)
+            assert (s2 - ref_s).abs().max().item() <= 1e-5 * pm.box / pm.n_p, (fam, t)
+            pm.set_tuning()
+    assert pm.get_tuning() == dict.fromkeys(FAMILIES, 256)
+
+
+def test_autotune_keeps_the_fastest_measured_candidate():
+    pm = _pm()
+    s, _ = pm.init_lpt(seed=3)
+    before = s.clone()
+    chosen, ms = pm.autotune(s)
+    assert torch.equal(s, before)                    # the particles are not modified
+    cands = (128, 256, 512)
+    for k, fam in enumerate(FAMILIES):
+        assert np.all(ms[k] > 0), (fam, ms[k])
+        assert chosen[fam] == cands[int(np.argmin(ms[k]))], (fam, ms[k], chosen)
+
+
+def test_small_mesh_keeps_the_default_z_pass():
+    pm = _pm(n_p=16, n_m=64, box=64.0)
+    s, _ = pm.init_lpt(seed=1)
+    chosen, ms = pm.autotune(s)
+    assert chosen["fft_z"] == 256 and np.all(ms[3] == 0)
+
+
+def test_invalid_block_size_is_rejected():
+    from paper_2211_09958_gb300.pm import PMError
+    pm = _pm(n_p=16, n_m=64, box=64.0)
+    with pytest.raises(PMError):
+        pm.set_tuning(paint=100)
+    assert pm.get_tuning()["paint"] == 256
