@@ -11,6 +11,10 @@ adjoint together (also reported separately).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload NAME] [--sim-steps S]
 
+--workload learned_pm128_mesh128 trains the learned force correction on
+reference runs first (untimed), reports its P(k) gain, then times the
+corrected forward integration.
+
 With N > 1 (under torchrun) every rank runs an independent replica (the
 path does not shard; no data-path collective), value = all ranks' work /
 max time.  --impl reference times the FP64 CPU oracle instead.
@@ -33,6 +37,8 @@ sys.path.insert(0, ROOT)
 from paper_2211_09958_gb300.configs import WORKLOADS  # noqa: E402
 
 METRIC = "particle-steps/s (fwd+adjoint) at 512³"
+LEARNED_WORKLOAD = "learned_pm128_mesh128"
+LEARNED_METRIC = "particle-steps/s (learned-correction PM forward) at 128³ on a 128³ mesh"
 UNIT = "particle-steps/s"
 DEFAULT_WORKLOAD = "pm512_mesh1024"
 ORACLE_SAMPLE = dict(n_p=64, n_m=128, box=125.0, n_steps=1)
@@ -191,6 +197,30 @@ def oracle_sample(seed=0):
     return {"value": work / (t2 - t0), "fwd_s": t1 - t0, "adj_s": t2 - t1, "seconds": t2 - t0}
 
 
+LEARNED_SAMPLE = dict(n_p=64, n_m=64, box=128.0)
+LEARNED_SAMPLE_TEXT = ("FP64 oracle (numpy + scipy.fft), one corrected force evaluation (PM force + per-cell MLP "
+                       "correction, bf16 rounding points) for 64^3 particles on a 64^3 mesh, 128 Mpc/h (the "
+                       "learned workload's resolution at 1/8 of its particles); particle-steps/s of that sample")
+
+
+def oracle_learned_sample(seed=0):
+    """Time the FP64 oracle's corrected force (PM force + network
+    correction) on a bounded sample of the learned workload's resolution."""
+    from oracle import learned as olearned
+    from oracle import pm as opm
+    from oracle.cosmology import Cosmology
+    from paper_2211_09958_gb300 import inputs
+
+    smp = LEARNED_SAMPLE
+    st = opm.Setup(smp["n_p"], smp["n_m"], smp["box"], Cosmology(0.3, 0.8))
+    s = inputs.random_displacements(st.n_p, st.box, seed, scale=0.5).astype(np.float64)
+    theta = inputs.mlp_params((32, 128, 128, 3), seed=seed).astype(np.float64)
+    t0 = time.perf_counter()
+    opm.force(s, st) + olearned.predict(s, 0.5, theta, st)
+    dt = time.perf_counter() - t0
+    return {"value": st.n_p ** 3 / dt, "seconds": dt}
+
+
 def _cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -208,20 +238,24 @@ def run_reference(args):
     if world > 1 and rank != 0:
         return 0
     w = WORKLOADS[args.workload]
+    learned = w.name == LEARNED_WORKLOAD
+    sample_fn = oracle_learned_sample if learned else oracle_sample
     for _ in range(args.warmup):
-        oracle_sample()
+        sample_fn()
     times, vals = [], []
     for k in range(args.steps):
-        r = oracle_sample(seed=k)
+        r = sample_fn(seed=k)
         times.append(r["seconds"])
         vals.append(r["value"])
     value = float(np.mean(vals))
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": LEARNED_METRIC if learned else METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "sample": ORACLE_SAMPLE},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": SAMPLE_TEXT},
+        "config": {"workload": w.name, "sample": LEARNED_SAMPLE if learned else ORACLE_SAMPLE},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                         "sample": LEARNED_SAMPLE_TEXT if learned else SAMPLE_TEXT},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -389,6 +423,144 @@ def run_ours(args):
     return 0
 
 
+def run_learned(args):
+    """The learned-correction workload: train the network on reference runs
+    (untimed), judge its P(k) gain, then time the corrected forward
+    integration of a batch of 4 runs (2LPT + 40 corrected KDK steps)."""
+    rank, local_rank, world = _dist_env()
+    w = WORKLOADS[args.workload]
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = {"value": float(np.mean([oracle_learned_sample(seed=k)["value"] for k in range(2)]))}
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2211_09958_gb300 import learn
+
+    st = learn.LearnedSetup(n_p=w.n_p, n_m=w.n_m, box=w.box, n_steps=w.n_steps, group=4)
+    t0 = time.perf_counter()
+    seeds = list(range(100 + 1000 * rank, 100 + 1000 * rank + args.learn_runs))
+    theta, log = learn.train(st, seeds, epochs=args.learn_epochs, lr=1e-3, lr_final=1e-4)
+    train_s = time.perf_counter() - t0
+    ev = learn.evaluate(st, theta, [90000 + 4 * rank + j for j in range(4)])
+
+    pm = st.coarse()
+    pm.nn_set_params(theta)
+    pm.nn_enable(True)
+    dev = pm.device
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.ic_seed + 7919 * rank)
+    noise = torch.randn((pm.n_batch, w.n_p, w.n_p, w.n_p), generator=gen, device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+    tuning = pm.get_tuning()
+    if not args.no_autotune:
+        s_t, _ = pm.init_lpt(noise)
+        tuning, _ = pm.autotune(s_t)
+        del s_t
+
+    def hot_path(nz):
+        s, p = pm.init_lpt(nz)
+        pm.integrate(s, p)
+        return s
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        hot_path(noise)
+    barrier()
+    lib = pm._lib
+    lib.pm_profile(pm._ctx, 1)
+    lib.pm_profile_read(pm._ctx, None, None, 0)
+    launches0 = pm.launch_count()
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        barrier()
+        for k in range(args.steps):
+            ev_a[k].record(stream)
+            hot_path(noise)
+            ev_b[k].record(stream)
+        barrier()
+    launches = pm.launch_count() - launches0
+    import ctypes
+    nk = lib.pm_profile_kinds(pm._ctx)
+    counts = (ctypes.c_int64 * nk)()
+    kms = (ctypes.c_double * nk)()
+    lib.pm_profile_read(pm._ctx, counts, kms, nk)
+    lib.pm_profile(pm._ctx, 0)
+    kernels = {lib.pm_profile_name(pm._ctx, i).decode(): (int(counts[i]), float(kms[i])) for i in range(nk)}
+    total_ms = float(sum(a.elapsed_time(b) for a, b in zip(ev_a, ev_b)))
+
+    # end to end: noise from pinned host memory in, final displacements out
+    h_noise = noise.cpu().pin_memory()
+    h_s = torch.empty((pm.n_batch, pm.n_part, 3), dtype=torch.float32).pin_memory()
+    hot_path(h_noise.to(dev, non_blocking=True))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        h_s.copy_(hot_path(h_noise.to(dev, non_blocking=True)), non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+
+    work = pm.n_batch * w.n_p ** 3 * w.n_steps
+    t_max, e2e_max = total_ms, e2e_ms
+    if dist is not None:
+        t = torch.tensor([total_ms, e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, e2e_max = float(t[0]), float(t[1])
+    value = world * work * args.steps / (t_max / 1e3)
+    if rank == 0:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        peak = float(d.get("bf16_tflops_sustained", 1700.0))
+        cells = pm.n_batch * w.n_m ** 3
+        flops = 2.0 * (32 * 128 + 128 * 128 + 128 * 3) * cells     # algorithmic MLP flops per evaluation
+        cnt, ms = kernels.get("nn_fwd_tc", (0, 0.0))
+        achieved = flops / (ms / cnt / 1e3) / 1e12 if cnt else None
+        table = {k: {"launches": c, "total_ms": round(m, 3), "share": round(m / total_ms, 4)}
+                 for k, (c, m) in kernels.items()}
+        line = {
+            "metric": LEARNED_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "config": {"workload": w.name, "n_p": w.n_p, "n_m": w.n_m, "box_mpc_h": w.box, "n_steps": w.n_steps,
+                       "n_batch": pm.n_batch, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "mesh and particle working set > L2 per step (4 x 128^3 x 16 B meshes)",
+                       "tuning": tuning},
+            "roofline": {"bound": "tensor", "kernel": "nn_fwd_tc", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+                         "peak_source": "measured (bf16, sustained)",
+                         "algorithmic_flops_per_launch": flops, "traffic": None},
+            "learned": {
+                "train_runs": args.learn_runs, "epochs": args.learn_epochs, "train_seconds": round(train_s, 1),
+                "k_cut_h_per_mpc": ev["k_cut"],
+                "pk_max_abs_rel_err": {k: ev[k]["max_abs_rel_err"] for k in ("plain", "corrected", "plain_2x")},
+                "particle_steps_per_s": {k: ev[k]["particle_steps_per_s"] for k in ("plain", "corrected", "plain_2x")},
+                "reference": "PM on a 4x finer mesh with 4x the steps, same 2LPT start",
+            },
+            "kernels": table,
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(),
+            "e2e": {"value": world * work * args.steps / (e2e_max / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(h_noise.numel() * 4), "d2h_bytes_per_step": int(h_s.numel() * 4)},
+            "cpu_baseline": None if cpu is None else {
+                "value": cpu["value"], "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": LEARNED_SAMPLE_TEXT},
+        }
+        print(json.dumps(line))
+    pm.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,9 +571,13 @@ def main():
     ap.add_argument("--sim-steps", type=int, default=0, help="override the number of KDK steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--learn-runs", type=int, default=32, help="reference runs the correction trains on")
+    ap.add_argument("--learn-epochs", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == LEARNED_WORKLOAD:
+        return run_learned(args)
     return run_ours(args)
 
 
