@@ -17,10 +17,11 @@
 // X_k = sum_n x_n e^{-2 pi i k n / n}, inverse without 1/n.  The spectral
 // kernels apply the 1/n^3.
 //
-// A line of L = M1 * M2 complex points is transformed by the four-step
-// method: M1 threads each do an M2-point FFT in registers on a stride-M1
-// subsequence, multiply by W_L^{n1 k2}, exchange through shared memory (pitch
-// M2 + 1 to spread banks), and M2 threads each do an M1-point FFT.  The
+// A line of L = M1 * M2 complex points (M1 <= M2, both powers of two) is
+// transformed by the four-step method: M1 threads each do an M2-point FFT in
+// registers on a stride-M1 subsequence, multiply by W_L^{n1 k2}, exchange
+// through shared memory (pitch M2 + 1 to spread banks), and each thread then
+// does M2 / M1 of the M2 M1-point FFTs, so that no thread idles.  The
 // register FFTs are radix-2 decimation in frequency (bit-reversed output),
 // fully unrolled.  Twiddles come from a table of W_1024^j computed in double
 // precision on the host; the 32 register-FFT twiddles sit in constant memory.
@@ -47,9 +48,11 @@ __host__ __device__ constexpr int bitrev(int k, int bits) {
     for (int i = 0; i < bits; ++i) r = (r << 1) | ((k >> i) & 1);
     return r;
 }
-// L = split1(L) * (L / split1(L)), split1(L) >= L / split1(L), both <= 32.
-__host__ __device__ constexpr int split1(int l) { return 1 << ((ilog2(l) + 1) / 2); }
-__host__ __device__ constexpr int line_pitch(int l) { return l + split1(l) + 2; }  // >= M1 (M2 + 1), even
+// L = lsplit(L) * msplit(L): lsplit(L) <= msplit(L) <= 32, lsplit the number
+// of threads per line.
+__host__ __device__ constexpr int msplit(int l) { return 1 << ((ilog2(l) + 1) / 2); }
+__host__ __device__ constexpr int lsplit(int l) { return l / msplit(l); }
+__host__ __device__ constexpr int line_pitch(int l) { return l + msplit(l) + 2; }  // >= M1 (M2 + 1), even
 
 // In-register radix-2 DIF FFT of R <= 32 points; v[i] ends as X[bitrev(i)].
 template <int R, bool INV>
@@ -75,16 +78,15 @@ __device__ __forceinline__ void reg_fft(float2 (&v)[R]) {
     }
 }
 
-// Four-step FFT of one line of L = M1 * M2 points held in shared memory
-// (pitch >= M1 (M2 + 1)), by the M1 threads t = 0 .. M1-1 of one warp (or
-// sub-warp).  Every lane of the warp must call it (it uses __syncwarp).
+// Steps 2-4 of the four-step FFT once thread t holds its M2 points
+// v[n2] = x[t + M1 n2]: transform, twiddle, exchange through `line`
+// (pitch >= M1 (M2 + 1)), then the M1-point transforms of columns
+// c = t, t + M1, ...; the result X[k] lands in line[k] (natural order).
+// Every lane of the warp must call it (it uses __syncwarp).
 template <int L, bool INV>
-__device__ __forceinline__ void line_fft(float2 *line, int t, const float2 *__restrict__ tw) {
-    constexpr int M1 = split1(L), M2 = L / M1;
-    float2 v[M2];
-#pragma unroll
-    for (int n2 = 0; n2 < M2; ++n2) v[n2] = line[t + M1 * n2];
-    __syncwarp();
+__device__ __forceinline__ void line_fft_regs(float2 (&v)[msplit(L)], float2 *line, int t,
+                                              const float2 *__restrict__ tw) {
+    constexpr int M1 = lsplit(L), M2 = msplit(L);
     reg_fft<M2, INV>(v);
 #pragma unroll
     for (int k2 = 0; k2 < M2; ++k2) {
@@ -93,46 +95,31 @@ __device__ __forceinline__ void line_fft(float2 *line, int t, const float2 *__re
         line[t * (M2 + 1) + k2] = cmul(v[bitrev(k2, ilog2(M2))], w);
     }
     __syncwarp();
-    float2 u[M1];
-    if (t < M2) {
+    float2 u[M2 / M1][M1];
 #pragma unroll
-        for (int n1 = 0; n1 < M1; ++n1) u[n1] = line[n1 * (M2 + 1) + t];
-    }
+    for (int j = 0; j < M2 / M1; ++j)
+#pragma unroll
+        for (int n1 = 0; n1 < M1; ++n1) u[j][n1] = line[n1 * (M2 + 1) + t + M1 * j];
     __syncwarp();
-    if (t < M2) {
-        reg_fft<M1, INV>(u);
 #pragma unroll
-        for (int k1 = 0; k1 < M1; ++k1) line[t + M2 * k1] = u[bitrev(k1, ilog2(M1))];
+    for (int j = 0; j < M2 / M1; ++j) {
+        reg_fft<M1, INV>(u[j]);
+#pragma unroll
+        for (int k1 = 0; k1 < M1; ++k1) line[t + M1 * j + M2 * k1] = u[j][bitrev(k1, ilog2(M1))];
     }
     __syncwarp();
 }
 
-// Same as line_fft, but step 1 starts from the M2 points v[n2] = line[t + M1 n2]
-// already in registers (loaded by the caller from global memory).
+// Four-step FFT of one line of L points held in shared memory, by the M1
+// threads t = 0 .. M1-1 of one warp (or sub-warp).
 template <int L, bool INV>
-__device__ __forceinline__ void line_fft_regs(float2 (&v)[L / split1(L)], float2 *line, int t,
-                                              const float2 *__restrict__ tw) {
-    constexpr int M1 = split1(L), M2 = L / M1;
-    reg_fft<M2, INV>(v);
+__device__ __forceinline__ void line_fft(float2 *line, int t, const float2 *__restrict__ tw) {
+    constexpr int M1 = lsplit(L), M2 = msplit(L);
+    float2 v[M2];
 #pragma unroll
-    for (int k2 = 0; k2 < M2; ++k2) {
-        float2 w = __ldg(tw + t * k2 * (1024 / L));
-        if (INV) w.y = -w.y;
-        line[t * (M2 + 1) + k2] = cmul(v[bitrev(k2, ilog2(M2))], w);
-    }
+    for (int n2 = 0; n2 < M2; ++n2) v[n2] = line[t + M1 * n2];
     __syncwarp();
-    float2 u[M1];
-    if (t < M2) {
-#pragma unroll
-        for (int n1 = 0; n1 < M1; ++n1) u[n1] = line[n1 * (M2 + 1) + t];
-    }
-    __syncwarp();
-    if (t < M2) {
-        reg_fft<M1, INV>(u);
-#pragma unroll
-        for (int k1 = 0; k1 < M1; ++k1) line[t + M2 * k1] = u[bitrev(k1, ilog2(M1))];
-    }
-    __syncwarp();
+    line_fft_regs<L, INV>(v, line, t, tw);
 }
 
 // --------------------------------------------------------------- z pass ---
@@ -140,7 +127,7 @@ __device__ __forceinline__ void line_fft_regs(float2 (&v)[L / split1(L)], float2
 // Z pass of n-point rows, G lines per row, about T threads per block.
 template <int N, int G, int T = 256>
 struct ZShape {
-    static constexpr int M = N / 2, TL = split1(M), LP = line_pitch(M);
+    static constexpr int M = N / 2, TL = lsplit(M), LP = line_pitch(M);
     static constexpr int Y = (T / TL / G) < N ? (T / TL / G) : N;  // rows per block
     static constexpr int LINES = Y * G, THREADS = LINES * TL;
 };
@@ -160,7 +147,7 @@ __global__ void __launch_bounds__(T) k_fft_z_fwd(const float *__restrict__ in, f
     {
         // point n of line (row y0 + yl, field g) is the complex pair of reals
         // (2n, 2n + 1), i.e. floats G (2n) + g and G (2n + 1) + g of the row
-        constexpr int M1 = split1(M), M2 = M / M1;
+        constexpr int M1 = lsplit(M), M2 = msplit(M);
         const float *row = in + ((bx * N + y0 + yl) * (int64_t)N) * G + g;
         float2 v[M2];
 #pragma unroll
@@ -211,7 +198,7 @@ __global__ void __launch_bounds__(T) k_fft_z_inv(const float2 *__restrict__ spec
         // built from the half-spectrum pair (X_k, X_{M-k}):
         //   Z_k = (X_k + conj X_{M-k}) + i (X_k - conj X_{M-k}) W_N^{-k}
         // (imaginary parts of X_0 and X_M taken as zero)
-        constexpr int M1 = split1(M), M2 = M / M1;
+        constexpr int M1 = lsplit(M), M2 = msplit(M);
         float2 v[M2];
         if (g < GS) {
             const int64_t run = bx / N, xx = bx % N;
@@ -261,10 +248,11 @@ constexpr int kPencil = 8;
 // column w straight into registers (a warp covers 4 rows x 64 bytes per
 // load), transforms them and writes the twiddled result to the exchange
 // buffer [n1][k2][w] (n1 pitch M2*8 + 8 keeps half-warps on distinct banks);
-// step 3: thread (k2, w) transforms over n1 and stores straight to global.
+// step 3: thread (r, w) transforms columns k2 = r, r + M1, ... over n1 and
+// stores straight to global (M1 <= M2, so every thread has work).
 template <int L>
 struct PencilShape {
-    static constexpr int M1 = split1(L), M2 = L / M1, THREADS = M1 * kPencil, YP = M2 * kPencil + kPencil;
+    static constexpr int M1 = lsplit(L), M2 = msplit(L), THREADS = M1 * kPencil, YP = M2 * kPencil + kPencil;
     static constexpr int SMEM = M1 * YP;  // complex elements
 };
 
@@ -294,8 +282,9 @@ __global__ void __launch_bounds__(PencilShape<L>::THREADS, 2) k_fft_pencil(float
         }
     }
     __syncthreads();
-    const int k2 = r;
-    if (k2 < M2) {
+#pragma unroll
+    for (int j = 0; j < M2 / M1; ++j) {
+        const int k2 = r + M1 * j;
         float2 u[M1];
 #pragma unroll
         for (int n1 = 0; n1 < M1; ++n1) u[n1] = ys[n1 * YP + k2 * W + w];
