@@ -256,7 +256,9 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
 /* Launch-shape autotuner.  Four kernel families have a tunable block size
  * (128, 256 or 512 threads): [0] CIC paint, [1] CIC read, [2] spectral
  * force / adjoint multiply, [3] z-pass FFT (own transform, n_m >= 256; other
- * meshes keep 256).  Defaults are 256.
+ * meshes keep 256); defaults 256.  [4] is the x-pass FFT pencil width in
+ * complex columns, 8 or 16 (16: two adjacent y rows of 8 kz, 128 contiguous
+ * bytes per x row; own transform only); default 8.
  *
  * pm_autotune     times every candidate of each family in turn (the others
  *                 held at their current best) on this context's scratch
@@ -264,12 +266,12 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  *                 (device [n_batch][n_p^3][3], not modified), 3 launches
  *                 after a warm-up, CUDA events on the context stream; keeps
  *                 the fastest.  ms (host, may be NULL) receives the mean
- *                 time in ms of each candidate, [family][128, 256, 512]
- *                 (0 where not timed).  Synchronises the stream.
- * pm_set_tuning   set the four block sizes explicitly (PM_EINVAL otherwise)
- * pm_get_tuning   read them (host int[4])
+ *                 time in ms of each candidate, [family][3] in the order
+ *                 above (0 where not timed).  Synchronises the stream.
+ * pm_set_tuning   set all five explicitly (PM_EINVAL for other values)
+ * pm_get_tuning   read them (host int[PM_TUNE_KINDS])
  * Results do not depend on the choice beyond the order of FP32 atomics. */
-#define PM_TUNE_KINDS 4
+#define PM_TUNE_KINDS 5
 int pm_autotune(pm_ctx *ctx, const float *s, float *ms);
 int pm_set_tuning(pm_ctx *ctx, const int *threads);
 int pm_get_tuning(pm_ctx *ctx, int *threads);

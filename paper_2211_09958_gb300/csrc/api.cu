@@ -73,9 +73,9 @@ struct pm_ctx {
         int64_t launches;
     };
     std::vector<GraphEntry> graphs;
-    // launch shapes (block sizes) of the tunable kernel families:
-    // paint, read, spectral force/adjoint, z-pass FFT (n >= 256)
-    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256};
+    // launch shapes of the tunable kernel families: block sizes of paint,
+    // read, spectral force/adjoint, z-pass FFT (n >= 256); x-pass pencil width
+    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8};
     // learned force correction (own-FFT meshes only)
     bool nn_on = false;
     void *nn_packed = nullptr;
@@ -604,11 +604,15 @@ const char *pm_last_error(const pm_ctx *ctx) { return ctx ? ctx->err.c_str() : g
 
 int64_t pm_launch_count(const pm_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+const int kTuneCand[PM_TUNE_KINDS][3] = {{128, 256, 512}, {128, 256, 512}, {128, 256, 512}, {128, 256, 512}, {8, 16, 0}};
+
 static int set_tuning(pm_ctx *ctx, const int *t) {
     for (int k = 0; k < PM_TUNE_KINDS; ++k)
-        if (t[k] != 128 && t[k] != 256 && t[k] != 512) return fail(ctx, PM_EINVAL, "block sizes must be 128, 256 or 512");
+        if (t[k] <= 0 || (t[k] != kTuneCand[k][0] && t[k] != kTuneCand[k][1] && t[k] != kTuneCand[k][2]))
+            return fail(ctx, PM_EINVAL, "block sizes must be 128, 256 or 512 and the x-pass width 8 or 16");
     for (int k = 0; k < PM_TUNE_KINDS; ++k) ctx->tune[k] = t[k];
     ctx->fg.zthreads = ctx->tune[3];
+    ctx->fg.xwidth = ctx->tune[4];
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);  // captured with the old shapes
     ctx->graphs.clear();
     return PM_OK;
@@ -662,25 +666,29 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
             if ((e = launch_spectral(SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream)) != cudaSuccess) return e;
             return launch_spectral(SPEC_ADJ, mesh_spec(ctx), ctx->d_pref, ctx->stream);
         }
+        if (kind == 4) {
+            if ((e = launch_fft_pencils(0, false, ctx->spec, 0, 4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
+            return launch_fft_pencils(0, true, ctx->spec, 0, 4, ctx->fg, ctx->stream);
+        }
         if ((e = launch_fft_z_fwd(1, ctx->r1, ctx->spec, ctx->fg, ctx->stream)) != cudaSuccess) return e;
         if ((e = launch_fft_z_fwd(4, ctx->r4, ctx->spec, ctx->fg, ctx->stream)) != cudaSuccess) return e;
         if ((e = launch_fft_z_inv(3, ctx->spec, ctx->r4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
         return launch_fft_z_inv(4, ctx->spec, ctx->r4, ctx->fg, ctx->stream);
     };
-    const int cand[3] = {128, 256, 512};
     int best[PM_TUNE_KINDS];
     for (int k = 0; k < PM_TUNE_KINDS; ++k) best[k] = ctx->tune[k];
     rc = force_meshes(ctx, s, nullptr);
     for (int kind = 0; kind < PM_TUNE_KINDS && rc == PM_OK; ++kind) {
-        if (kind == 3 && !(ctx->own && ctx->P.n_m >= 256)) {
+        if ((kind == 3 && !(ctx->own && ctx->P.n_m >= 256)) || (kind == 4 && !ctx->own)) {
             if (ms) ms[3 * kind] = ms[3 * kind + 1] = ms[3 * kind + 2] = 0.f;
             continue;
         }
         float best_ms = 0.f;
-        for (int c = 0; c < 3 && rc == PM_OK; ++c) {
+        if (ms) ms[3 * kind + 2] = 0.f;
+        for (int c = 0; c < 3 && rc == PM_OK && kTuneCand[kind][c]; ++c) {
             int t[PM_TUNE_KINDS];
             for (int k = 0; k < PM_TUNE_KINDS; ++k) t[k] = best[k];
-            t[kind] = cand[c];
+            t[kind] = kTuneCand[kind][c];
             if ((rc = set_tuning(ctx, t)) != PM_OK) break;
             cudaError_t e = body(kind);  // warm-up (first use of this variant)
             cudaEventRecord(e0, ctx->stream);
@@ -697,7 +705,7 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
             if (ms) ms[3 * kind + c] = t_ms;
             if (c == 0 || t_ms < best_ms) {
                 best_ms = t_ms;
-                best[kind] = cand[c];
+                best[kind] = kTuneCand[kind][c];
             }
         }
     }

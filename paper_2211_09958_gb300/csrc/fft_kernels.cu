@@ -250,17 +250,20 @@ constexpr int kPencil = 8;
 // buffer [n1][k2][w] (n1 pitch M2*8 + 8 keeps half-warps on distinct banks);
 // step 3: thread (r, w) transforms columns k2 = r, r + M1, ... over n1 and
 // stores straight to global (M1 <= M2, so every thread has work).
-template <int L>
+// W = 16 (the x pass, autotuned): two adjacent y chunks, 128 contiguous
+// bytes per row.
+template <int L, int W = kPencil>
 struct PencilShape {
-    static constexpr int M1 = lsplit(L), M2 = msplit(L), THREADS = M1 * kPencil, YP = M2 * kPencil + kPencil;
+    static constexpr int M1 = lsplit(L), M2 = msplit(L), THREADS = M1 * W, YP = M2 * W + W;
     static constexpr int SMEM = M1 * YP;  // complex elements
+    static constexpr int MINB = THREADS > 256 ? 1 : 2;
 };
 
-template <int L, bool INV>
-__global__ void __launch_bounds__(PencilShape<L>::THREADS, 2) k_fft_pencil(float2 *data, PencilGeom pg,
-                                                                            const float2 *__restrict__ tw) {
-    using S = PencilShape<L>;
-    constexpr int M1 = S::M1, M2 = S::M2, YP = S::YP, W = kPencil;
+template <int L, bool INV, int W>
+__global__ void __launch_bounds__(PencilShape<L, W>::THREADS, PencilShape<L, W>::MINB)
+    k_fft_pencil(float2 *data, PencilGeom pg, const float2 *__restrict__ tw) {
+    using S = PencilShape<L, W>;
+    constexpr int M1 = S::M1, M2 = S::M2, YP = S::YP;
     extern __shared__ float4 smraw[];
     float2 *ys = reinterpret_cast<float2 *>(smraw);
     const int tid = threadIdx.x, w = tid % W, r = tid / W;
@@ -334,14 +337,21 @@ cudaError_t z_inv_n(const float2 *spec, float *out, const FftGeom &fg, cudaStrea
     return z_inv_t<N, GS, GO, 256>(spec, out, fg, st);
 }
 
-template <int L, bool INV>
-cudaError_t pencil_n(float2 *data, const PencilGeom &pg, int64_t blocks, const float2 *tw, cudaStream_t st) {
-    using S = PencilShape<L>;
+template <int L, bool INV, int W>
+cudaError_t pencil_w(float2 *data, const PencilGeom &pg, int64_t blocks, const float2 *tw, cudaStream_t st) {
+    using S = PencilShape<L, W>;
     const size_t smem = sizeof(float2) * S::SMEM;
-    cudaError_t e = cudaFuncSetAttribute(k_fft_pencil<L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fft_pencil<L, INV, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fft_pencil<L, INV><<<(unsigned)blocks, S::THREADS, smem, st>>>(data, pg, tw);
+    k_fft_pencil<L, INV, W><<<(unsigned)blocks, S::THREADS, smem, st>>>(data, pg, tw);
     return cudaGetLastError();
+}
+
+template <int L, bool INV>
+cudaError_t pencil_n(float2 *data, const PencilGeom &pg, int width, int64_t blocks, const float2 *tw,
+                     cudaStream_t st) {
+    return width == 16 ? pencil_w<L, INV, 16>(data, pg, blocks, tw, st) : pencil_w<L, INV, 8>(data, pg, blocks, tw, st);
 }
 
 template <int G>
@@ -373,15 +383,16 @@ cudaError_t z_inv_g(const float2 *spec, float *out, const FftGeom &fg, cudaStrea
 }
 
 template <bool INV>
-cudaError_t pencil_l(float2 *data, const PencilGeom &pg, int n, int64_t blocks, const float2 *tw, cudaStream_t st) {
+cudaError_t pencil_l(float2 *data, const PencilGeom &pg, int width, int n, int64_t blocks, const float2 *tw,
+                     cudaStream_t st) {
     switch (n) {
-        case 16: return pencil_n<16, INV>(data, pg, blocks, tw, st);
-        case 32: return pencil_n<32, INV>(data, pg, blocks, tw, st);
-        case 64: return pencil_n<64, INV>(data, pg, blocks, tw, st);
-        case 128: return pencil_n<128, INV>(data, pg, blocks, tw, st);
-        case 256: return pencil_n<256, INV>(data, pg, blocks, tw, st);
-        case 512: return pencil_n<512, INV>(data, pg, blocks, tw, st);
-        case 1024: return pencil_n<1024, INV>(data, pg, blocks, tw, st);
+        case 16: return pencil_n<16, INV>(data, pg, width, blocks, tw, st);
+        case 32: return pencil_n<32, INV>(data, pg, width, blocks, tw, st);
+        case 64: return pencil_n<64, INV>(data, pg, width, blocks, tw, st);
+        case 128: return pencil_n<128, INV>(data, pg, width, blocks, tw, st);
+        case 256: return pencil_n<256, INV>(data, pg, width, blocks, tw, st);
+        case 512: return pencil_n<512, INV>(data, pg, width, blocks, tw, st);
+        case 1024: return pencil_n<1024, INV>(data, pg, width, blocks, tw, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -445,20 +456,22 @@ cudaError_t launch_fft_z_inv(int gs, const float2 *spec, float *out, const FftGe
 cudaError_t launch_fft_pencils(int axis, bool inverse, float2 *spec, int f0, int nf, const FftGeom &fg,
                                cudaStream_t st) {
     const int n = fg.n;
+    const int width = axis == 0 && fg.xwidth == 16 ? 16 : kPencil;
     PencilGeom pg{};
     pg.nkz = 1;
-    pg.nmid = n;
+    pg.nmid = n / (width / kPencil);
     pg.os = (int64_t)n * n * kPencil;
     float2 *base = spec + f0 * fg.fstride;
     if (axis == 1) {  // lines along y: a contiguous n x 8 slab
         pg.ls = kPencil;
         pg.ms = (int64_t)n * kPencil;
-    } else {          // lines along x: rows n * 8 complex apart
+    } else {          // lines along x: rows n * 8 complex apart; width / 8 adjacent y per pencil
         pg.ls = (int64_t)n * kPencil;
-        pg.ms = kPencil;
+        pg.ms = width;
     }
-    const int64_t blocks = (int64_t)nf * fg.nb * (fg.zc / kPencil) * n;
-    return inverse ? pencil_l<true>(base, pg, n, blocks, fg.tw, st) : pencil_l<false>(base, pg, n, blocks, fg.tw, st);
+    const int64_t blocks = (int64_t)nf * fg.nb * (fg.zc / kPencil) * pg.nmid;
+    return inverse ? pencil_l<true>(base, pg, width, n, blocks, fg.tw, st)
+                   : pencil_l<false>(base, pg, width, n, blocks, fg.tw, st);
 }
 
 }  // namespace pmgb

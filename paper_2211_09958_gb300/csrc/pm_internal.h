@@ -146,6 +146,7 @@ struct FftGeom {
     int64_t fstride;    // complex elements per spectrum field (all runs)
     const float2 *tw;   // W_1024^j, j < 1024
     int zthreads;       // z-pass block size for n >= 256: 128, 256 (also for 0) or 512 (autotuned)
+    int xwidth;         // x-pass pencil width in complex columns: 8 (also for 0) or 16 (autotuned)
 };
 
 struct PencilGeom {

@@ -216,23 +216,24 @@ class ParticleMesh:
         return loss.value
 
     # ------------------------------------------------------- autotuner --
-    TUNE_FAMILIES = ("paint", "read", "spectral", "fft_z")
+    TUNE_FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x")
 
     def autotune(self, s):
-        """Pick the fastest block size per kernel family on particles s;
-        returns (chosen {family: threads}, times [family][128, 256, 512] ms)."""
+        """Pick the fastest launch shape per kernel family on particles s;
+        returns (chosen {family: value}, times [family][candidate] ms; the
+        block-size families try 128, 256, 512 threads, fft_x widths 8, 16)."""
         self._particles(s, "s")
-        ms = np.zeros((4, 3), np.float32)
+        ms = np.zeros((len(self.TUNE_FAMILIES), 3), np.float32)
         self._call("pm_autotune", _ptr(s), ms.ctypes.data_as(ctypes.c_void_p))
         return self.get_tuning(), ms
 
     def get_tuning(self):
-        t = np.zeros(4, np.int32)
+        t = np.zeros(len(self.TUNE_FAMILIES), np.int32)
         self._call("pm_get_tuning", t.ctypes.data_as(ctypes.c_void_p))
         return dict(zip(self.TUNE_FAMILIES, (int(v) for v in t)))
 
-    def set_tuning(self, paint=256, read=256, spectral=256, fft_z=256):
-        t = np.array([paint, read, spectral, fft_z], np.int32)
+    def set_tuning(self, paint=256, read=256, spectral=256, fft_z=256, fft_x=8):
+        t = np.array([paint, read, spectral, fft_z, fft_x], np.int32)
         self._call("pm_set_tuning", t.ctypes.data_as(ctypes.c_void_p))
 
     def use_graphs(self, enable=True):
