@@ -102,16 +102,21 @@ def growth_tables(a, om):
     return g
 
 
-def time_grid(a_init, a_final, n_steps):
-    """Uniform steps in a [reading]; half steps at the arithmetic midpoint."""
+def time_grid(a_init, a_final, n_steps, log_a=False):
+    """Uniform steps in a, half steps at the arithmetic midpoint [reading];
+    with ``log_a`` uniform in ln a, half steps at the geometric midpoint (the
+    solver variant)."""
+    if log_a:
+        a = a_init * (a_final / a_init) ** (np.arange(n_steps + 1) / n_steps)
+        return a, np.sqrt(a[:-1] * a[1:])
     a = a_init + (a_final - a_init) * np.arange(n_steps + 1) / n_steps
     return a, 0.5 * (a[:-1] + a[1:])
 
 
-def kdk_coefficients(cosmo, a_init, a_final, n_steps):
+def kdk_coefficients(cosmo, a_init, a_final, n_steps, log_a=False):
     """Per step n: K_a (first half kick, force at a_n), Dr (drift, momentum at
     a_{n+1/2}), K_b (second half kick, force at a_{n+1})."""
-    a, ah = time_grid(a_init, a_final, n_steps)
+    a, ah = time_grid(a_init, a_final, n_steps, log_a)
     g = growth_tables(np.concatenate([a, ah]), cosmo.omega_m)
     n = n_steps
     gp_a, gp_h = g["gp"][: n + 1], g["gp"][n + 1:]
@@ -123,10 +128,10 @@ def kdk_coefficients(cosmo, a_init, a_final, n_steps):
     return {"a": a, "ah": ah, "K_a": k_a, "Dr": drift, "K_b": k_b}
 
 
-def kdk_coefficients_domega(cosmo, a_init, a_final, n_steps):
+def kdk_coefficients_domega(cosmo, a_init, a_final, n_steps, log_a=False):
     """d(K_a, Dr, K_b)/dOm by central differences of the FP64 tables."""
-    up = kdk_coefficients(cosmo.with_omega_m(cosmo.omega_m + FD_OMEGA), a_init, a_final, n_steps)
-    dn = kdk_coefficients(cosmo.with_omega_m(cosmo.omega_m - FD_OMEGA), a_init, a_final, n_steps)
+    up = kdk_coefficients(cosmo.with_omega_m(cosmo.omega_m + FD_OMEGA), a_init, a_final, n_steps, log_a)
+    dn = kdk_coefficients(cosmo.with_omega_m(cosmo.omega_m - FD_OMEGA), a_init, a_final, n_steps, log_a)
     return {k: (up[k] - dn[k]) / (2 * FD_OMEGA) for k in ("K_a", "Dr", "K_b")}
 
 

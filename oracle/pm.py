@@ -20,6 +20,10 @@ displacement s = x - q and momentum p = a^3 E dx/da.
   density       rho(c) = alpha sum_i W(x_i - c) - 1, alpha = (n_m / n_p)^3
   force         F_j(k) = i D_j(k) (3/2) Om rho(k) / k^2, zero at k = 0 and
                 where n_j is the Nyquist index; F_j(c) = IDFT; F_i = sum_c W F(c)
+  solver flags  SPECTRAL_GRADIENT (1): D_j = k_j instead (exact spectral
+                gradient, zero at the Nyquist index); DECONVOLVE (2): the Green
+                function divided by the CIC window of paint and read,
+                prod_j sinc^4(k_j h / 2); LOG_A (4): steps uniform in ln a
   gradient      D_j(k) = (8 sin(k_j h) - sin(2 k_j h)) / (6 h), the 4-point
                 central difference in Fourier space [reading]: it vanishes
                 smoothly at the Nyquist frequency.  With a mesh finer than the
@@ -55,6 +59,7 @@ class Setup:
     a_init: float = 1.0 / 64
     a_final: float = 1.0
     n_steps: int = 10
+    solver: int = 0                   # bit mask of the solver flags below
 
     @property
     def cell(self):
@@ -167,23 +172,35 @@ def density(s, setup):
 
 # -------------------------------------------------------------- force ----
 
+SPECTRAL_GRADIENT, DECONVOLVE, LOG_A = 1, 2, 4
+
+
 def gradient_operator(k, h):
     """Fourier multiplier of the 4-point central difference d/dx on a mesh of
     spacing h (times i): (8 sin(k h) - sin(2 k h)) / (6 h)."""
     return (8.0 * np.sin(k * h) - np.sin(2.0 * k * h)) / (6.0 * h)
 
 
-def gradient_green_multipliers(n, box, omega_m):
+def cic_window(k, h):
+    """Fourier transform of one CIC assignment along one axis, sinc^2(k h / 2)."""
+    return np.sinc(k * h / (2.0 * np.pi)) ** 2
+
+
+def gradient_green_multipliers(n, box, omega_m, solver=0):
     """i D_j (3/2) Om / k^2 on the rfft grid (D_j the 4-point difference
-    gradient, k^2 exact), zero at k = 0 and where n_j is the Nyquist index
-    (so each inverse transform is exactly real) [reading]."""
+    gradient, or k_j with SPECTRAL_GRADIENT; k^2 exact; divided by the paint
+    and read CIC windows with DECONVOLVE), zero at k = 0 and where n_j is the
+    Nyquist index (so each inverse transform is exactly real) [reading]."""
     (kx, ky, kz), nyq = rfft_wavenumbers(n, box)
     k2 = kx ** 2 + ky ** 2 + kz ** 2
     k2s = np.where(k2 > 0, k2, 1.0)
     h = box / n
+    if solver & DECONVOLVE:
+        k2s = k2s * (cic_window(kx, h) * cic_window(ky, h) * cic_window(kz, h)) ** 2
     out = []
     for kj, mj in zip((kx, ky, kz), nyq):
-        m = 1j * gradient_operator(kj, h) * (1.5 * omega_m) / k2s
+        dj = kj if solver & SPECTRAL_GRADIENT else gradient_operator(kj, h)
+        m = 1j * dj * (1.5 * omega_m) / k2s
         m = np.where((k2 > 0) & ~mj, m, 0.0)
         out.append(m)
     return out
@@ -192,7 +209,7 @@ def gradient_green_multipliers(n, box, omega_m):
 def force_meshes(x, setup):
     rho = setup.alpha * cic_paint(x, setup.n_m, setup.cell) - 1.0
     rho_k = rfftn(rho)
-    mult = gradient_green_multipliers(setup.n_m, setup.box, setup.cosmo.omega_m)
+    mult = gradient_green_multipliers(setup.n_m, setup.box, setup.cosmo.omega_m, setup.solver)
     return [irfftn(m * rho_k, setup.n_m) for m in mult]
 
 
@@ -213,7 +230,7 @@ def force_vjp(s, v, setup):
     term_a = np.zeros((len(x), 3))
     for j in range(3):
         term_a += cic_read_grad(x, meshes[j], setup.cell) * v[:, j:j + 1]
-    mult = gradient_green_multipliers(setup.n_m, setup.box, setup.cosmo.omega_m)
+    mult = gradient_green_multipliers(setup.n_m, setup.box, setup.cosmo.omega_m, setup.solver)
     psi_k = 0.0
     for j in range(3):
         u_j = cic_paint(x, setup.n_m, setup.cell, v[:, j])
@@ -226,7 +243,7 @@ def force_vjp(s, v, setup):
 # ---------------------------------------------------------------- KDK ----
 
 def coefficients(setup):
-    return kdk_coefficients(setup.cosmo, setup.a_init, setup.a_final, setup.n_steps)
+    return kdk_coefficients(setup.cosmo, setup.a_init, setup.a_final, setup.n_steps, bool(setup.solver & LOG_A))
 
 
 def integrate(s, p, setup, force_fn=None, steps=None):
@@ -294,7 +311,7 @@ def adjoint_integrate(s, p, f, lam, mu, setup):
 def dynamics_domega(grads, setup):
     """Total d/dOm of the dynamics part: chain through the coefficient tables
     plus the direct force prefactor."""
-    d = kdk_coefficients_domega(setup.cosmo, setup.a_init, setup.a_final, setup.n_steps)
+    d = kdk_coefficients_domega(setup.cosmo, setup.a_init, setup.a_final, setup.n_steps, bool(setup.solver & LOG_A))
     return (np.dot(grads["K_a"], d["K_a"]) + np.dot(grads["Dr"], d["Dr"])
             + np.dot(grads["K_b"], d["K_b"]) + grads["omega_m_direct"])
 

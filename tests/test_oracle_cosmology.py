@@ -69,11 +69,13 @@ def test_tophat_series_matches_closed_form():
 
 
 @pytest.mark.parametrize("n_steps", [1, 7, 50])
-def test_kdk_exact_for_linear_force(n_steps):
+@pytest.mark.parametrize("solver", [0, 4])
+def test_kdk_exact_for_linear_force(n_steps, solver):
     # With the linear-theory force F = 3/2 Om s, growth-matched KDK reproduces
-    # the growing mode s = D1(a) s1, p = g_p(a) s1 exactly for any step count.
+    # the growing mode s = D1(a) s1, p = g_p(a) s1 exactly for any step count,
+    # with steps uniform in a or (solver flag 4) in ln a.
     cosmo = C.Cosmology(0.3)
-    st = Setup(4, 8, 100.0, cosmo, a_init=1 / 64, a_final=1.0, n_steps=n_steps)
+    st = Setup(4, 8, 100.0, cosmo, a_init=1 / 64, a_final=1.0, n_steps=n_steps, solver=solver)
     s1 = np.random.default_rng(3).standard_normal((64, 3))
     gi = C.growth_tables(np.array([st.a_init, st.a_final]), cosmo.omega_m)
     s0, p0 = gi["D1"][0] * s1, gi["gp"][0] * s1
@@ -89,3 +91,10 @@ def test_coefficient_domega_step_independent():
     dn = C.kdk_coefficients(cosmo.with_omega_m(0.3 - 1e-3), 1 / 64, 1.0, 5)
     for k in ("K_a", "Dr", "K_b"):
         np.testing.assert_allclose(d1[k], (up[k] - dn[k]) / 2e-3, rtol=1e-5)
+
+
+def test_log_a_grid_is_geometric():
+    a, ah = C.time_grid(1 / 64, 1.0, 6, log_a=True)
+    assert a[0] == 1 / 64 and abs(a[-1] - 1.0) < 1e-15
+    np.testing.assert_allclose(np.diff(np.log(a)), np.log(64) / 6, rtol=1e-12)
+    np.testing.assert_allclose(np.log(ah), 0.5 * (np.log(a[:-1]) + np.log(a[1:])), rtol=1e-12)
