@@ -77,7 +77,24 @@ typedef struct pm_config {
     double n_s;         /* primordial spectral index                          */
     const double *omega_m; /* host [n_batch]: matter density, (0, 1]         */
     const double *sigma8;  /* host [n_batch]: amplitude at a = 1, > 0         */
+    int32_t solver;        /* bit mask of PM_SOLVER_* variants, 0 = defaults  */
 } pm_config;
+
+/* Solver variants (readings the paper leaves open; the defaults are the
+ * 4-point difference gradient, no window correction, steps uniform in a):
+ *   PM_SOLVER_SPECTRAL_GRADIENT  gradient i k_j (zero at the Nyquist index)
+ *                                instead of i (8 sin k_j h - sin 2 k_j h)/6h;
+ *                                on meshes finer than the particle lattice it
+ *                                overestimates the linear force by O(k)
+ *   PM_SOLVER_DECONVOLVE         Green's function divided by the paint and
+ *                                read CIC windows, prod_j sinc^4(k_j h / 2)
+ *                                (sharper force at n_m = n_p; amplifies
+ *                                lattice aliasing at n_m > n_p)
+ *   PM_SOLVER_LOG_A              KDK steps uniform in ln a, half steps at the
+ *                                geometric midpoint */
+#define PM_SOLVER_SPECTRAL_GRADIENT 1
+#define PM_SOLVER_DECONVOLVE 2
+#define PM_SOLVER_LOG_A 4
 
 /* Create a context: validates cfg, computes the FP64 growth and coefficient
  * tables on the host, allocates the scratch meshes and creates the cuFFT

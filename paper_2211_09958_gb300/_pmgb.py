@@ -33,7 +33,11 @@ class PmConfig(ctypes.Structure):
         ("n_s", ctypes.c_double),
         ("omega_m", _c_double_p),
         ("sigma8", _c_double_p),
+        ("solver", ctypes.c_int32),
     ]
+
+
+SOLVER_SPECTRAL_GRADIENT, SOLVER_DECONVOLVE, SOLVER_LOG_A = 1, 2, 4
 
 
 _P = ctypes.c_void_p
@@ -106,12 +110,12 @@ def _dptr(a):
     return a.ctypes.data_as(_c_double_p)
 
 
-def make_config(n_p, n_m, box, omega_m, sigma8, n_steps, a_init=1.0 / 64, a_final=1.0, h=0.7, n_s=0.96):
+def make_config(n_p, n_m, box, omega_m, sigma8, n_steps, a_init=1.0 / 64, a_final=1.0, h=0.7, n_s=0.96, solver=0):
     om = np.ascontiguousarray(np.atleast_1d(omega_m), dtype=np.float64)
     s8 = np.ascontiguousarray(np.atleast_1d(sigma8), dtype=np.float64)
     if om.shape != s8.shape:
         raise ValueError("omega_m and sigma8 need the same length")
-    cfg = PmConfig(n_p, n_m, len(om), n_steps, box, a_init, a_final, h, n_s, _dptr(om), _dptr(s8))
+    cfg = PmConfig(n_p, n_m, len(om), n_steps, box, a_init, a_final, h, n_s, _dptr(om), _dptr(s8), int(solver))
     cfg._keep = (om, s8)
     return cfg
 

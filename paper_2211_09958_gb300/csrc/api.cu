@@ -39,6 +39,7 @@ struct pm_ctx {
     float4 *d_table = nullptr;
     float *d_pref = nullptr;
     float *d_grad = nullptr;  // [n_m] difference-gradient multiplier per axis index
+    float *d_dec = nullptr;   // [n_m] CIC deconvolution factor per axis index (solver flag)
     float4 *d_fac = nullptr;
     LinParams *d_lin = nullptr;
     double *d_red = nullptr;
@@ -275,11 +276,11 @@ Spec mesh_spec(pm_ctx *ctx) {
     if (ctx->own) {
         const int64_t per = (int64_t)n * n * ctx->fg.zc;
         return Spec{ctx->spec, per * ctx->P.n_batch, per, n, ctx->P.n_batch, kf, ctx->fg.zc, 1, ctx->d_grad,
-                    ctx->tune[2]};
+                    ctx->d_dec, ctx->tune[2]};
     }
     const int64_t modes = ctx->mesh_pad / 2;
     return Spec{reinterpret_cast<float2 *>(ctx->mesh), modes * ctx->P.n_batch, modes, n, ctx->P.n_batch, kf, n / 2 + 1, 0,
-                ctx->d_grad, ctx->tune[2]};
+                ctx->d_grad, ctx->d_dec, ctx->tune[2]};
 }
 
 MeshRef lat_ref(pm_ctx *ctx) {
@@ -461,9 +462,7 @@ int run_graphed(pm_ctx *ctx, int kind, int b, int e, const void *q0, const void 
     return PM_OK;
 }
 
-double a_of(pm_ctx *ctx, int n) {
-    return ctx->P.a_init + (ctx->P.a_final - ctx->P.a_init) * n / ctx->P.n_steps;
-}
+double a_of(pm_ctx *ctx, int n) { return step_a(ctx->P, n); }
 
 int check_ptr(pm_ctx *ctx, const void *p, const char *name) {
     if (!p) return fail(ctx, PM_EINVAL, std::string(name) + " must not be NULL");
@@ -770,6 +769,7 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
     if (!(c.box > 0)) return fail(nullptr, PM_EINVAL, "box must be > 0");
     if (!(c.a_init > 0 && c.a_final > c.a_init)) return fail(nullptr, PM_EINVAL, "need 0 < a_init < a_final");
     if (!(c.h > 0)) return fail(nullptr, PM_EINVAL, "h must be > 0");
+    if (c.solver & ~7) return fail(nullptr, PM_EINVAL, "unknown solver flag");
     {
         int rc = check_cosmology(nullptr, c.omega_m, c.sigma8, c.n_batch);
         if (rc) return rc;
@@ -778,7 +778,7 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
     if (npart * c.n_batch * 3 > ((int64_t)1 << 40)) return fail(nullptr, PM_ERANGE, "too many particles");
 
     pm_ctx *ctx = new pm_ctx();
-    ctx->P = Params{c.n_p, c.n_m, c.n_batch, c.n_steps, c.box, c.a_init, c.a_final, c.h, c.n_s};
+    ctx->P = Params{c.n_p, c.n_m, c.n_batch, c.n_steps, c.box, c.a_init, c.a_final, c.h, c.n_s, c.solver};
     ctx->om.assign(c.omega_m, c.omega_m + c.n_batch);
     ctx->s8.assign(c.sigma8, c.sigma8 + c.n_batch);
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {
@@ -830,6 +830,7 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
     if (cudaMalloc(&ctx->d_table, sizeof(float4) * (size_t)c.n_steps * B) != cudaSuccess ||
         cudaMalloc(&ctx->d_pref, sizeof(float) * B) != cudaSuccess ||
         cudaMalloc(&ctx->d_grad, sizeof(float) * ctx->P.n_m) != cudaSuccess ||
+        cudaMalloc(&ctx->d_dec, sizeof(float) * ctx->P.n_m) != cudaSuccess ||
         cudaMalloc(&ctx->d_fac, sizeof(float4) * B) != cudaSuccess ||
         cudaMalloc(&ctx->d_lin, sizeof(LinParams) * B) != cudaSuccess ||
         cudaMalloc(&ctx->d_red, sizeof(double) * B * 2 * (c.n_steps + 1)) != cudaSuccess ||
@@ -841,14 +842,21 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
     }
     {
         // D(k) = (8 sin(k h) - sin(2 k h)) / (6 h) per axis index, k = 2 pi n_j / L
-        std::vector<float> grad(c.n_m);
+        // (k itself with the spectral-gradient flag; 0 at the Nyquist index);
+        // deconvolution 1 / sinc^4(k h / 2) per axis (1 without the flag)
+        std::vector<float> grad(c.n_m), dec(c.n_m);
         const double h = c.box / c.n_m;
         for (int j = 0; j < c.n_m; ++j) {
             const int nj = j < c.n_m / 2 ? j : j - c.n_m;
             const double kh = 2.0 * M_PI * nj / c.n_m;
-            grad[j] = 2 * j == c.n_m ? 0.f : (float)((8.0 * std::sin(kh) - std::sin(2.0 * kh)) / (6.0 * h));
+            const double d = (c.solver & PM_SOLVER_SPECTRAL_GRADIENT) ? kh / h
+                                                                       : (8.0 * std::sin(kh) - std::sin(2.0 * kh)) / (6.0 * h);
+            grad[j] = 2 * j == c.n_m ? 0.f : (float)d;
+            const double x = 0.5 * kh, sc = nj == 0 ? 1.0 : std::sin(x) / x;
+            dec[j] = (c.solver & PM_SOLVER_DECONVOLVE) ? (float)(1.0 / (sc * sc * sc * sc)) : 1.f;
         }
-        if (cudaMemcpy(ctx->d_grad, grad.data(), sizeof(float) * c.n_m, cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (cudaMemcpy(ctx->d_grad, grad.data(), sizeof(float) * c.n_m, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ctx->d_dec, dec.data(), sizeof(float) * c.n_m, cudaMemcpyHostToDevice) != cudaSuccess) {
             cudaGetLastError();
             fail(ctx, PM_ECUDA, "cannot upload the gradient table");
             return bail(PM_ECUDA);
@@ -900,7 +908,7 @@ int pm_destroy(pm_ctx *ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->spec, (void *)ctx->tw}) 
         if (p) cudaFree(p);
-    for (void *p : {(void *)ctx->mesh, (void *)ctx->lat, (void *)ctx->d_table, (void *)ctx->d_pref, (void *)ctx->d_grad,
+    for (void *p : {(void *)ctx->mesh, (void *)ctx->lat, (void *)ctx->d_table, (void *)ctx->d_pref, (void *)ctx->d_grad, (void *)ctx->d_dec,
                     (void *)ctx->d_fac, (void *)ctx->d_lin, (void *)ctx->d_red, (void *)ctx->d_pk,
                     (void *)ctx->d_lred, ctx->work})
         if (p) cudaFree(p);
@@ -954,7 +962,9 @@ int pm_host_coefficients(const pm_config *cfg, double *kdk, double *dkdk, double
         int rc = check_cosmology(nullptr, cfg->omega_m, cfg->sigma8, cfg->n_batch);
         if (rc) return rc;
     }
-    Params P{cfg->n_p, cfg->n_m, cfg->n_batch, cfg->n_steps, cfg->box, cfg->a_init, cfg->a_final, cfg->h, cfg->n_s};
+    if (cfg->solver & ~7) return fail(nullptr, PM_EINVAL, "unknown solver flag");
+    Params P{cfg->n_p, cfg->n_m, cfg->n_batch, cfg->n_steps, cfg->box, cfg->a_init, cfg->a_final, cfg->h, cfg->n_s,
+             cfg->solver};
     const int N = cfg->n_steps;
     for (int b = 0; b < cfg->n_batch; ++b) {
         HostTables t;

@@ -13,7 +13,8 @@
 //   drift Dr(a->b; c) = (D1(b) - D1(a)) / g_p(c)
 //   step n: K_a = K(a_n -> a_h; a_n), Dr = Dr(a_n -> a_{n+1}; a_h),
 //           K_b = K(a_h -> a_{n+1}; a_{n+1}), a_h = (a_n + a_{n+1}) / 2,
-//           a_n uniform between a_init and a_final.
+//           a_n uniform between a_init and a_final (or, with the log-a
+//           solver flag, uniform in ln a with a_h the geometric midpoint).
 //   P(k) = A k^ns T_BBKS(k / (Om h))^2, A from the top-hat sigma8 integral.
 // Integration: classical RK4 in ln a with steps <= 1e-3; sigma8 integral:
 // composite Simpson in ln k over [1e-5, 1e3] h/Mpc, 10^4 intervals.
@@ -110,11 +111,23 @@ void growth_at(double om, const std::vector<double> &a, std::vector<Growth> *out
     }
 }
 
-void kdk_factors(double om, double a_init, double a_final, int n_steps, std::vector<double> *ka,
-                 std::vector<double> *dr, std::vector<double> *kb) {
+double step_a(const Params &p, int n) {
+    if (p.solver & 4) return p.a_init * std::pow(p.a_final / p.a_init, (double)n / p.n_steps);
+    return p.a_init + (p.a_final - p.a_init) * n / p.n_steps;
+}
+
+double half_step_a(const Params &p, int n) {
+    if (p.solver & 4) return std::sqrt(step_a(p, n) * step_a(p, n + 1));
+    return 0.5 * (step_a(p, n) + step_a(p, n + 1));
+}
+
+namespace {
+void kdk_factors(double om, const Params &p, std::vector<double> *ka, std::vector<double> *dr,
+                 std::vector<double> *kb) {
+    const int n_steps = p.n_steps;
     std::vector<double> a(n_steps + 1), ah(n_steps);
-    for (int n = 0; n <= n_steps; ++n) a[n] = a_init + (a_final - a_init) * n / n_steps;
-    for (int n = 0; n < n_steps; ++n) ah[n] = 0.5 * (a[n] + a[n + 1]);
+    for (int n = 0; n <= n_steps; ++n) a[n] = step_a(p, n);
+    for (int n = 0; n < n_steps; ++n) ah[n] = half_step_a(p, n);
     std::vector<double> all(a);
     all.insert(all.end(), ah.begin(), ah.end());
     std::vector<Growth> g;
@@ -129,6 +142,7 @@ void kdk_factors(double om, double a_init, double a_final, int n_steps, std::vec
         (*kb)[n] = (g1.gp - gh.gp) / g1.gf;
     }
 }
+}  // namespace
 
 void lpt_factors(double om, double a_init, double out[4]) {
     std::vector<Growth> g;
@@ -171,10 +185,10 @@ double power_amplitude(double om, double s8, double h, double ns) {
 }
 
 void host_tables(const Params &p, double om, double s8, HostTables *t) {
-    kdk_factors(om, p.a_init, p.a_final, p.n_steps, &t->ka, &t->dr, &t->kb);
+    kdk_factors(om, p, &t->ka, &t->dr, &t->kb);
     std::vector<double> ka_u, dr_u, kb_u, ka_d, dr_d, kb_d;
-    kdk_factors(om + kFdOmega, p.a_init, p.a_final, p.n_steps, &ka_u, &dr_u, &kb_u);
-    kdk_factors(om - kFdOmega, p.a_init, p.a_final, p.n_steps, &ka_d, &dr_d, &kb_d);
+    kdk_factors(om + kFdOmega, p, &ka_u, &dr_u, &kb_u);
+    kdk_factors(om - kFdOmega, p, &ka_d, &dr_d, &kb_d);
     t->dka.resize(p.n_steps);
     t->ddr.resize(p.n_steps);
     t->dkb.resize(p.n_steps);

@@ -14,7 +14,14 @@ namespace pmgb {
 struct Params {
     int n_p, n_m, n_batch, n_steps;
     double box, a_init, a_final, h, n_s;
+    int solver;  // PM_SOLVER_* bit mask
 };
+
+// Scale factor of step boundary n (0 .. n_steps) and of the half step
+// after it: uniform in a (midpoint arithmetic) or, with the log-a solver
+// flag (4), uniform in ln a (midpoint geometric).
+double step_a(const Params &p, int n);
+double half_step_a(const Params &p, int n);
 
 struct Growth {
     double D1, dD1, D2, dD2, gp, gp2, gf;
@@ -137,6 +144,7 @@ struct Spec {
     int zc;
     int blk;
     const float *grad;  // [n] 4-point difference gradient D(k) per axis index (force kernels)
+    const float *dec;   // [n] per-axis CIC deconvolution 1/sinc^4(pi n_j / n), NULL = none
     int threads;        // force-kernel block size: 128, 256 (also for 0) or 512 (autotuned)
 };
 

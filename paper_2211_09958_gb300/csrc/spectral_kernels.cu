@@ -8,7 +8,9 @@
 // (n/2 + 1) complex entries; wavenumber index j maps to n_j = j for
 // j < n/2 and j - n otherwise (the Nyquist index n/2 maps to -n/2 on the
 // full axes and +n/2 on the half axis).
-//   force    F_j(k) = i D_j (3/2) Om delta(k) / k^2 / n^3, zero at k = 0;
+//   force    F_j(k) = i D_j (3/2) Om delta(k) / k^2 / n^3 (times the per-axis
+//            CIC deconvolution factors, 1 unless that solver flag is set),
+//            zero at k = 0;
 //            D_j = (8 sin(k_j h) - sin(2 k_j h)) / (6 h), the 4-point central
 //            difference gradient, from a per-axis table that is exactly zero
 //            at the Nyquist index (inverse transforms real)
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(T) k_spec_force(Spec sp, const float *pref) {
     if (iz > n / 2) return;
     const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
     const float k2 = kx * kx + ky * ky + kz * kz;
-    const float g = k2 > 0.f ? pref[b] / k2 : 0.f;
+    const float g = k2 > 0.f ? pref[b] / k2 * (__ldg(sp.dec + ix) * __ldg(sp.dec + iy) * __ldg(sp.dec + iz)) : 0.f;
     float2 *c0 = sp.c + (int64_t)b * sp.bstride + m;
     const float2 d = *c0;
     c0[0] = times_i(d, __ldg(sp.grad + ix) * g);
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(T) k_spec_adj(Spec sp, const float *pref) {
     if (iz > n / 2) return;
     const float kx = sp.kf * signed_index(ix, n), ky = sp.kf * signed_index(iy, n), kz = sp.kf * iz;
     const float k2 = kx * kx + ky * ky + kz * kz;
-    const float g = k2 > 0.f ? pref[b] / k2 : 0.f;
+    const float g = k2 > 0.f ? pref[b] / k2 * (__ldg(sp.dec + ix) * __ldg(sp.dec + iy) * __ldg(sp.dec + iz)) : 0.f;
     float2 *c0 = sp.c + (int64_t)b * sp.bstride + m;
     const int64_t fs = sp.fstride;
     const float2 d = c0[0], ux = c0[fs], uy = c0[2 * fs], uz = c0[3 * fs];

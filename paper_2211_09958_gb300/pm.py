@@ -28,13 +28,13 @@ class ParticleMesh:
     """A batch of n_batch PM simulations sharing (n_p, n_m, box, steps)."""
 
     def __init__(self, n_p, n_m, box, omega_m=0.3, sigma8=0.8, n_steps=10, a_init=1.0 / 64, a_final=1.0,
-                 h=0.7, n_s=0.96, device=None):
+                 h=0.7, n_s=0.96, device=None, solver=0):
         if not torch.cuda.is_available():
             raise PMError("ParticleMesh needs a CUDA device (there is no CPU path)")
         self._lib = _pmgb.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
-        self.cfg = _pmgb.make_config(n_p, n_m, box, omega_m, sigma8, n_steps, a_init, a_final, h, n_s)
+        self.cfg = _pmgb.make_config(n_p, n_m, box, omega_m, sigma8, n_steps, a_init, a_final, h, n_s, solver)
         self.n_p, self.n_m, self.box, self.n_steps = n_p, n_m, float(box), n_steps
         self.n_batch = self.cfg.n_batch
         self.omega_m = np.array(self.cfg._keep[0])

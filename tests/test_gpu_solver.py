@@ -1,0 +1,77 @@
+"""GPU parity of the solver variants (pm_config.solver, include/pmgb.h):
+the exact spectral gradient, CIC deconvolution and steps uniform in ln a,
+against the FP64 oracle with the same flags.  Tolerances as for the default
+solver (tests/test_gpu_parity.py): force 2e-5 of max |F|, state after the
+integration 1e-4 of the spacing and of max |p|, gradients relative L2 1e-3."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import lpt as olpt
+from oracle import pm as opm
+from oracle.cosmology import Cosmology
+from paper_2211_09958_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FLAGS = [1, 2, 3]
+
+
+def _pm(n_p, n_m, box, solver, steps=4):
+    from paper_2211_09958_gb300.pm import ParticleMesh
+    return ParticleMesh(n_p, n_m, box, 0.3, 0.8, steps, solver=solver)
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _setup(pm, solver):
+    return opm.Setup(pm.n_p, pm.n_m, pm.box, Cosmology(0.3, 0.8), n_steps=pm.n_steps, solver=solver)
+
+
+@pytest.mark.parametrize("solver", FLAGS)
+@pytest.mark.parametrize("n_p,n_m,box", [(16, 32, 64.0), (16, 16, 48.0), (12, 24, 40.0)])
+def test_force_parity_with_solver_flags(solver, n_p, n_m, box):
+    pm = _pm(n_p, n_m, box, solver)
+    s = inputs.random_displacements(n_p, box, seed=n_m + solver, scale=0.6)
+    f = _host(pm.pm_force(_cuda(s)[None]))[0]
+    ref = opm.force(s.astype(np.float64), _setup(pm, solver))
+    assert np.max(np.abs(f - ref)) < 2e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("solver", [4, 7])
+def test_integrate_parity_with_solver_flags(solver):
+    pm = _pm(16, 32, 64.0, solver, steps=6)
+    noise = inputs.white_noise(16, seed=12)
+    s, p = pm.init_lpt(_cuda(noise)[None])
+    s0, p0 = _host(s)[0], _host(p)[0]
+    pm.integrate(s, p)
+    st = _setup(pm, solver)
+    rs, rp, _ = opm.integrate(s0, p0, st)
+    assert np.max(np.abs(_host(s)[0] - rs)) < 1e-4 * st.spacing
+    assert np.max(np.abs(_host(p)[0] - rp)) < 1e-4 * np.max(np.abs(rp))
+
+
+def test_loss_gradient_parity_with_all_flags():
+    pm = _pm(16, 32, 64.0, 7, steps=3)
+    noise = inputs.white_noise(16, seed=4)
+    target = inputs.target_field(32, seed=5)
+    from paper_2211_09958_gb300.pm import simulate, density
+    nz = _cuda(noise)[None].requires_grad_(True)
+    om = torch.tensor([0.3], dtype=torch.float64)
+    s8 = torch.tensor([0.8], dtype=torch.float64)
+    s, _ = simulate(pm, nz, om, s8)
+    d = density(pm, s)
+    loss = ((d - _cuda(target)[None]) ** 2).mean()
+    loss.backward()
+    st = _setup(pm, 7)
+    rl, rg, _, _ = opm.loss_and_grad(noise.astype(np.float64), target.astype(np.float64), st)
+    assert abs(loss.item() - rl) <= 1e-4 * abs(rl)
+    g = _host(nz.grad)[0]
+    assert np.linalg.norm(g - rg) <= 1e-3 * np.linalg.norm(rg)

@@ -71,3 +71,24 @@ def test_host_tables_match_oracle(lib, om, s8, steps):
     e = 1e-4
     dlna = (np.log(C.power_amplitude(cosmo.with_omega_m(om + e))) - np.log(C.power_amplitude(cosmo.with_omega_m(om - e)))) / (2 * e)
     np.testing.assert_allclose(amp[0, 1], dlna, rtol=1e-6)
+
+
+@pytest.mark.parametrize("steps", [5, 40])
+def test_log_a_tables_match_oracle(lib, steps):
+    cfg = _pmgb.make_config(32, 64, 128.0, [0.3], [0.8], steps, solver=_pmgb.SOLVER_LOG_A)
+    kdk, dkdk, _, _ = _pmgb.host_coefficients(cfg)
+    cosmo = C.Cosmology(0.3, 0.8)
+    ref = C.kdk_coefficients(cosmo, 1 / 64, 1.0, steps, log_a=True)
+    dref = C.kdk_coefficients_domega(cosmo, 1 / 64, 1.0, steps, log_a=True)
+    for j, k in enumerate(("K_a", "Dr", "K_b")):
+        np.testing.assert_allclose(kdk[0, :, j], ref[k], rtol=1e-9)
+        np.testing.assert_allclose(dkdk[0, :, j], dref[k], rtol=2e-6, atol=1e-9)
+    plain, _, _, _ = _pmgb.host_coefficients(_pmgb.make_config(32, 64, 128.0, [0.3], [0.8], steps))
+    assert not np.allclose(plain, kdk)                  # the flag reaches the tables
+
+
+def test_unknown_solver_flag_is_rejected(lib):
+    cfg = _pmgb.make_config(32, 64, 128.0, [0.3], [0.8], 4, solver=8)
+    out = ctypes.c_void_p()
+    assert lib.pm_create(ctypes.byref(cfg), ctypes.byref(out)) == -1
+    assert b"solver" in lib.pm_last_error(None)
