@@ -275,7 +275,12 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  * force / adjoint multiply, [3] z-pass FFT (own transform, n_m >= 256; other
  * meshes keep 256); defaults 256.  [4] is the x-pass FFT pencil width in
  * complex columns, 8 or 16 (16: two adjacent y rows of 8 kz, 128 contiguous
- * bytes per x row; own transform only); default 8.
+ * bytes per x row; own transform only); default 8.  [5] is how the z-pass
+ * inverse reads the spectrum (own transform, n_m >= 256): 1 per-thread
+ * loads, 2 one TMA tensor copy per field into shared memory (default where
+ * the driver provides the tensor-map encoder; a copy that does not complete
+ * within a bounded wait is reported by the next synchronising call as
+ * PM_ECUDA).
  *
  * pm_autotune     times every candidate of each family in turn (the others
  *                 held at their current best) on this context's scratch
@@ -288,7 +293,7 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  * pm_set_tuning   set all five explicitly (PM_EINVAL for other values)
  * pm_get_tuning   read them (host int[PM_TUNE_KINDS])
  * Results do not depend on the choice beyond the order of FP32 atomics. */
-#define PM_TUNE_KINDS 5
+#define PM_TUNE_KINDS 6
 int pm_autotune(pm_ctx *ctx, const float *s, float *ms);
 int pm_set_tuning(pm_ctx *ctx, const int *threads);
 int pm_get_tuning(pm_ctx *ctx, int *threads);

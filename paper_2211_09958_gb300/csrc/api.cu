@@ -52,6 +52,8 @@ struct pm_ctx {
     FftGeom fg{};
     float *r1 = nullptr, *r4 = nullptr;
     float2 *spec = nullptr, *tw = nullptr;
+    ZInvMap zmaps[3] = {};   // TMA descriptors of the blocked spectrum (z inverse)
+    int *d_err = nullptr;    // device error flag (bounded TMA waits)
     bool have_plans = false;
     void *work = nullptr;
     std::string err;
@@ -76,7 +78,7 @@ struct pm_ctx {
     std::vector<GraphEntry> graphs;
     // launch shapes of the tunable kernel families: block sizes of paint,
     // read, spectral force/adjoint, z-pass FFT (n >= 256); x-pass pencil width
-    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8};
+    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8, 2};
     // learned force correction (own-FFT meshes only)
     bool nn_on = false;
     void *nn_packed = nullptr;
@@ -464,6 +466,19 @@ int run_graphed(pm_ctx *ctx, int kind, int b, int e, const void *q0, const void 
 
 double a_of(pm_ctx *ctx, int n) { return step_a(ctx->P, n); }
 
+// Report (and clear) a device-side error flag (a TMA wait that timed out);
+// call after a stream synchronisation.
+int device_check(pm_ctx *ctx) {
+    if (!ctx->d_err) return PM_OK;
+    int flag = 0;
+    PM_CUDA(ctx, cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        PM_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+        return fail(ctx, PM_ECUDA, "a bounded device wait (TMA copy of the spectrum) timed out");
+    }
+    return PM_OK;
+}
+
 int check_ptr(pm_ctx *ctx, const void *p, const char *name) {
     if (!p) return fail(ctx, PM_EINVAL, std::string(name) + " must not be NULL");
     if ((uintptr_t)p % 4) return fail(ctx, PM_EINVAL, std::string(name) + " must be 4-byte aligned");
@@ -603,15 +618,18 @@ const char *pm_last_error(const pm_ctx *ctx) { return ctx ? ctx->err.c_str() : g
 
 int64_t pm_launch_count(const pm_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
-const int kTuneCand[PM_TUNE_KINDS][3] = {{128, 256, 512}, {128, 256, 512}, {128, 256, 512}, {128, 256, 512}, {8, 16, 0}};
+const int kTuneCand[PM_TUNE_KINDS][3] = {{128, 256, 512}, {128, 256, 512}, {128, 256, 512},
+                                         {128, 256, 512}, {8, 16, 0},      {1, 2, 0}};
 
 static int set_tuning(pm_ctx *ctx, const int *t) {
     for (int k = 0; k < PM_TUNE_KINDS; ++k)
         if (t[k] <= 0 || (t[k] != kTuneCand[k][0] && t[k] != kTuneCand[k][1] && t[k] != kTuneCand[k][2]))
-            return fail(ctx, PM_EINVAL, "block sizes must be 128, 256 or 512 and the x-pass width 8 or 16");
+            return fail(ctx, PM_EINVAL,
+                        "block sizes must be 128, 256 or 512, the x-pass width 8 or 16, the z staging 1 or 2");
     for (int k = 0; k < PM_TUNE_KINDS; ++k) ctx->tune[k] = t[k];
     ctx->fg.zthreads = ctx->tune[3];
     ctx->fg.xwidth = ctx->tune[4];
+    ctx->fg.ztma = ctx->tune[5] == 2;
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);  // captured with the old shapes
     ctx->graphs.clear();
     return PM_OK;
@@ -669,6 +687,10 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
             if ((e = launch_fft_pencils(0, false, ctx->spec, 0, 4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
             return launch_fft_pencils(0, true, ctx->spec, 0, 4, ctx->fg, ctx->stream);
         }
+        if (kind == 5) {
+            if ((e = launch_fft_z_inv(3, ctx->spec, ctx->r4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
+            return launch_fft_z_inv(4, ctx->spec, ctx->r4, ctx->fg, ctx->stream);
+        }
         if ((e = launch_fft_z_fwd(1, ctx->r1, ctx->spec, ctx->fg, ctx->stream)) != cudaSuccess) return e;
         if ((e = launch_fft_z_fwd(4, ctx->r4, ctx->spec, ctx->fg, ctx->stream)) != cudaSuccess) return e;
         if ((e = launch_fft_z_inv(3, ctx->spec, ctx->r4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
@@ -678,7 +700,8 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
     for (int k = 0; k < PM_TUNE_KINDS; ++k) best[k] = ctx->tune[k];
     rc = force_meshes(ctx, s, nullptr);
     for (int kind = 0; kind < PM_TUNE_KINDS && rc == PM_OK; ++kind) {
-        if ((kind == 3 && !(ctx->own && ctx->P.n_m >= 256)) || (kind == 4 && !ctx->own)) {
+        if ((kind == 3 && !(ctx->own && ctx->P.n_m >= 256)) || (kind == 4 && !ctx->own) ||
+            (kind == 5 && !(ctx->own && ctx->zmaps[0].valid))) {
             if (ms) ms[3 * kind] = ms[3 * kind + 1] = ms[3 * kind + 2] = 0.f;
             continue;
         }
@@ -822,6 +845,15 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
             return bail(PM_ENOMEM);
         }
         ctx->fg.tw = ctx->tw;
+        if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            fail(ctx, PM_ENOMEM, "cannot allocate the device error flag");
+            return bail(PM_ENOMEM);
+        }
+        ctx->fg.err = ctx->d_err;
+        ctx->fg.tmaps = ctx->zmaps;
+        ctx->fg.ztma = encode_z_inv_maps(ctx->spec, ctx->fg, ctx->zmaps) ? 1 : 0;
+        ctx->tune[5] = ctx->fg.ztma ? 2 : 1;
     } else if (cudaMalloc(&ctx->mesh, sizeof(float) * (size_t)ctx->mesh_pad * B * kMeshFields) != cudaSuccess) {
         cudaGetLastError();
         fail(ctx, PM_ENOMEM, "cannot allocate the FFT meshes");
@@ -906,7 +938,7 @@ int pm_destroy(pm_ctx *ctx) {
                     (void *)ctx->nn_err, (void *)ctx->nn_feat})
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-    for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->spec, (void *)ctx->tw}) 
+    for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->spec, (void *)ctx->tw, (void *)ctx->d_err}) 
         if (p) cudaFree(p);
     for (void *p : {(void *)ctx->mesh, (void *)ctx->lat, (void *)ctx->d_table, (void *)ctx->d_pref, (void *)ctx->d_grad, (void *)ctx->d_dec,
                     (void *)ctx->d_fac, (void *)ctx->d_lin, (void *)ctx->d_red, (void *)ctx->d_pk,
@@ -1115,6 +1147,7 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
         PM_CUDA(ctx, cudaMemcpyAsync(red.data(), ctx->d_red, sizeof(double) * red.size(), cudaMemcpyDeviceToHost,
                                      ctx->stream));
         PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        PM_TRY(device_check(ctx));
         for (int b = 0; b < B; ++b) {
             const HostTables &t = ctx->tabs[b];
             const double om = ctx->om[b];

@@ -26,6 +26,8 @@
 // fully unrolled.  Twiddles come from a table of W_1024^j computed in double
 // precision on the host; the 32 register-FFT twiddles sit in constant memory.
 
+#include <cuda.h>
+
 #include <cmath>
 
 #include "pm_internal.h"
@@ -180,19 +182,72 @@ __global__ void __launch_bounds__(T) k_fft_z_fwd(const float *__restrict__ in, f
     }
 }
 
+// Bounded wait on an mbarrier phase (TMA completion).
+__device__ __forceinline__ bool tma_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Inverse: spectrum fields 0 .. GS-1 -> real mesh with GO interleaved
 // slots per cell (GO = 4: slots >= GS written as 0; GO = 1: plain rows).
-template <int N, int GS, int GO, int T>
-__global__ void __launch_bounds__(T) k_fft_z_inv(const float2 *__restrict__ spec, float *out, FftGeom fg) {
+// TMA: the block's Y rows of each field, kz blocks 0 .. M/8, arrive in
+// shared memory by one 5-D tensor copy per field ([16 floats][y][x][kz
+// block][field, run]; box 16 x Y x 1 x (M/8 + 1) x 1) instead of per-thread
+// loads; the staged rows share the space of the line buffers (consumed
+// into registers before the transforms write there).
+template <int N, int GS, int GO, int T, bool TMA>
+__global__ void __launch_bounds__(T) k_fft_z_inv(const float2 *__restrict__ spec, float *out, FftGeom fg,
+                                                 const __grid_constant__ CUtensorMap tmap) {
     using S = ZShape<N, GO, T>;
     constexpr int M = S::M, TL = S::TL, Y = S::Y, LP = S::LP;
-    extern __shared__ float4 smraw[];
+    constexpr int NB = M / 8 + 1;  // kz blocks holding kz = 0 .. M
+    extern __shared__ __align__(128) float4 smraw[];  // TMA destination: 128-byte aligned
     float2 *sm = reinterpret_cast<float2 *>(smraw);
     const int tid = threadIdx.x, line = tid / TL, t = tid % TL;
     constexpr int NYB = N / Y;
     const int y0 = (int)(blockIdx.x % NYB) * Y;
     const int64_t bx = blockIdx.x / NYB;
     const int yl = line / GO, g = line % GO;
+    if (TMA) {
+        __shared__ __align__(8) uint64_t bar_mem;
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bar_mem);
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        int ok = 1;
+        if (tid == 0) {
+            constexpr uint32_t bytes = GS * NB * Y * 64;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+            const int run = (int)(bx / N), xx = (int)(bx % N);
+            const uint32_t dst0 = (uint32_t)__cvta_generic_to_shared(sm);
+#pragma unroll
+            for (int f = 0; f < GS; ++f) {
+                const int c4 = f * fg.nb + run;
+                asm volatile(
+                    "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                    "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst0 + f * NB * Y * 64),
+                    "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(y0), "r"(xx), "r"(0), "r"(c4), "r"(bar)
+                    : "memory");
+            }
+            ok = tma_wait(bar, 0);
+            if (!ok) {
+                atomicExch(fg.err, 1);
+                tma_wait(bar, 0);  // let the copies in flight land before the block exits (bounded)
+            }
+        }
+        if (!__syncthreads_and(ok)) return;
+    }
     {
         // step 1 of the inverse M-point FFT starts from Z_k, k = t + M1 n2,
         // built from the half-spectrum pair (X_k, X_{M-k}):
@@ -204,10 +259,19 @@ __global__ void __launch_bounds__(T) k_fft_z_inv(const float2 *__restrict__ spec
             const int64_t run = bx / N, xx = bx % N;
             const float2 *src = spec + g * fg.fstride + (run * (fg.zc / 8) * N * N + xx * N + y0 + yl) * 8;
             constexpr int64_t KB = (int64_t)N * N * 8;
+            // staged: field g, kz block b, row yl at sm[((g NB + b) Y + yl) 8]
+            const float2 *stg = sm + ((int64_t)g * NB * Y + yl) * 8;
 #pragma unroll
             for (int n2 = 0; n2 < M2; ++n2) {
                 const int k = t + M1 * n2, km = M - k;
-                float2 xk = __ldg(src + (k >> 3) * KB + (k & 7)), xm = __ldg(src + (km >> 3) * KB + (km & 7));
+                float2 xk, xm;
+                if (TMA) {
+                    xk = stg[(k >> 3) * Y * 8 + (k & 7)];
+                    xm = stg[(km >> 3) * Y * 8 + (km & 7)];
+                } else {
+                    xk = __ldg(src + (k >> 3) * KB + (k & 7));
+                    xm = __ldg(src + (km >> 3) * KB + (km & 7));
+                }
                 if (k == 0) {
                     xk.y = 0.f;
                     xm.y = 0.f;
@@ -221,6 +285,7 @@ __global__ void __launch_bounds__(T) k_fft_z_inv(const float2 *__restrict__ spec
 #pragma unroll
             for (int n2 = 0; n2 < M2; ++n2) v[n2] = make_float2(0.f, 0.f);
         }
+        if (TMA) __syncthreads();  // every staged value is in registers before the line buffers reuse the space
         line_fft_regs<M, true>(v, sm + line * LP, t, fg.tw);
     }
     __syncthreads();
@@ -309,16 +374,28 @@ cudaError_t z_fwd_t(const float *in, float2 *spec, const FftGeom &fg, cudaStream
     return cudaGetLastError();
 }
 
-template <int N, int GS, int GO, int T>
-cudaError_t z_inv_t(const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st) {
+template <int N, int GS, int GO, int T, bool TMA>
+cudaError_t z_inv_tt(const float2 *spec, float *out, const FftGeom &fg, const CUtensorMap &tmap, cudaStream_t st) {
     using S = ZShape<N, GO, T>;
-    const size_t smem = sizeof(float2) * S::LINES * S::LP;
+    const size_t lines = sizeof(float2) * S::LINES * S::LP, staged = (size_t)GS * (S::M / 8 + 1) * S::Y * 64;
+    const size_t smem = TMA && staged > lines ? staged : lines;
     cudaError_t e =
-        cudaFuncSetAttribute(k_fft_z_inv<N, GS, GO, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_fft_z_inv<N, GS, GO, T, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)fg.nb * N * (N / S::Y);
-    k_fft_z_inv<N, GS, GO, T><<<(unsigned)blocks, S::THREADS, smem, st>>>(spec, out, fg);
+    k_fft_z_inv<N, GS, GO, T, TMA><<<(unsigned)blocks, S::THREADS, smem, st>>>(spec, out, fg, tmap);
     return cudaGetLastError();
+}
+
+// TMA staging where a map for this block shape exists (n >= 256, 4 output
+// slots, own transform), per-thread loads otherwise.
+template <int N, int GS, int GO, int T>
+cudaError_t z_inv_t(const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st) {
+    constexpr int ti = T == 128 ? 0 : (T == 256 ? 1 : 2);
+    if (N >= 256 && GO == 4 && fg.ztma && fg.tmaps && fg.tmaps[ti].valid)
+        return z_inv_tt<N, GS, GO, T, (N >= 256 && GO == 4)>(spec, out, fg, fg.tmaps[ti].map, st);
+    static const CUtensorMap none{};
+    return z_inv_tt<N, GS, GO, T, false>(spec, out, fg, none, st);
 }
 
 // Block-size variants (the autotuner's choice) only where rows are long
@@ -435,6 +512,44 @@ cudaError_t upload_fft_constants(float2 *tw_dev) {
     cudaError_t e = cudaMemcpyToSymbol(c_w32, w32, sizeof(w32));
     if (e != cudaSuccess) return e;
     return cudaMemcpy(tw_dev, w1024, sizeof(w1024), cudaMemcpyHostToDevice);
+}
+
+int z_inv_rows(int n, int threads) {
+    const int m = n / 2, tl = m / (1 << ((ilog2(m) + 1) / 2)), y = threads / tl / 4;
+    return y < n ? y : n;
+}
+
+// 5-D tensor maps over the blocked spectrum for the TMA z inverse, one per
+// block size (rows per block Y): dims, innermost first, [16 floats][y][x][kz
+// block][field * nb + run], box [16][Y][1][n/16 + 1][1].  Returns false (and
+// leaves the maps invalid) when the driver entry point is unavailable.
+bool encode_z_inv_maps(float2 *spec, const FftGeom &fg, ZInvMap maps[3]) {
+    for (int i = 0; i < 3; ++i) maps[i].valid = false;
+    if (fg.n < 256) return false;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return false;
+    }
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    Encode encode = reinterpret_cast<Encode>(fn);
+    const uint64_t n = fg.n;
+    const cuuint64_t dims[5] = {16, n, n, (cuuint64_t)(fg.zc / 8), (cuuint64_t)(4 * fg.nb)};
+    const cuuint64_t strides[4] = {64, n * 64, n * n * 64, (cuuint64_t)(fg.zc / 8) * n * n * 64};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const int threads[3] = {128, 256, 512};
+    for (int i = 0; i < 3; ++i) {
+        const cuuint32_t box[5] = {16, (cuuint32_t)z_inv_rows(fg.n, threads[i]), 1, (cuuint32_t)(fg.n / 16 + 1), 1};
+        const CUresult r = encode(&maps[i].map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, spec, dims, strides, box, estr,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        maps[i].valid = r == CUDA_SUCCESS;
+    }
+    return maps[0].valid && maps[1].valid && maps[2].valid;
 }
 
 cudaError_t launch_fft_z_fwd(int g, const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {

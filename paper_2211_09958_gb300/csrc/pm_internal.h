@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 PM library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -149,11 +150,19 @@ struct Spec {
 };
 
 // The library's own FFT (fft_kernels.cu): spectra [field][run][kz/8][x][y][kz%8].
+struct ZInvMap {
+    CUtensorMap map;  // TMA descriptor of the blocked spectrum for one z-inverse block shape
+    bool valid;
+};
+
 struct FftGeom {
     int n, nb, zc;
     int64_t fstride;    // complex elements per spectrum field (all runs)
     const float2 *tw;   // W_1024^j, j < 1024
     int zthreads;       // z-pass block size for n >= 256: 128, 256 (also for 0) or 512 (autotuned)
+    int ztma;           // z inverse: 1 = stage the spectrum rows with TMA (where maps exist)
+    const ZInvMap *tmaps;  // host array [3] (block sizes 128, 256, 512), or NULL
+    int *err;           // device flag set when a TMA wait times out
     int xwidth;         // x-pass pencil width in complex columns: 8 (also for 0) or 16 (autotuned)
 };
 
@@ -165,6 +174,7 @@ bool own_fft_supported(int n);
 int own_fft_zc(int n);
 cudaError_t upload_fft_constants(float2 *tw_dev);
 cudaError_t launch_fft_z_fwd(int g, const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st);
+bool encode_z_inv_maps(float2 *spec, const FftGeom &fg, ZInvMap maps[3]);
 // gs = 4 or 3: spectrum fields -> 4-slot interleaved real mesh; gs = 1: plain real mesh.
 cudaError_t launch_fft_z_inv(int gs, const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st);
 cudaError_t launch_fft_pencils(int axis, bool inverse, float2 *spec, int f0, int nf, const FftGeom &fg,

@@ -10,10 +10,10 @@ from paper_2211_09958_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x")
+FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x", "z_staging")
 CANDIDATES = {"paint": (128, 256, 512), "read": (128, 256, 512), "spectral": (128, 256, 512),
-              "fft_z": (128, 256, 512), "fft_x": (8, 16)}
-DEFAULT = {"paint": 256, "read": 256, "spectral": 256, "fft_z": 256, "fft_x": 8}
+              "fft_z": (128, 256, 512), "fft_x": (8, 16), "z_staging": (1, 2)}
+DEFAULT = {"paint": 256, "read": 256, "spectral": 256, "fft_z": 256, "fft_x": 8, "z_staging": 2}
 
 
 def _pm(n_p=32, n_m=256, box=128.0, steps=3):
@@ -31,15 +31,15 @@ def test_every_block_size_gives_the_same_force_and_trajectory():
     scale_f = ref_f.abs().max().item()
     for fam in FAMILIES:
         for t in CANDIDATES[fam]:
-            if t == DEFAULT[fam]:
+            if t == DEFAULT[fam] or fam == "z_staging":
                 continue
-            pm.set_tuning(**{fam: t})
+            pm.set_tuning(**{fam: t, "z_staging": 2})
             f = pm.pm_force(s0)
             assert (f - ref_f).abs().max().item() <= 2e-5 * scale_f, (fam, t)
             s2, p2 = s.clone(), p.clone()
             pm.integrate(s2, p2)
             assert (s2 - ref_s).abs().max().item() <= 1e-5 * pm.box / pm.n_p, (fam, t)
-            pm.set_tuning()
+            pm.set_tuning(z_staging=2)
     assert pm.get_tuning() == DEFAULT
 
 
@@ -61,6 +61,25 @@ def test_small_mesh_keeps_the_default_z_pass():
     s, _ = pm.init_lpt(seed=1)
     chosen, ms = pm.autotune(s)
     assert chosen["fft_z"] == 256 and np.all(ms[3] == 0)
+    assert chosen["z_staging"] == 1 and np.all(ms[5] == 0)       # no TMA maps below n_m = 256
+
+
+def test_tma_and_load_staging_give_the_same_adjoint():
+    # the z inverse with TMA-staged spectrum rows against per-thread loads,
+    # through a full adjoint step (force and psi meshes)
+    pm = _pm(n_p=32, n_m=256, box=128.0, steps=2)
+    assert pm.get_tuning()["z_staging"] == 2                      # TMA is the default at n_m = 256
+    s, p = pm.init_lpt(seed=8)
+    f = pm.integrate(s, p)
+    lam = torch.from_numpy(np.random.default_rng(2).standard_normal(tuple(s.shape)).astype(np.float32)).cuda()
+    out = {}
+    for staging in (2, 1):
+        pm.set_tuning(z_staging=staging)
+        s2, p2, l2, m2 = s.clone(), p.clone(), lam.clone(), torch.zeros_like(p)
+        dom = pm.adjoint_integrate(s2, p2, f.clone(), l2, m2)
+        out[staging] = (l2, m2, dom)
+    for a, b in zip(out[1][:2], out[2][:2]):
+        assert (a - b).abs().max().item() <= 1e-4 * b.abs().max().item()
 
 
 def test_invalid_block_size_is_rejected():
