@@ -90,3 +90,15 @@ def test_invalid_block_size_is_rejected():
     with pytest.raises(PMError):
         pm.set_tuning(fft_x=32)
     assert pm.get_tuning()["paint"] == 256
+
+
+def test_tma_staging_gives_the_same_forces_and_power():
+    pm = _pm(n_p=32, n_m=256, box=128.0, steps=2)
+    s = torch.from_numpy(inputs.random_displacements(32, 128.0, seed=4, scale=0.5)).cuda()[None]
+    res = {}
+    for staging in (2, 1):
+        pm.set_tuning(z_staging=staging)
+        res[staging] = (pm.pm_force(s), pm.power_spectrum(s)[1])
+    f2, f1 = res[2][0], res[1][0]
+    assert (f2 - f1).abs().max().item() <= 2e-5 * f1.abs().max().item()
+    np.testing.assert_allclose(res[2][1], res[1][1], rtol=1e-5)
