@@ -280,7 +280,9 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  * loads, 2 one TMA tensor copy per field into shared memory (default where
  * the driver provides the tensor-map encoder; a copy that does not complete
  * within a bounded wait is reported by the next synchronising call as
- * PM_ECUDA).
+ * PM_ECUDA).  [6] is how the z-pass forward of 4 interleaved fields reads its
+ * rows (own transform): 1 per-thread strided loads, 2 coalesced 16-byte
+ * loads staged through shared memory; default 1.
  *
  * pm_autotune     times every candidate of each family in turn (the others
  *                 held at their current best) on this context's scratch
@@ -293,7 +295,7 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  * pm_set_tuning   set all five explicitly (PM_EINVAL for other values)
  * pm_get_tuning   read them (host int[PM_TUNE_KINDS])
  * Results do not depend on the choice beyond the order of FP32 atomics. */
-#define PM_TUNE_KINDS 6
+#define PM_TUNE_KINDS 7
 int pm_autotune(pm_ctx *ctx, const float *s, float *ms);
 int pm_set_tuning(pm_ctx *ctx, const int *threads);
 int pm_get_tuning(pm_ctx *ctx, int *threads);

@@ -78,7 +78,7 @@ struct pm_ctx {
     std::vector<GraphEntry> graphs;
     // launch shapes of the tunable kernel families: block sizes of paint,
     // read, spectral force/adjoint, z-pass FFT (n >= 256); x-pass pencil width
-    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8, 2};
+    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8, 2, 1};
     // learned force correction (own-FFT meshes only)
     bool nn_on = false;
     void *nn_packed = nullptr;
@@ -619,17 +619,19 @@ const char *pm_last_error(const pm_ctx *ctx) { return ctx ? ctx->err.c_str() : g
 int64_t pm_launch_count(const pm_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 const int kTuneCand[PM_TUNE_KINDS][3] = {{128, 256, 512}, {128, 256, 512}, {128, 256, 512},
-                                         {128, 256, 512}, {8, 16, 0},      {1, 2, 0}};
+                                         {128, 256, 512}, {8, 16, 0},      {1, 2, 0},
+                                         {1, 2, 0}};
 
 static int set_tuning(pm_ctx *ctx, const int *t) {
     for (int k = 0; k < PM_TUNE_KINDS; ++k)
         if (t[k] <= 0 || (t[k] != kTuneCand[k][0] && t[k] != kTuneCand[k][1] && t[k] != kTuneCand[k][2]))
             return fail(ctx, PM_EINVAL,
-                        "block sizes must be 128, 256 or 512, the x-pass width 8 or 16, the z staging 1 or 2");
+                        "block sizes must be 128, 256 or 512, the x-pass width 8 or 16, the z stagings 1 or 2");
     for (int k = 0; k < PM_TUNE_KINDS; ++k) ctx->tune[k] = t[k];
     ctx->fg.zthreads = ctx->tune[3];
     ctx->fg.xwidth = ctx->tune[4];
     ctx->fg.ztma = ctx->tune[5] == 2;
+    ctx->fg.zstage = ctx->tune[6] == 2;
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);  // captured with the old shapes
     ctx->graphs.clear();
     return PM_OK;
@@ -687,6 +689,7 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
             if ((e = launch_fft_pencils(0, false, ctx->spec, 0, 4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
             return launch_fft_pencils(0, true, ctx->spec, 0, 4, ctx->fg, ctx->stream);
         }
+        if (kind == 6) return launch_fft_z_fwd(4, ctx->r4, ctx->spec, ctx->fg, ctx->stream);
         if (kind == 5) {
             if ((e = launch_fft_z_inv(3, ctx->spec, ctx->r4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
             return launch_fft_z_inv(4, ctx->spec, ctx->r4, ctx->fg, ctx->stream);
@@ -701,7 +704,7 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
     rc = force_meshes(ctx, s, nullptr);
     for (int kind = 0; kind < PM_TUNE_KINDS && rc == PM_OK; ++kind) {
         if ((kind == 3 && !(ctx->own && ctx->P.n_m >= 256)) || (kind == 4 && !ctx->own) ||
-            (kind == 5 && !(ctx->own && ctx->zmaps[0].valid))) {
+            (kind == 5 && !(ctx->own && ctx->zmaps[0].valid)) || (kind == 6 && !ctx->own)) {
             if (ms) ms[3 * kind] = ms[3 * kind + 1] = ms[3 * kind + 2] = 0.f;
             continue;
         }

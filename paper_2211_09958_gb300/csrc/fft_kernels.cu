@@ -134,8 +134,10 @@ struct ZShape {
     static constexpr int LINES = Y * G, THREADS = LINES * TL;
 };
 
-// Forward: G interleaved real fields -> spectrum fields 0 .. G-1.
-template <int N, int G, int T>
+// Forward: G interleaved real fields -> spectrum fields 0 .. G-1.  STAGE
+// (G = 4, autotuned): the block's rows arrive through coalesced 16-byte
+// loads into the line buffers instead of per-thread strided loads.
+template <int N, int G, int T, bool STAGE>
 __global__ void __launch_bounds__(T) k_fft_z_fwd(const float *__restrict__ in, float2 *spec, FftGeom fg) {
     using S = ZShape<N, G, T>;
     constexpr int M = S::M, TL = S::TL, Y = S::Y, LP = S::LP;
@@ -146,7 +148,23 @@ __global__ void __launch_bounds__(T) k_fft_z_fwd(const float *__restrict__ in, f
     const int y0 = (int)(blockIdx.x % NYB) * Y;
     const int64_t bx = blockIdx.x / NYB;  // run * N + x
     const int yl = line / G, g = line % G;
-    {
+    if (G == 4 && STAGE) {
+        // line (yl, g) gets the reals of row y0 + yl, field g, as floats
+        // 0 .. N-1, from coalesced 16-byte loads (one float4 = the 4 fields
+        // of one cell)
+        const float4 *src = reinterpret_cast<const float4 *>(in) + (bx * N + y0) * (int64_t)N;
+        float *fl = reinterpret_cast<float *>(sm);
+        for (int e = tid; e < Y * N; e += S::THREADS) {
+            const float4 v = __ldg(src + e);
+            float *l0 = fl + (e / N) * 4 * (2 * LP) + (e % N);
+            l0[0] = v.x;
+            l0[2 * LP] = v.y;
+            l0[4 * LP] = v.z;
+            l0[6 * LP] = v.w;
+        }
+        __syncthreads();
+        line_fft<M, false>(sm + line * LP, t, fg.tw);
+    } else {
         // point n of line (row y0 + yl, field g) is the complex pair of reals
         // (2n, 2n + 1), i.e. floats G (2n) + g and G (2n + 1) + g of the row
         constexpr int M1 = lsplit(M), M2 = msplit(M);
@@ -362,16 +380,22 @@ __global__ void __launch_bounds__(PencilShape<L, W>::THREADS, PencilShape<L, W>:
     }
 }
 
-template <int N, int G, int T>
-cudaError_t z_fwd_t(const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {
+template <int N, int G, int T, bool STAGE>
+cudaError_t z_fwd_tt(const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {
     using S = ZShape<N, G, T>;
     const size_t smem = sizeof(float2) * S::LINES * S::LP;
     cudaError_t e =
-        cudaFuncSetAttribute(k_fft_z_fwd<N, G, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_fft_z_fwd<N, G, T, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)fg.nb * N * (N / S::Y);
-    k_fft_z_fwd<N, G, T><<<(unsigned)blocks, S::THREADS, smem, st>>>(in, spec, fg);
+    k_fft_z_fwd<N, G, T, STAGE><<<(unsigned)blocks, S::THREADS, smem, st>>>(in, spec, fg);
     return cudaGetLastError();
+}
+
+template <int N, int G, int T>
+cudaError_t z_fwd_t(const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {
+    if (G == 4 && fg.zstage) return z_fwd_tt<N, G, T, (G == 4)>(in, spec, fg, st);
+    return z_fwd_tt<N, G, T, false>(in, spec, fg, st);
 }
 
 template <int N, int GS, int GO, int T, bool TMA>

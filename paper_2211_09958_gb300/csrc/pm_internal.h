@@ -161,6 +161,7 @@ struct FftGeom {
     const float2 *tw;   // W_1024^j, j < 1024
     int zthreads;       // z-pass block size for n >= 256: 128, 256 (also for 0) or 512 (autotuned)
     int ztma;           // z inverse: 1 = stage the spectrum rows with TMA (where maps exist)
+    int zstage;         // z forward (4 fields): 1 = coalesced 16-byte staging of the input rows
     const ZInvMap *tmaps;  // host array [3] (block sizes 128, 256, 512), or NULL
     int *err;           // device flag set when a TMA wait times out
     int xwidth;         // x-pass pencil width in complex columns: 8 (also for 0) or 16 (autotuned)
