@@ -89,7 +89,7 @@ def forward(x, theta, rounding=True):
 
 def correction_mesh(s, a, theta, setup, rounding=True):
     """dF on the coarse mesh, (n^3, 3), for particles at displacement s."""
-    rho = setup.alpha * pm.cic_paint(pm.positions(s, setup), setup.n_m, setup.cell)
+    rho = setup.alpha * pm.cic_paint(pm.positions(s, setup), setup.n_m, setup.cell, order=setup.order)
     y, _ = forward(features(rho, a), theta, rounding)
     return output_scale(setup) * y
 
@@ -103,7 +103,7 @@ def predict(s, a, theta, setup, rounding=True):
     dfm = correction_mesh(s, a, theta, setup, rounding)
     x = pm.positions(s, setup)
     n = setup.n_m
-    return np.stack([pm.cic_read(x, dfm[:, j].reshape(n, n, n), setup.cell) for j in range(3)], axis=1)
+    return np.stack([pm.cic_read(x, dfm[:, j].reshape(n, n, n), setup.cell, setup.order) for j in range(3)], axis=1)
 
 
 def loss(s, target, a, theta, setup, rounding=True):
@@ -118,16 +118,16 @@ def loss_and_grad(s, target, a, theta, setup, rounding=True):
     p = unflatten(theta)
     n = setup.n_m
     xpos = pm.positions(s, setup)
-    rho = setup.alpha * pm.cic_paint(xpos, n, setup.cell)
+    rho = setup.alpha * pm.cic_paint(xpos, n, setup.cell, order=setup.order)
     feat = features(rho, a)
     y, (x, h1, h2) = forward(feat, theta, rounding)
     so = output_scale(setup)
-    pred = np.stack([pm.cic_read(xpos, (so * y[:, j]).reshape(n, n, n), setup.cell) for j in range(3)], axis=1)
+    pred = np.stack([pm.cic_read(xpos, (so * y[:, j]).reshape(n, n, n), setup.cell, setup.order) for j in range(3)], axis=1)
     d = pred - target
     npart = len(s)
     L = float(np.sum(d * d) / npart)
     # adjoint of the read: paint the residual cotangent 2 d / N
-    gy = np.stack([pm.cic_paint(xpos, n, setup.cell, 2.0 * d[:, j] / npart).ravel() for j in range(3)], axis=1)
+    gy = np.stack([pm.cic_paint(xpos, n, setup.cell, 2.0 * d[:, j] / npart, setup.order).ravel() for j in range(3)], axis=1)
     gy = r(so * gy)
     g = {}
     g["W3"] = h2.T @ gy

@@ -22,8 +22,12 @@ displacement s = x - q and momentum p = a^3 E dx/da.
                 where n_j is the Nyquist index; F_j(c) = IDFT; F_i = sum_c W F(c)
   solver flags  SPECTRAL_GRADIENT (1): D_j = k_j instead (exact spectral
                 gradient, zero at the Nyquist index); DECONVOLVE (2): the Green
-                function divided by the CIC window of paint and read,
-                prod_j sinc^4(k_j h / 2); LOG_A (4): steps uniform in ln a
+                function divided by the assignment window of paint and read,
+                prod_j sinc^(2 p)(k_j h / 2) (p = 2 CIC, 3 TSC); LOG_A (4):
+                steps uniform in ln a; TSC (8): triangular-shaped-cloud
+                assignment (quadratic B-spline over 3 nodes per axis:
+                j = round(u), d = u - j, weights 1/2 (1/2 - d)^2, 3/4 - d^2,
+                1/2 (1/2 + d)^2 at j - 1, j, j + 1) in paint and read
   gradient      D_j(k) = (8 sin(k_j h) - sin(2 k_j h)) / (6 h), the 4-point
                 central difference in Fourier space [reading]: it vanishes
                 smoothly at the Nyquist frequency.  With a mesh finer than the
@@ -60,6 +64,11 @@ class Setup:
     a_final: float = 1.0
     n_steps: int = 10
     solver: int = 0                   # bit mask of the solver flags below
+
+    @property
+    def order(self):
+        """Assignment order: 2 (CIC) or 3 (TSC, solver flag 8)."""
+        return 3 if self.solver & 8 else 2
 
     @property
     def cell(self):
@@ -114,20 +123,32 @@ def irfftn(a, n):
 
 # ---------------------------------------------------------------- CIC ----
 
-def cic_corners(x, n_m, cell):
-    """For each of the 8 corners: flat mesh index, weight W and dW/dx (N,3).
-    dW/dx uses the one-sided slopes -1/h, +1/h of the floor convention."""
+def _axis_weights(u, order, cell):
+    """First node, then per node k = 0 .. order-1: weight and d weight / dx,
+    per axis (arrays shaped like u)."""
+    if order == 2:                    # CIC, floor convention
+        base = np.floor(u)
+        f = u - base
+        return base.astype(np.int64), [(1.0 - f, -np.ones_like(f) / cell), (f, np.ones_like(f) / cell)]
+    j = np.floor(u + 0.5)             # TSC: nearest node j, d in [-1/2, 1/2)
+    d = u - j
+    return (j - 1).astype(np.int64), [(0.5 * (0.5 - d) ** 2, -(0.5 - d) / cell),
+                                      (0.75 - d * d, -2.0 * d / cell),
+                                      (0.5 * (0.5 + d) ** 2, (0.5 + d) / cell)]
+
+
+def cic_corners(x, n_m, cell, order=2):
+    """For each of the order^3 corners: flat mesh index, weight W and dW/dx
+    (N,3).  CIC (order 2) dW/dx uses the one-sided slopes -1/h, +1/h of the
+    floor convention; TSC (order 3) weights are C^1."""
     u = x / cell
-    base = np.floor(u)
-    f = u - base
-    base = base.astype(np.int64)
+    base, ax = _axis_weights(u, order, cell)
     out = []
-    for off in itertools.product((0, 1), repeat=3):
-        off = np.array(off)
-        idx = (base + off) % n_m
+    for off in itertools.product(range(order), repeat=3):
+        idx = (base + np.array(off)) % n_m
         flat = (idx[:, 0] * n_m + idx[:, 1]) * n_m + idx[:, 2]
-        w1 = np.where(off == 1, f, 1.0 - f)
-        dw1 = np.where(off == 1, 1.0, -1.0) / cell
+        w1 = np.stack([ax[off[d]][0][:, d] for d in range(3)], axis=1)
+        dw1 = [ax[off[d]][1][:, d] for d in range(3)]
         w = w1[:, 0] * w1[:, 1] * w1[:, 2]
         grad = np.stack([dw1[0] * w1[:, 1] * w1[:, 2],
                          w1[:, 0] * dw1[1] * w1[:, 2],
@@ -136,43 +157,43 @@ def cic_corners(x, n_m, cell):
     return out
 
 
-def cic_paint(x, n_m, cell, weights=None):
-    """sum_i weights_i W(x_i - c) on the n_m^3 mesh."""
+def cic_paint(x, n_m, cell, weights=None, order=2):
+    """sum_i weights_i W(x_i - c) on the n_m^3 mesh (CIC, or TSC for order 3)."""
     mesh = np.zeros(n_m ** 3)
     wts = np.ones(len(x)) if weights is None else weights
-    for flat, w, _ in cic_corners(x, n_m, cell):
+    for flat, w, _ in cic_corners(x, n_m, cell, order):
         mesh += np.bincount(flat, weights=w * wts, minlength=n_m ** 3)
     return mesh.reshape(n_m, n_m, n_m)
 
 
-def cic_read(x, mesh, cell):
+def cic_read(x, mesh, cell, order=2):
     """sum_c W(x_i - c) mesh(c) per particle."""
     n_m = mesh.shape[0]
     flatmesh = mesh.ravel()
     val = np.zeros(len(x))
-    for flat, w, _ in cic_corners(x, n_m, cell):
+    for flat, w, _ in cic_corners(x, n_m, cell, order):
         val += w * flatmesh[flat]
     return val
 
 
-def cic_read_grad(x, mesh, cell):
+def cic_read_grad(x, mesh, cell, order=2):
     """sum_c dW(x_i - c)/dx_i mesh(c) per particle, (N, 3)."""
     n_m = mesh.shape[0]
     flatmesh = mesh.ravel()
     val = np.zeros((len(x), 3))
-    for flat, _, grad in cic_corners(x, n_m, cell):
+    for flat, _, grad in cic_corners(x, n_m, cell, order):
         val += grad * flatmesh[flat][:, None]
     return val
 
 
 def density(s, setup):
     """CIC density contrast alpha sum W - 1 of the particles at s."""
-    return setup.alpha * cic_paint(positions(s, setup), setup.n_m, setup.cell) - 1.0
+    return setup.alpha * cic_paint(positions(s, setup), setup.n_m, setup.cell, order=setup.order) - 1.0
 
 
 # -------------------------------------------------------------- force ----
 
-SPECTRAL_GRADIENT, DECONVOLVE, LOG_A = 1, 2, 4
+SPECTRAL_GRADIENT, DECONVOLVE, LOG_A, TSC = 1, 2, 4, 8
 
 
 def gradient_operator(k, h):
@@ -181,12 +202,14 @@ def gradient_operator(k, h):
     return (8.0 * np.sin(k * h) - np.sin(2.0 * k * h)) / (6.0 * h)
 
 
-def cic_window(k, h):
-    """Fourier transform of one CIC assignment along one axis, sinc^2(k h / 2)."""
-    return np.sinc(k * h / (2.0 * np.pi)) ** 2
+def cic_window(k, h, order=2):
+    """Fourier transform of one assignment along one axis, sinc^order(k h / 2)
+    (CIC order 2, TSC order 3)."""
+    return np.sinc(k * h / (2.0 * np.pi)) ** order
 
 
 def gradient_green_multipliers(n, box, omega_m, solver=0):
+    order = 3 if solver & TSC else 2
     """i D_j (3/2) Om / k^2 on the rfft grid (D_j the 4-point difference
     gradient, or k_j with SPECTRAL_GRADIENT; k^2 exact; divided by the paint
     and read CIC windows with DECONVOLVE), zero at k = 0 and where n_j is the
@@ -196,7 +219,7 @@ def gradient_green_multipliers(n, box, omega_m, solver=0):
     k2s = np.where(k2 > 0, k2, 1.0)
     h = box / n
     if solver & DECONVOLVE:
-        k2s = k2s * (cic_window(kx, h) * cic_window(ky, h) * cic_window(kz, h)) ** 2
+        k2s = k2s * (cic_window(kx, h, order) * cic_window(ky, h, order) * cic_window(kz, h, order)) ** 2
     out = []
     for kj, mj in zip((kx, ky, kz), nyq):
         dj = kj if solver & SPECTRAL_GRADIENT else gradient_operator(kj, h)
@@ -207,7 +230,7 @@ def gradient_green_multipliers(n, box, omega_m, solver=0):
 
 
 def force_meshes(x, setup):
-    rho = setup.alpha * cic_paint(x, setup.n_m, setup.cell) - 1.0
+    rho = setup.alpha * cic_paint(x, setup.n_m, setup.cell, order=setup.order) - 1.0
     rho_k = rfftn(rho)
     mult = gradient_green_multipliers(setup.n_m, setup.box, setup.cosmo.omega_m, setup.solver)
     return [irfftn(m * rho_k, setup.n_m) for m in mult]
@@ -217,7 +240,7 @@ def force(s, setup):
     """PM force per particle, (N, 3), in lattice order."""
     x = positions(s, setup)
     meshes = force_meshes(x, setup)
-    return np.stack([cic_read(x, m, setup.cell) for m in meshes], axis=1)
+    return np.stack([cic_read(x, m, setup.cell, setup.order) for m in meshes], axis=1)
 
 
 def force_vjp(s, v, setup):
@@ -229,14 +252,14 @@ def force_vjp(s, v, setup):
     meshes = force_meshes(x, setup)
     term_a = np.zeros((len(x), 3))
     for j in range(3):
-        term_a += cic_read_grad(x, meshes[j], setup.cell) * v[:, j:j + 1]
+        term_a += cic_read_grad(x, meshes[j], setup.cell, setup.order) * v[:, j:j + 1]
     mult = gradient_green_multipliers(setup.n_m, setup.box, setup.cosmo.omega_m, setup.solver)
     psi_k = 0.0
     for j in range(3):
-        u_j = cic_paint(x, setup.n_m, setup.cell, v[:, j])
+        u_j = cic_paint(x, setup.n_m, setup.cell, v[:, j], setup.order)
         psi_k = psi_k + np.conj(mult[j]) * rfftn(u_j)
     psi = irfftn(psi_k, setup.n_m)
-    term_b = setup.alpha * cic_read_grad(x, psi, setup.cell)
+    term_b = setup.alpha * cic_read_grad(x, psi, setup.cell, setup.order)
     return term_a + term_b
 
 
@@ -328,12 +351,12 @@ def mse_loss_grad(s, target, setup):
     """dL/ds: the CIC-weight-gradient read of 2 (delta - target) / n_m^3."""
     x = positions(s, setup)
     g_mesh = 2.0 * (density(s, setup) - target) / setup.n_m ** 3
-    return setup.alpha * cic_read_grad(x, g_mesh, setup.cell)
+    return setup.alpha * cic_read_grad(x, g_mesh, setup.cell, setup.order)
 
 
 def density_vjp(s, g_mesh, setup):
     """Cotangent of s for a cotangent g_mesh of ``density(s)``."""
-    return setup.alpha * cic_read_grad(positions(s, setup), g_mesh, setup.cell)
+    return setup.alpha * cic_read_grad(positions(s, setup), g_mesh, setup.cell, setup.order)
 
 
 # ----------------------------------------------------- power spectrum ----

@@ -259,3 +259,78 @@ def test_deconvolution_flattens_the_linear_response(solver):
     plain16 = err(16, solver & ~pm.DECONVOLVE)
     dec16, dec32 = err(16, solver), err(32, solver)
     assert dec16 < plain16 / 5 and dec32 < dec16 / 5, (plain16, dec16, dec32)
+
+
+# ------------------------------------------------------------------- TSC --
+
+def _bspline2(r):
+    # quadratic B-spline of unit width (the TSC kernel), r in cells
+    a = np.abs(r)
+    return np.where(a < 0.5, 0.75 - a * a, np.where(a < 1.5, 0.5 * (1.5 - a) ** 2, 0.0))
+
+
+def _tsc_mesh(x, n, cell):
+    c = np.arange(n) * cell
+    box = n * cell
+    mesh = np.zeros((n, n, n))
+    for xi in x:
+        w = [_bspline2(((xi[d] - c + 0.5 * box) % box - 0.5 * box) / cell) for d in range(3)]
+        mesh += w[0][:, None, None] * w[1][None, :, None] * w[2][None, None, :]
+    return mesh
+
+
+def test_tsc_paint_and_read_equal_the_bspline_definition():
+    rng = np.random.default_rng(10)
+    n, cell = 6, 1.3
+    x = _special_positions(rng, n, cell, 40)
+    x[4] = [0.5 * cell, 1.5 * cell, 2.5 * cell]                 # half-node ties
+    np.testing.assert_allclose(pm.cic_paint(x, n, cell, order=3), _tsc_mesh(x, n, cell), atol=1e-12)
+    mesh = rng.standard_normal((n, n, n))
+    ref = np.array([np.sum(_tsc_mesh(xi[None], n, cell) * mesh) for xi in x])
+    np.testing.assert_allclose(pm.cic_read(x, mesh, cell, order=3), ref, atol=1e-12)
+
+
+def test_tsc_mass_conservation_and_gradient():
+    rng = np.random.default_rng(11)
+    st = Setup(8, 16, 40.0, solver=pm.TSC)
+    s = rng.normal(0, 3.0, (8 ** 3, 3))
+    assert abs(np.sum(pm.density(s, st) + 1.0) - 16 ** 3) < 1e-9
+    n, cell = 8, 1.1
+    mesh = rng.standard_normal((n, n, n))
+    x = rng.uniform(0, n * cell, (50, 3))
+    g = pm.cic_read_grad(x, mesh, cell, order=3)
+    eps = 1e-6
+    for d in range(3):
+        dx = np.zeros(3)
+        dx[d] = eps
+        fd = (pm.cic_read(x + dx, mesh, cell, 3) - pm.cic_read(x - dx, mesh, cell, 3)) / (2 * eps)
+        np.testing.assert_allclose(g[:, d], fd, rtol=1e-6, atol=1e-6)
+
+
+def test_tsc_force_vjp_matches_finite_difference():
+    rng = np.random.default_rng(12)
+    st = Setup(4, 8, 10.0, solver=pm.TSC)
+    s = rng.normal(0, 0.6, (64, 3))
+    v = rng.standard_normal((64, 3))
+    g = pm.force_vjp(s, v, st)
+    eps = 1e-6
+    for _ in range(6):
+        d = rng.standard_normal((64, 3))
+        fd = (np.sum(v * pm.force(s + eps * d, st)) - np.sum(v * pm.force(s - eps * d, st))) / (2 * eps)
+        assert abs(fd - np.sum(g * d)) < 1e-6 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("ratio", [1, 2])
+def test_tsc_linear_force_converges(ratio):
+    # the plane-wave force F -> 3/2 Om s with an O(k^2) error, TSC at mesh
+    # ratios 1 and 2
+    errs = []
+    for n_p in (16, 32):
+        box = 8.0 * n_p
+        st = Setup(n_p, ratio * n_p, box, pm.Cosmology(0.3), solver=pm.TSC)
+        q = pm.lattice(n_p, box, ratio * n_p)
+        s = np.zeros_like(q)
+        s[:, 0] = 1e-4 * np.sin(2 * np.pi * q[:, 0] / box)
+        f = pm.force(s, st)[:, 0]
+        errs.append(abs(f @ s[:, 0] / (s[:, 0] @ s[:, 0]) / (1.5 * 0.3) - 1.0))
+    assert errs[0] < 5e-2 and errs[1] < errs[0] / 3.0, errs
