@@ -91,10 +91,17 @@ typedef struct pm_config {
  *                                (sharper force at n_m = n_p; amplifies
  *                                lattice aliasing at n_m > n_p)
  *   PM_SOLVER_LOG_A              KDK steps uniform in ln a, half steps at the
- *                                geometric midpoint */
+ *                                geometric midpoint
+ *   PM_SOLVER_TSC                triangular-shaped-cloud paint and read (the
+ *                                quadratic B-spline over 3 nodes per axis,
+ *                                nodes j - 1, j, j + 1 of the nearest node j)
+ *                                instead of cloud-in-cell; with
+ *                                PM_SOLVER_DECONVOLVE the window is
+ *                                prod_j sinc^6(k_j h / 2) */
 #define PM_SOLVER_SPECTRAL_GRADIENT 1
 #define PM_SOLVER_DECONVOLVE 2
 #define PM_SOLVER_LOG_A 4
+#define PM_SOLVER_TSC 8
 
 /* Create a context: validates cfg, computes the FP64 growth and coefficient
  * tables on the host, allocates the scratch meshes and creates the cuFFT

@@ -37,7 +37,7 @@ class PmConfig(ctypes.Structure):
     ]
 
 
-SOLVER_SPECTRAL_GRADIENT, SOLVER_DECONVOLVE, SOLVER_LOG_A = 1, 2, 4
+SOLVER_SPECTRAL_GRADIENT, SOLVER_DECONVOLVE, SOLVER_LOG_A, SOLVER_TSC = 1, 2, 4, 8
 
 
 _P = ctypes.c_void_p

@@ -795,7 +795,7 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
     if (!(c.box > 0)) return fail(nullptr, PM_EINVAL, "box must be > 0");
     if (!(c.a_init > 0 && c.a_final > c.a_init)) return fail(nullptr, PM_EINVAL, "need 0 < a_init < a_final");
     if (!(c.h > 0)) return fail(nullptr, PM_EINVAL, "h must be > 0");
-    if (c.solver & ~7) return fail(nullptr, PM_EINVAL, "unknown solver flag");
+    if (c.solver & ~15) return fail(nullptr, PM_EINVAL, "unknown solver flag");
     {
         int rc = check_cosmology(nullptr, c.omega_m, c.sigma8, c.n_batch);
         if (rc) return rc;
@@ -814,6 +814,7 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
     ctx->g.np = c.n_p;
     ctx->g.nm = c.n_m;
     ctx->g.nb = c.n_batch;
+    ctx->g.order = (c.solver & PM_SOLVER_TSC) ? 3 : 2;
     ctx->g.npart = npart;
     ctx->g.ratio = (c.n_m % c.n_p == 0) ? c.n_m / c.n_p : 0;
     ctx->g.inv_np = 1.0f / c.n_p;
@@ -888,7 +889,8 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
                                                                        : (8.0 * std::sin(kh) - std::sin(2.0 * kh)) / (6.0 * h);
             grad[j] = 2 * j == c.n_m ? 0.f : (float)d;
             const double x = 0.5 * kh, sc = nj == 0 ? 1.0 : std::sin(x) / x;
-            dec[j] = (c.solver & PM_SOLVER_DECONVOLVE) ? (float)(1.0 / (sc * sc * sc * sc)) : 1.f;
+            const double win = std::pow(sc, (c.solver & PM_SOLVER_TSC) ? 6.0 : 4.0);  // paint and read windows
+            dec[j] = (c.solver & PM_SOLVER_DECONVOLVE) ? (float)(1.0 / win) : 1.f;
         }
         if (cudaMemcpy(ctx->d_grad, grad.data(), sizeof(float) * c.n_m, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(ctx->d_dec, dec.data(), sizeof(float) * c.n_m, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -997,7 +999,7 @@ int pm_host_coefficients(const pm_config *cfg, double *kdk, double *dkdk, double
         int rc = check_cosmology(nullptr, cfg->omega_m, cfg->sigma8, cfg->n_batch);
         if (rc) return rc;
     }
-    if (cfg->solver & ~7) return fail(nullptr, PM_EINVAL, "unknown solver flag");
+    if (cfg->solver & ~15) return fail(nullptr, PM_EINVAL, "unknown solver flag");
     Params P{cfg->n_p, cfg->n_m, cfg->n_batch, cfg->n_steps, cfg->box, cfg->a_init, cfg->a_final, cfg->h, cfg->n_s,
              cfg->solver};
     const int N = cfg->n_steps;

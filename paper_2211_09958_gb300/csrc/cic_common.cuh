@@ -53,6 +53,74 @@ __device__ __forceinline__ void locate(int64_t i, float sx, float sy, float sz, 
     axis_cell(li[2], sz, g, c[2], f[2]);
 }
 
+// TSC along one axis: nearest node j = floor(t + 1/2) of the node
+// coordinate t, d = t - j in [-1/2, 1/2); c0 = j - 1 (mod n_m), the first of
+// the three nodes j - 1, j, j + 1.
+__device__ __forceinline__ void axis_tsc(int li, float sv, const Geom &g, int &c0, float &d) {
+    int qi;
+    float qf;
+    if (g.ratio) {
+        qi = li * g.ratio;
+        qf = 0.f;
+    } else {
+        const int64_t num = (int64_t)li * g.nm;
+        qi = (int)(num / g.np);
+        qf = (float)(num - (int64_t)qi * g.np) * g.inv_np;
+    }
+    const float t = qf + 0.5f + sv * g.inv_h;
+    const float fl = floorf(t + 0.5f);
+    int cj = (qi + (int)fl - 1) % g.nm;
+    if (cj < 0) cj += g.nm;
+    c0 = cj;
+    d = t - fl;
+}
+
+// The assignment stencil of one particle: K nodes per axis (2 CIC, 3 TSC),
+// their weights and d weight / dx.
+template <int K>
+struct Stencil {
+    int n[3][K];
+    float w[3][K], dw[3][K];
+};
+
+template <int K>
+__device__ __forceinline__ void stencil(int64_t i, float sx, float sy, float sz, const Geom &g, Stencil<K> &st) {
+    const int nm = g.nm;
+    if (K == 2) {
+        int c[3];
+        float f[3];
+        locate(i, sx, sy, sz, g, c, f);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            st.n[a][0] = c[a];
+            st.n[a][K - 1] = c[a] + 1 == nm ? 0 : c[a] + 1;
+            st.w[a][0] = 1.f - f[a];
+            st.w[a][K - 1] = f[a];
+            st.dw[a][0] = -g.inv_h;
+            st.dw[a][K - 1] = g.inv_h;
+        }
+    } else {
+        int li[3];
+        lattice_ijk(i, g.np, li);
+        const float sv[3] = {sx, sy, sz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int c0;
+            float d;
+            axis_tsc(li[a], sv[a], g, c0, d);
+#pragma unroll
+            for (int k = 0; k < K; ++k) st.n[a][k] = c0 + k >= nm ? c0 + k - nm : c0 + k;
+            const float lo = 0.5f - d, hi = 0.5f + d;
+            st.w[a][0] = 0.5f * lo * lo;
+            st.w[a][1] = 0.75f - d * d;
+            st.w[a][K - 1] = 0.5f * hi * hi;
+            st.dw[a][0] = -lo * g.inv_h;
+            st.dw[a][1] = -2.f * d * g.inv_h;
+            st.dw[a][K - 1] = hi * g.inv_h;
+        }
+    }
+}
+
 // Sum v over a block of THREADS threads and add it to dst[q * stride]
 // (one double atomic per block and value).  Every thread must call it.
 template <int THREADS, int N>

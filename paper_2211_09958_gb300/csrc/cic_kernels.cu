@@ -1,4 +1,5 @@
-// Cloud-in-cell (CIC) particle kernels, one thread per particle in lattice
+// Particle-mesh assignment kernels (cloud-in-cell, or triangular-shaped
+// cloud with solver flag 8: stencils in cic_common.cuh), one thread per particle in lattice
 // order: paint with global float atomics (a single 16-byte vector atomic per
 // corner when the four adjoint fields are interleaved), read with the
 // kick / adjoint update fused in, and the particle-local pre-step kernels.
@@ -26,7 +27,7 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
                  : "memory");
 }
 
-template <int MODE, int T>
+template <int MODE, int T, int K>
 __global__ void __launch_bounds__(T) k_paint(PaintArgs a) {
     const int b = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * T + threadIdx.x;
@@ -39,26 +40,21 @@ __global__ void __launch_bounds__(T) k_paint(PaintArgs a) {
         wv[2] = a.mu[gi + 1];
         wv[3] = a.mu[gi + 2];
     }
-    int c[3];
-    float f[3];
-    locate(i, sx, sy, sz, a.g, c, f);
+    cic::Stencil<K> st;
+    cic::stencil<K>(i, sx, sy, sz, a.g, st);
     const int nm = a.g.nm, zs = a.mesh.zs;
-    const int xs[2] = {c[0], c[0] + 1 == nm ? 0 : c[0] + 1};
-    const int ys[2] = {c[1], c[1] + 1 == nm ? 0 : c[1] + 1};
-    const int zz[2] = {c[2], c[2] + 1 == nm ? 0 : c[2] + 1};
-    const float wx[2] = {1.f - f[0], f[0]}, wy[2] = {1.f - f[1], f[1]}, wz[2] = {1.f - f[2], f[2]};
     float *base = a.mesh.ptr + (int64_t)b * a.mesh.bstride;
     constexpr int NF = MODE == PAINT_ADJ ? 4 : 1;
     const bool il = NF == 4 && a.mesh.il == 4;
 #pragma unroll
-    for (int ox = 0; ox < 2; ++ox)
+    for (int ox = 0; ox < K; ++ox)
 #pragma unroll
-        for (int oy = 0; oy < 2; ++oy) {
-            const int64_t row = ((int64_t)xs[ox] * nm + ys[oy]) * zs;
+        for (int oy = 0; oy < K; ++oy) {
+            const int64_t row = ((int64_t)st.n[0][ox] * nm + st.n[1][oy]) * zs;
 #pragma unroll
-            for (int oz = 0; oz < 2; ++oz) {
-                const float w = wx[ox] * wy[oy] * wz[oz];
-                const int64_t idx = row + zz[oz];
+            for (int oz = 0; oz < K; ++oz) {
+                const float w = st.w[0][ox] * st.w[1][oy] * st.w[2][oz];
+                const int64_t idx = row + st.n[2][oz];
                 if (il) {
                     red_add_v4(base + 4 * idx, w * wv[0], w * wv[1], w * wv[2], w * wv[3]);
                 } else {
@@ -69,7 +65,7 @@ __global__ void __launch_bounds__(T) k_paint(PaintArgs a) {
         }
 }
 
-template <int MODE, bool IL, int T>
+template <int MODE, bool IL, int T, int K>
 __global__ void __launch_bounds__(T) k_read(ReadArgs a) {
     const int b = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * T + threadIdx.x;
@@ -77,15 +73,11 @@ __global__ void __launch_bounds__(T) k_read(ReadArgs a) {
     if (i < a.g.npart) {
         const int64_t gi = ((int64_t)b * a.g.npart + i) * 3;
         const float sx = a.s[gi], sy = a.s[gi + 1], sz = a.s[gi + 2];
-        int c[3];
-        float f[3];
-        locate(i, sx, sy, sz, a.g, c, f);
+        cic::Stencil<K> st;
+        cic::stencil<K>(i, sx, sy, sz, a.g, st);
         const int nm = a.g.nm, zs = a.mesh.zs;
-        const int xs[2] = {c[0], c[0] + 1 == nm ? 0 : c[0] + 1};
-        const int ys[2] = {c[1], c[1] + 1 == nm ? 0 : c[1] + 1};
-        const int zz[2] = {c[2], c[2] + 1 == nm ? 0 : c[2] + 1};
-        const float wx[2] = {1.f - f[0], f[0]}, wy[2] = {1.f - f[1], f[1]}, wz[2] = {1.f - f[2], f[2]};
-        const float dw[2] = {-a.g.inv_h, a.g.inv_h};
+        const float(&wx)[K] = st.w[0], (&wy)[K] = st.w[1], (&wz)[K] = st.w[2];
+        const float(&dx)[K] = st.dw[0], (&dy)[K] = st.dw[1], (&dz)[K] = st.dw[2];
         const float *m0 = a.mesh.ptr + (int64_t)b * a.mesh.bstride;
         const float *m1 = m0 + a.mesh.fstride;
         const float *m2 = m1 + a.mesh.fstride;
@@ -98,18 +90,18 @@ __global__ void __launch_bounds__(T) k_read(ReadArgs a) {
         }
         float F[3] = {0.f, 0.f, 0.f}, G[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int ox = 0; ox < 2; ++ox)
+        for (int ox = 0; ox < K; ++ox)
 #pragma unroll
-            for (int oy = 0; oy < 2; ++oy) {
-                const int64_t row = ((int64_t)xs[ox] * nm + ys[oy]) * zs;
+            for (int oy = 0; oy < K; ++oy) {
+                const int64_t row = ((int64_t)st.n[0][ox] * nm + st.n[1][oy]) * zs;
 #pragma unroll
-                for (int oz = 0; oz < 2; ++oz) {
-                    const int64_t idx = row + zz[oz];
+                for (int oz = 0; oz < K; ++oz) {
+                    const int64_t idx = row + st.n[2][oz];
                     if (MODE == READ_GRAD) {
                         const float v = __ldg(m0 + idx);
-                        G[0] += dw[ox] * wy[oy] * wz[oz] * v;
-                        G[1] += wx[ox] * dw[oy] * wz[oz] * v;
-                        G[2] += wx[ox] * wy[oy] * dw[oz] * v;
+                        G[0] += dx[ox] * wy[oy] * wz[oz] * v;
+                        G[1] += wx[ox] * dy[oy] * wz[oz] * v;
+                        G[2] += wx[ox] * wy[oy] * dz[oz] * v;
                     } else {
                         const float w = wx[ox] * wy[oy] * wz[oz];
                         float fx, fy, fz, fp = 0.f;
@@ -130,9 +122,9 @@ __global__ void __launch_bounds__(T) k_read(ReadArgs a) {
                         F[2] += w * fz;
                         if (MODE == READ_ADJ) {
                             const float gv = mu[0] * fx + mu[1] * fy + mu[2] * fz + a.g.alpha * fp;
-                            G[0] += dw[ox] * wy[oy] * wz[oz] * gv;
-                            G[1] += wx[ox] * dw[oy] * wz[oz] * gv;
-                            G[2] += wx[ox] * wy[oy] * dw[oz] * gv;
+                            G[0] += dx[ox] * wy[oy] * wz[oz] * gv;
+                            G[1] += wx[ox] * dy[oy] * wz[oz] * gv;
+                            G[2] += wx[ox] * wy[oy] * dz[oz] * gv;
                         }
                     }
                 }
@@ -227,39 +219,43 @@ __global__ void __launch_bounds__(kThreads) k_mse(MeshRef mesh, const float *tar
 
 dim3 particle_grid(const Geom &g, int t = kThreads) { return dim3((unsigned)((g.npart + t - 1) / t), g.nb); }
 
-template <int T>
+template <int T, int K = 2>
 void paint_t(int mode, const PaintArgs &a, cudaStream_t st) {
     const dim3 grid = particle_grid(a.g, T);
     if (mode == PAINT_DENSITY)
-        k_paint<PAINT_DENSITY, T><<<grid, T, 0, st>>>(a);
+        k_paint<PAINT_DENSITY, T, K><<<grid, T, 0, st>>>(a);
     else
-        k_paint<PAINT_ADJ, T><<<grid, T, 0, st>>>(a);
+        k_paint<PAINT_ADJ, T, K><<<grid, T, 0, st>>>(a);
 }
 
-template <bool IL, int T>
+template <bool IL, int T, int K>
 void read_il(int mode, const ReadArgs &a, cudaStream_t st) {
     const dim3 grid = particle_grid(a.g, T);
     switch (mode) {
-        case READ_FORCE: k_read<READ_FORCE, IL, T><<<grid, T, 0, st>>>(a); break;
-        case READ_KICK_DRIFT: k_read<READ_KICK_DRIFT, IL, T><<<grid, T, 0, st>>>(a); break;
-        case READ_HALF_KICK: k_read<READ_HALF_KICK, IL, T><<<grid, T, 0, st>>>(a); break;
-        case READ_ADJ: k_read<READ_ADJ, IL, T><<<grid, T, 0, st>>>(a); break;
+        case READ_FORCE: k_read<READ_FORCE, IL, T, K><<<grid, T, 0, st>>>(a); break;
+        case READ_KICK_DRIFT: k_read<READ_KICK_DRIFT, IL, T, K><<<grid, T, 0, st>>>(a); break;
+        case READ_HALF_KICK: k_read<READ_HALF_KICK, IL, T, K><<<grid, T, 0, st>>>(a); break;
+        case READ_ADJ: k_read<READ_ADJ, IL, T, K><<<grid, T, 0, st>>>(a); break;
         default: break;
     }
 }
 
-template <int T>
+template <int T, int K = 2>
 void read_t(int mode, const ReadArgs &a, cudaStream_t st) {
     if (a.mesh.il == 4)
-        read_il<true, T>(mode, a, st);
+        read_il<true, T, K>(mode, a, st);
     else
-        read_il<false, T>(mode, a, st);
+        read_il<false, T, K>(mode, a, st);
 }
 
 }  // namespace
 
 cudaError_t launch_paint(int mode, const PaintArgs &a, cudaStream_t st) {
     if (mode != PAINT_DENSITY && mode != PAINT_ADJ) return cudaErrorInvalidValue;
+    if (a.g.order == 3) {  // TSC: one block size
+        paint_t<kThreads, 3>(mode, a, st);
+        return cudaGetLastError();
+    }
     switch (a.threads) {
         case 128: paint_t<128>(mode, a, st); break;
         case 512: paint_t<512>(mode, a, st); break;
@@ -270,7 +266,12 @@ cudaError_t launch_paint(int mode, const PaintArgs &a, cudaStream_t st) {
 
 cudaError_t launch_read(int mode, const ReadArgs &a, cudaStream_t st) {
     if (mode == READ_GRAD) {
-        k_read<READ_GRAD, false, kThreads><<<particle_grid(a.g), kThreads, 0, st>>>(a);
+        if (a.g.order == 3)
+            k_read<READ_GRAD, false, kThreads, 3><<<particle_grid(a.g), kThreads, 0, st>>>(a);
+        else
+            k_read<READ_GRAD, false, kThreads, 2><<<particle_grid(a.g), kThreads, 0, st>>>(a);
+    } else if (mode >= READ_FORCE && mode <= READ_ADJ && a.g.order == 3) {
+        read_t<kThreads, 3>(mode, a, st);
     } else if (mode >= READ_FORCE && mode <= READ_ADJ) {
         switch (a.threads) {
             case 128: read_t<128>(mode, a, st); break;

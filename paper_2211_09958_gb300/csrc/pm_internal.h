@@ -56,6 +56,7 @@ struct Geom {
     float inv_np;        // 1 / np
     float inv_h;         // nm / box
     float alpha;         // (nm / np)^3
+    int order;           // assignment: 2 (CIC; also for 0) or 3 (TSC, solver flag 8)
 };
 
 // A set of real meshes: field f of batch b starts at ptr + f*fstride + b*bstride;

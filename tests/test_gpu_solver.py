@@ -1,5 +1,6 @@
 """GPU parity of the solver variants (pm_config.solver, include/pmgb.h):
-the exact spectral gradient, CIC deconvolution and steps uniform in ln a,
+the exact spectral gradient, window deconvolution, steps uniform in ln a and
+TSC assignment,
 against the FP64 oracle with the same flags.  Tolerances as for the default
 solver (tests/test_gpu_parity.py): force 2e-5 of max |F|, state after the
 integration 1e-4 of the spacing and of max |p|, gradients relative L2 1e-3."""
@@ -15,7 +16,7 @@ from paper_2211_09958_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-FLAGS = [1, 2, 3]
+FLAGS = [1, 2, 3, 8, 10]
 
 
 def _pm(n_p, n_m, box, solver, steps=4):
@@ -45,7 +46,7 @@ def test_force_parity_with_solver_flags(solver, n_p, n_m, box):
     assert np.max(np.abs(f - ref)) < 2e-5 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("solver", [4, 7])
+@pytest.mark.parametrize("solver", [4, 7, 12])
 def test_integrate_parity_with_solver_flags(solver):
     pm = _pm(16, 32, 64.0, solver, steps=6)
     noise = inputs.white_noise(16, seed=12)
@@ -58,8 +59,9 @@ def test_integrate_parity_with_solver_flags(solver):
     assert np.max(np.abs(_host(p)[0] - rp)) < 1e-4 * np.max(np.abs(rp))
 
 
-def test_loss_gradient_parity_with_all_flags():
-    pm = _pm(16, 32, 64.0, 7, steps=3)
+@pytest.mark.parametrize("solver", [7, 15])
+def test_loss_gradient_parity_with_all_flags(solver):
+    pm = _pm(16, 32, 64.0, solver, steps=3)
     noise = inputs.white_noise(16, seed=4)
     target = inputs.target_field(32, seed=5)
     from paper_2211_09958_gb300.pm import simulate, density
@@ -70,7 +72,7 @@ def test_loss_gradient_parity_with_all_flags():
     d = density(pm, s)
     loss = ((d - _cuda(target)[None]) ** 2).mean()
     loss.backward()
-    st = _setup(pm, 7)
+    st = _setup(pm, solver)
     rl, rg, _, _ = opm.loss_and_grad(noise.astype(np.float64), target.astype(np.float64), st)
     assert abs(loss.item() - rl) <= 1e-4 * abs(rl)
     g = _host(nz.grad)[0]

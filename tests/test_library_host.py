@@ -88,7 +88,7 @@ def test_log_a_tables_match_oracle(lib, steps):
 
 
 def test_unknown_solver_flag_is_rejected(lib):
-    cfg = _pmgb.make_config(32, 64, 128.0, [0.3], [0.8], 4, solver=8)
+    cfg = _pmgb.make_config(32, 64, 128.0, [0.3], [0.8], 4, solver=16)
     out = ctypes.c_void_p()
     assert lib.pm_create(ctypes.byref(cfg), ctypes.byref(out)) == -1
     assert b"solver" in lib.pm_last_error(None)
