@@ -171,6 +171,20 @@ def _ncu_traffic(kind, workload):
     return ent["dram_bytes_per_launch"] * (scale if scale else 1.0) if (scale or ent.get("workload") == workload) else None
 
 
+def replica_throughput(dist, world, work, steps, times_ms, device="cpu"):
+    """Whole-job throughput of `world` independent replicas: each rank did
+    `work` units per step for `steps` steps; the job took the slowest rank's
+    time.  times_ms: this rank's timings (ms) -> (max over ranks of each,
+    world * work * steps / max time for each)."""
+    import torch
+    t = list(times_ms)
+    if dist is not None:
+        buf = torch.tensor(t, dtype=torch.float64, device=device)
+        dist.all_reduce(buf, op=dist.ReduceOp.MAX)
+        t = [float(v) for v in buf]
+    return t, [world * work * steps / (v / 1e3) for v in t]
+
+
 # ----------------------------------------------------------------- oracle --
 
 def oracle_sample(seed=0):
@@ -368,14 +382,7 @@ def run_ours(args):
     d2h = h_grad.numel() * 4 + 8 * pm.n_batch * 4        # dnoise + loss, dOm (dyn, IC), dsigma8
 
     work = pm.n_batch * w.n_p ** 3 * n_steps            # particle-steps per rank per bench step
-    t_max = total_ms
-    e2e_max = e2e_ms
-    if dist is not None:
-        t = torch.tensor([total_ms, e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max, e2e_max = float(t[0]), float(t[1])
-    value = world * work * args.steps / (t_max / 1e3)
-    e2e_value = world * work * args.steps / (e2e_max / 1e3)
+    (t_max, e2e_max), (value, e2e_value) = replica_throughput(dist, world, work, args.steps, (total_ms, e2e_ms), dev)
 
     if rank == 0:
         hbm, peak_src = _peaks()
@@ -511,12 +518,7 @@ def run_learned(args):
     e2e_ms = e0.elapsed_time(e1)
 
     work = pm.n_batch * w.n_p ** 3 * w.n_steps
-    t_max, e2e_max = total_ms, e2e_ms
-    if dist is not None:
-        t = torch.tensor([total_ms, e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max, e2e_max = float(t[0]), float(t[1])
-    value = world * work * args.steps / (t_max / 1e3)
+    (t_max, e2e_max), (value, _) = replica_throughput(dist, world, work, args.steps, (total_ms, e2e_ms), dev)
     if rank == 0:
         d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
