@@ -155,3 +155,106 @@ def init_params(seed):
         else:
             theta.append(rng.standard_normal(shape) * np.sqrt(2.0 / shape[0]))
     return np.concatenate([t.ravel() for t in theta])
+
+
+# ------------------------------------------- through the trajectory -------
+#
+# Training the correction on the trajectory (rather than on forces) needs
+# its vector-Jacobian products inside the reverse-time adjoint.  With
+# dF(c) = s_out y(x(c)), x(c)_q = asinh(rho(c + o_q) - 1), rho = alpha sum W
+# and the corrected particle force F_i = sum_c W(x_i - c) dF(c), the
+# cotangent v of F gives
+#   u(c)        = sum_i W(x_i - c) v_i                     (paint of v)
+#   g_s (read)  = sum_c dW(x_i - c)/dx_i (v_i . dF(c))
+#   g_y(c)      = s_out u(c);  g_x = MLP backward of g_y;  g_theta likewise
+#   g_rho(c')   = sum_q g_x(c' - o_q, q) / sqrt(1 + (rho(c') - 1)^2)
+#   g_s (paint) = alpha sum_c dW(x_i - c)/dx_i g_rho(c)
+# The bf16 rounding points are those of loss_and_grad (activation and output
+# cotangents rounded before the products), with the feature cotangent g_x
+# taken from the rounded g1 and W1.
+
+
+def _mlp_backward(x, h1, h2, gy, theta, r):
+    """MLP backward from the output cotangent gy (cells, 3): returns the
+    feature cotangent (cells, 32) and the flat parameter gradient."""
+    p = unflatten(theta)
+    g = {}
+    gy = r(gy)
+    g["W3"] = h2.T @ gy
+    g["b3"] = gy.sum(0)
+    g2 = (gy @ r(p["W3"]).T) * (h2 > 0)
+    g["b2"] = g2.sum(0)
+    g2 = r(g2)
+    g["W2"] = h1.T @ g2
+    g1 = (g2 @ r(p["W2"]).T) * (h1 > 0)
+    g["b1"] = g1.sum(0)
+    g1 = r(g1)
+    g["W1"] = x.T @ g1
+    gx = g1 @ r(p["W1"]).T
+    return gx, np.concatenate([g[name].ravel() for name, _ in param_shapes()])
+
+
+def correction_vjp(s, v, a, theta, setup, rounding=True):
+    """(g_s, g_theta): cotangents of the particles' displacements and of the
+    network parameters for the cotangent v (N, 3) of predict(s, a, ...)."""
+    r = bf16 if rounding else (lambda t: np.asarray(t, dtype=np.float64))
+    n, h, order = setup.n_m, setup.cell, setup.order
+    xpos = pm.positions(s, setup)
+    rho = setup.alpha * pm.cic_paint(xpos, n, h, order=order)
+    y, (x, h1, h2) = forward(features(rho, a), theta, rounding)
+    so = output_scale(setup)
+    dfm = [(so * y[:, j]).reshape(n, n, n) for j in range(3)]
+    g_read = np.zeros((len(s), 3))
+    for j in range(3):
+        g_read += pm.cic_read_grad(xpos, dfm[j], h, order) * v[:, j:j + 1]
+    u = np.stack([pm.cic_paint(xpos, n, h, v[:, j], order).ravel() for j in range(3)], axis=1)
+    gx, g_theta = _mlp_backward(x, h1, h2, so * u, theta, r)
+    g_d = np.zeros((n, n, n))
+    for q, (ox, oy, oz) in enumerate(OFFSETS):
+        # x(c)_q reads d(c + o_q): its cotangent lands on cell c + o_q
+        g_d += np.roll(gx[:, q].reshape(n, n, n), shift=(ox, oy, oz), axis=(0, 1, 2))
+    g_rho = g_d / np.sqrt(1.0 + (rho - 1.0) ** 2)
+    g_paint = setup.alpha * pm.cic_read_grad(xpos, g_rho, h, order)
+    return g_read + g_paint, g_theta
+
+
+def integrate_corrected(s, p, theta, setup, rounding=True):
+    """Forward KDK with the force PM + correction, the correction at each
+    evaluation's scale factor (step boundaries a_n)."""
+    c = pm.coefficients(setup)
+    a = c["a"]
+    s, p = s.copy(), p.copy()
+    f = pm.force(s, setup) + predict(s, a[0], theta, setup, rounding)
+    for n in range(setup.n_steps):
+        p = p + c["K_a"][n] * f
+        s = s + c["Dr"][n] * p
+        f = pm.force(s, setup) + predict(s, a[n + 1], theta, setup, rounding)
+        p = p + c["K_b"][n] * f
+    return s, p, f
+
+
+def adjoint_corrected(s, p, f, lam, mu, theta, setup, rounding=True):
+    """Discrete adjoint of integrate_corrected, backward in time along the
+    reconstructed trajectory: returns the initial (s, p), the cotangents of
+    the initial s and p, and the gradient with respect to the network
+    parameters (Om is held fixed here)."""
+    c = pm.coefficients(setup)
+    a = c["a"]
+    g_theta = np.zeros(n_params())
+    s, p, lam, mu = s.copy(), p.copy(), lam.copy(), mu.copy()
+
+    def vjp(y, v, ak, coef):
+        gs_nn, gt = correction_vjp(y, v, ak, theta, setup, rounding)
+        return coef * (pm.force_vjp(y, v, setup) + gs_nn), coef * gt
+
+    for n in reversed(range(setup.n_steps)):
+        gl, gt = vjp(s, mu, a[n + 1], c["K_b"][n])
+        lam, g_theta = lam + gl, g_theta + gt
+        p_half = p - c["K_b"][n] * f
+        mu = mu + c["Dr"][n] * lam
+        s = s - c["Dr"][n] * p_half
+        f = pm.force(s, setup) + predict(s, a[n], theta, setup, rounding)
+        gl, gt = vjp(s, mu, a[n], c["K_a"][n])
+        lam, g_theta = lam + gl, g_theta + gt
+        p = p_half - c["K_a"][n] * f
+    return s, p, lam, mu, g_theta
