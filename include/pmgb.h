@@ -257,9 +257,17 @@ int pm_host_coefficients(const pm_config *cfg, double *kdk, double *dkdk, double
  * pm_nn_get_params   download theta and/or the last gradient (host; NULL skips)
  * pm_nn_enable       apply the correction in pm_integrate and pm_kdk_step at
  *                    each evaluation's scale factor (pm_force stays the plain
- *                    PM force; pm_adjoint_integrate refuses with PM_ESTATE);
- *                    synchronises the stream and returns PM_ECUDA if a
+ *                    PM force); pm_adjoint_integrate then differentiates the
+ *                    corrected dynamics (the correction's VJPs at every
+ *                    reconstructed state) and leaves the gradient of its
+ *                    objective with respect to the network parameters in the
+ *                    context (pm_nn_get_params); its dOm output ignores the
+ *                    Om dependence of the correction's output scale.
+ *                    Synchronises the stream and returns PM_ECUDA if a
  *                    tensor-core wait of an earlier correction timed out
+ * pm_nn_adam_step    one Adam step (lr, beta 0.9 / 0.999, eps 1e-8, bias
+ *                    correction for step >= 1) with the gradient in the
+ *                    context (from pm_adjoint_integrate or pm_nn_train_step)
  * pm_nn_predict      dF device [n_batch][n_p^3][3]: the correction read at
  *                    the particles s for scale factor a
  * pm_nn_train_step   force matching at particles s: loss = mean over
@@ -273,6 +281,7 @@ int pm_nn_param_count(void);
 int pm_nn_set_params(pm_ctx *ctx, const float *theta);
 int pm_nn_get_params(pm_ctx *ctx, float *theta, float *grad);
 int pm_nn_enable(pm_ctx *ctx, int enable);
+int pm_nn_adam_step(pm_ctx *ctx, double lr, int64_t step);
 int pm_nn_predict(pm_ctx *ctx, const float *s, double a, float *dF);
 int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a, double weight, double lr,
                      int64_t step, int apply, double *loss);

@@ -73,6 +73,7 @@ _SIGNATURES = {
     "pm_nn_set_params": (ctypes.c_int, [_P, _P]),
     "pm_nn_get_params": (ctypes.c_int, [_P, _P, _P]),
     "pm_nn_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pm_nn_adam_step": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int64]),
     "pm_nn_predict": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
     "pm_nn_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                         ctypes.c_int,

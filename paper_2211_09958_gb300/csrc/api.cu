@@ -88,6 +88,8 @@ struct pm_ctx {
     double *nn_loss = nullptr;
     int *nn_err = nullptr;  // tensor-core kernel time-out flag
     __nv_bfloat16 *nn_feat = nullptr;  // feature mesh [run][n^3]
+    float *nn_mesh4 = nullptr;         // [run][n^3][4]: correction (0..2) and density cotangent (3) of an adjoint step
+    float *nn_gx = nullptr;            // [cells][32] feature cotangents
 };
 
 namespace {
@@ -384,8 +386,10 @@ int own_inverse(pm_ctx *ctx, float *real, int g) {
 // adjoint) in the scratch fields.  mu != NULL selects the 4-field adjoint
 // paint.
 int apply_correction(pm_ctx *ctx, double a);
+int correction_adjoint(pm_ctx *ctx, double a, int kick_step, int kick_sel);
+int64_t nn_cells(pm_ctx *ctx);
 
-int force_meshes(pm_ctx *ctx, const float *s, const float *mu, double a = -1.0) {
+int force_meshes(pm_ctx *ctx, const float *s, const float *mu, double a = -1.0, int kick_step = -1, int kick_sel = 0) {
     const bool adj = mu != nullptr;
     const int nf = adj ? 4 : 1;
     const int mode = adj ? PAINT_ADJ : PAINT_DENSITY;
@@ -399,8 +403,15 @@ int force_meshes(pm_ctx *ctx, const float *s, const float *mu, double a = -1.0) 
         PM_TRY(own_forward(ctx, real, nf));
         PM_LAUNCH(ctx, (adj ? "spectral_adj" : "spectral_force"),
                   launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream));
+        // the correction's adjoint reads the painted (rho, mu) still in r4
+        if (adj && ctx->nn_on && a > 0.0) PM_TRY(correction_adjoint(ctx, a, kick_step, kick_sel));
         PM_TRY(own_inverse(ctx, ctx->r4, adj ? 4 : 3));
         if (!adj && ctx->nn_on && a > 0.0) PM_TRY(apply_correction(ctx, a));
+        if (adj && ctx->nn_on && a > 0.0) {
+            const int64_t n4 = nn_cells(ctx);
+            PM_LAUNCH(ctx, "nn_add4", launch_add4(reinterpret_cast<float4 *>(ctx->r4),
+                                                  reinterpret_cast<const float4 *>(ctx->nn_mesh4), n4, ctx->stream));
+        }
         return PM_OK;
     }
     PM_MEMSET(ctx, cudaMemsetAsync(ctx->mesh, 0, sizeof(float) * ctx->mesh_pad * ctx->P.n_batch * nf, ctx->stream));
@@ -532,7 +543,9 @@ int ensure_nn(pm_ctx *ctx) {
         cudaMalloc(&ctx->nn_part, sizeof(float) * 3 * parts) != cudaSuccess ||
         cudaMalloc(&ctx->nn_loss, sizeof(double)) != cudaSuccess ||
         cudaMalloc(&ctx->nn_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->nn_err, 0, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&ctx->nn_feat, sizeof(__nv_bfloat16) * cells) != cudaSuccess) {
+        cudaMalloc(&ctx->nn_feat, sizeof(__nv_bfloat16) * cells) != cudaSuccess ||
+        cudaMalloc(&ctx->nn_mesh4, sizeof(float) * 4 * cells) != cudaSuccess ||
+        cudaMalloc(&ctx->nn_gx, sizeof(float) * NN_IN * cells) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, PM_ENOMEM, "cannot allocate the learned-correction buffers");
     }
@@ -544,8 +557,8 @@ int ensure_nn(pm_ctx *ctx) {
 
 NNArgs nn_args(pm_ctx *ctx, double a) {
     NNArgs na{};
-    na.w = NNWeights{ctx->nnw.w1t, ctx->nnw.w2t, ctx->nnw.w2n, ctx->nnw.w3t, ctx->nnw.w3n,
-                     ctx->nnw.b1, ctx->nnw.b2, ctx->nnw.b3, ctx->nnw.w1c, ctx->nnw.w2c, ctx->nnw.w3c};
+    na.w = NNWeights{ctx->nnw.w1t, ctx->nnw.w2t, ctx->nnw.w2n, ctx->nnw.w3t, ctx->nnw.w3n, ctx->nnw.b1,
+                     ctx->nnw.b2,  ctx->nnw.b3,  ctx->nnw.w1c, ctx->nnw.w2c, ctx->nnw.w3c, ctx->nnw.w1n};
     na.err = ctx->nn_err;
     na.feat = ctx->nn_feat;
     na.n = ctx->P.n_m;
@@ -587,6 +600,35 @@ int apply_correction(pm_ctx *ctx, double a) {
     na.accumulate = 1;
     PM_LAUNCH(ctx, "nn_feat", launch_nn_feat(ctx->r1, ctx->nn_feat, nn_cells(ctx), ctx->stream));
     PM_LAUNCH(ctx, "nn_fwd_tc", launch_nn_fwd_tc(na, nn_cells(ctx), ctx->stream));
+    return PM_OK;
+}
+
+// The correction inside an adjoint step, between the forward transforms of
+// the 4-field paint (r4 = alpha sum W, sum W mu) and the inverse ones:
+// network forward at a (activations kept, dF -> nn_mesh4 slots 0..2),
+// backward with the output cotangent s_out c u (c the step's kick factor):
+// parameter gradient accumulated, feature cotangents -> density cotangent
+// g_rho / c -> nn_mesh4 slot 3; after the inverse transforms nn_mesh4 is
+// added to (F, psi), so that the fused read applies the corrected force and
+// the full VJP.
+int correction_adjoint(pm_ctx *ctx, double a, int kick_step, int kick_sel) {
+    const int64_t cells = nn_cells(ctx);
+    NNArgs na = nn_args(ctx, a);
+    if (!na.w.w1n || !ctx->nn_mesh4 || !ctx->nn_gx || kick_step < 0 || kick_step >= ctx->P.n_steps)
+        return fail(ctx, PM_ESTATE, "learned-correction adjoint buffers are not set up");
+    na.rho = ctx->r4;
+    na.rho_stride = 4;
+    na.out = ctx->nn_mesh4;
+    na.accumulate = 0;
+    PM_LAUNCH(ctx, "nn_fwd_train", launch_nn_fwd(na, cells, true, ctx->stream));
+    na.gmesh = ctx->r4;
+    na.table = ctx->d_table;
+    na.kick_step = kick_step;
+    na.kick_sel = kick_sel;
+    na.nb = ctx->P.n_batch;
+    na.gx = ctx->nn_gx;
+    PM_LAUNCH(ctx, "nn_bwd", launch_nn_bwd(na, cells, ctx->stream));
+    PM_LAUNCH(ctx, "nn_grad_rho", launch_nn_grad_rho(na, ctx->r4, ctx->nn_mesh4, cells, ctx->stream));
     return PM_OK;
 }
 
@@ -940,7 +982,7 @@ int pm_destroy(pm_ctx *ctx) {
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     for (void *p : {(void *)ctx->nn_packed, (void *)ctx->nn_theta, (void *)ctx->nn_grad, (void *)ctx->nn_m,
                     (void *)ctx->nn_v, (void *)ctx->nn_part, (void *)ctx->nn_act, (void *)ctx->nn_loss,
-                    (void *)ctx->nn_err, (void *)ctx->nn_feat})
+                    (void *)ctx->nn_err, (void *)ctx->nn_feat, (void *)ctx->nn_mesh4, (void *)ctx->nn_gx})
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->spec, (void *)ctx->tw, (void *)ctx->d_err}) 
@@ -1101,12 +1143,13 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
     PM_TRY(check_ptr(ctx, mu, "mu"));
     if (step_begin < 0 || step_end > ctx->P.n_steps || step_begin >= step_end)
         return fail(ctx, PM_EINVAL, "need 0 <= step_begin < step_end <= n_steps");
-    if (ctx->nn_on) return fail(ctx, PM_ESTATE, "the learned correction has no reverse-time adjoint; disable it first");
     DeviceGuard guard(ctx->device);
     const int N = ctx->P.n_steps, B = ctx->P.n_batch;
     const int last = step_end - 1;
     PM_TRY(run_graphed(ctx, 2, step_begin, step_end, s, p, f, lam, mu, flags, [&]() -> int {
         PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * B * 2 * (N + 1), ctx->stream));
+        if (ctx->nn_on)  // parameter gradient of this adjoint run
+            PM_MEMSET(ctx, cudaMemsetAsync(ctx->nn_grad, 0, sizeof(float) * nn_param_count(), ctx->stream));
         if (flags & PM_ADJ_MU_ZERO) {
             // undo the last half kick with the stored F(s_N) (mu = 0: no VJP)
             PM_LAUNCH(ctx, "kick", launch_kick(ctx->g, p, f, ctx->d_table, last, KICK_B, -1.f, ctx->stream));
@@ -1118,7 +1161,7 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
             PM_LAUNCH(ctx, "pre_rev_drift", launch_pre(PRE_REV_DRIFT, pr, ctx->stream));
         } else {
             // VJP of the last half kick at s_N, fused with the reverse drift of step `last`
-            PM_TRY(force_meshes(ctx, s, mu));
+            PM_TRY(force_meshes(ctx, s, mu, a_of(ctx, last + 1), last, KICK_B));
             ReadArgs ra = read_args(ctx, s);
             ra.p = p;
             ra.lam = lam;
@@ -1131,7 +1174,7 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
             PM_TRY(read_forces(ctx, READ_ADJ, ra));
         }
         for (int n = last; n >= step_begin; --n) {
-            PM_TRY(force_meshes(ctx, s, mu));
+            PM_TRY(force_meshes(ctx, s, mu, a_of(ctx, n), n, n == step_begin ? KICK_A : KICK_MERGED));
             ReadArgs ra = read_args(ctx, s);
             ra.p = p;
             ra.lam = lam;
@@ -1381,6 +1424,20 @@ int pm_nn_get_params(pm_ctx *ctx, float *theta, float *grad) {
     PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (theta) PM_CUDA(ctx, cudaMemcpy(theta, ctx->nn_theta, sizeof(float) * np, cudaMemcpyDeviceToHost));
     if (grad) PM_CUDA(ctx, cudaMemcpy(grad, ctx->nn_grad, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    return PM_OK;
+}
+
+int pm_nn_adam_step(pm_ctx *ctx, double lr, int64_t step) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    if (!ctx->nn_theta) return fail(ctx, PM_ESTATE, "no network parameters set");
+    if (step < 1) return fail(ctx, PM_EINVAL, "Adam step count starts at 1");
+    DeviceGuard guard(ctx->device);
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 / (1.0 - std::pow(b1, (double)step)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow(b2, (double)step)));
+    PM_LAUNCH(ctx, "adam", launch_adam(ctx->nn_theta, ctx->nn_grad, ctx->nn_m, ctx->nn_v, nn_param_count(), (float)lr,
+                                       (float)b1, (float)b2, 1e-8f, c1, c2, ctx->stream));
+    PM_LAUNCH(ctx, "nn_pack", launch_nn_pack(ctx->nn_theta, ctx->nnw, ctx->stream));
     return PM_OK;
 }
 

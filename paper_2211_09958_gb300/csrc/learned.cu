@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd(NNArgs a, int64_t tiles)
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t cell0 = tile * TILE;  // global cell index (run-major)
     const int64_t run = cell0 / n3;
-    const float *rho = a.rho + run * n3;
+    const int rs = a.rho_stride == 4 ? 4 : 1;
+    const float *rho = a.rho + run * n3 * rs;
     const float s_out = a.pref[run] * a.s_scale;
     __syncthreads();  // previous tile's feature rows are consumed
     {
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd(NNArgs a, int64_t tiles)
         for (int q = half ? 14 : 0; q < (half ? 27 : 14); ++q) {
             const int ox = q / 9 - 1, oy = (q / 3) % 3 - 1, oz = q % 3 - 1;
             const int xx = (x + ox + n) % n, yy = (y + oy + n) % n, zz = (z + oz + n) % n;
-            const float v = __ldg(rho + ((int64_t)xx * n + yy) * n + zz);
+            const float v = __ldg(rho + (((int64_t)xx * n + yy) * n + zz) * rs);
             row[q] = __float2bfloat16_rn(asinhf(v - 1.f));
         }
         if (half) {
@@ -205,26 +206,33 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd(NNArgs a, int64_t tiles)
 }
 
 struct SmemBwd {
-    static constexpr int W2 = NH * KP2, W3 = NH * KP3;
-    static constexpr size_t BYTES = sizeof(bf16) * (W2 + W3) + sizeof(float) * (2 * NH + 8);
+    static constexpr int W2 = NH * KP2, W3 = NH * KP3, W1 = NI * KP2;
+    static constexpr size_t BYTES = sizeof(bf16) * (W2 + W3 + W1) + sizeof(float) * (2 * NH + 8);
 };
+
+__device__ __forceinline__ float kick_coef(const NNArgs &a, int64_t run) {
+    if (!a.table) return 1.f;
+    const float4 t = a.table[(int64_t)a.kick_step * a.nb + run];
+    return a.kick_sel == KICK_A ? t.x : (a.kick_sel == KICK_B ? t.z : t.w);
+}
 
 // Backward through the network for 128 cells per block: from the output
 // cotangent (slots 1..3 of the interleaved gradient mesh, times s_out) to the
 // activation cotangents g2, g1 (stored as bf16), with the bias gradients.
 __global__ void __launch_bounds__(THREADS, 2) k_mlp_bwd(NNArgs a, int64_t tiles) {
     extern __shared__ int4 smraw[];
-    bf16 *W2n = reinterpret_cast<bf16 *>(smraw), *W3n = W2n + SmemBwd::W2;
-    float *gbs = reinterpret_cast<float *>(W3n + SmemBwd::W3);  // block sums of gb2 [128], gb1 [128], gb3 [8]
+    bf16 *W2n = reinterpret_cast<bf16 *>(smraw), *W3n = W2n + SmemBwd::W2, *W1n = W3n + SmemBwd::W3;
+    float *gbs = reinterpret_cast<float *>(W1n + SmemBwd::W1);  // block sums of gb2 [128], gb1 [128], gb3 [8]
     copy16(W2n, a.w.w2n, SmemBwd::W2 * 2 / 16);
     copy16(W3n, a.w.w3n, SmemBwd::W3 * 2 / 16);
+    if (a.gx) copy16(W1n, a.w.w1n, SmemBwd::W1 * 2 / 16);
     for (int k = threadIdx.x; k < 2 * NH + 8; k += THREADS) gbs[k] = 0.f;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int64_t n3 = (int64_t)a.n * a.n * a.n;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t r0 = tile * TILE + 16 * warp;
-    const float s_out = a.pref[tile * TILE / n3] * a.s_scale;
+    const float s_out = a.pref[tile * TILE / n3] * a.s_scale * kick_coef(a, tile * TILE / n3);
     // output cotangent, C layout [16 x 8]; columns >= 3 are zero
     float gy[4];
 #pragma unroll
@@ -284,6 +292,19 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_bwd(NNArgs a, int64_t tiles)
             gf[j >> 1][(j & 1) * 2 + 1] = pack2(v2, v3);
         }
         store_frags(dst, r0, gf, g, t);
+    }
+    if (a.gx) {
+        // feature cotangent g_x = g1 W1^T (rows r0 .. r0 + 15, 32 features)
+        float ax[NI / 8][4];
+#pragma unroll
+        for (int j = 0; j < NI / 8; ++j) ax[j][0] = ax[j][1] = ax[j][2] = ax[j][3] = 0.f;
+        layer<NH / 16, NI / 8>(ax, gf, W1n, KP2, g, t);
+#pragma unroll
+        for (int j = 0; j < NI / 8; ++j) {
+            const int c = 8 * j + 2 * t;
+            *reinterpret_cast<float2 *>(a.gx + (r0 + g) * NI + c) = make_float2(ax[j][0], ax[j][1]);
+            *reinterpret_cast<float2 *>(a.gx + (r0 + g + 8) * NI + c) = make_float2(ax[j][2], ax[j][3]);
+        }
     }
     }
     __syncthreads();
@@ -373,6 +394,10 @@ __global__ void k_nn_pack(const float *theta, NNWeightsMut w) {
             const int r3 = k / KP3, c3 = k % KP3;
             w.w3n[k] = __float2bfloat16_rn(c3 < NO ? W3[r3 * NO + c3] : 0.f);
         }
+        if (k < NI * KP2) {
+            const int rn = k / KP2, cn = k % KP2;  // [feature][hidden]
+            w.w1n[k] = __float2bfloat16_rn(cn < NH ? W1[rn * NH + cn] : 0.f);
+        }
         if (k < NH) {
             w.b1[k] = b1[k];
             w.b2[k] = b2[k];
@@ -420,13 +445,57 @@ __global__ void k_nn_residual(float *pred, const float *target, int64_t n, float
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
 }
 
+// g_rho(c) = sum_q g_x(c - o_q, q) / sqrt(1 + (rho(c) - 1)^2), divided by the
+// run's kick factor (the read applies it to the whole VJP), into slot 3.
+__global__ void k_nn_grad_rho(NNArgs a, const float *rho4, float *out4, int64_t cells) {
+    const int n = a.n;
+    const int64_t n3 = (int64_t)n * n * n;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t run = c / n3, loc = c - run * n3;
+        const int x = (int)(loc / ((int64_t)n * n)), y = (int)((loc / n) % n), z = (int)(loc % n);
+        float acc = 0.f;
+#pragma unroll 1
+        for (int q = 0; q < 27; ++q) {
+            const int ox = q / 9 - 1, oy = (q / 3) % 3 - 1, oz = q % 3 - 1;
+            const int xx = (x - ox + n) % n, yy = (y - oy + n) % n, zz = (z - oz + n) % n;
+            acc += a.gx[(run * n3 + ((int64_t)xx * n + yy) * n + zz) * NI + q];
+        }
+        const float r = rho4[c * 4] - 1.f;
+        out4[c * 4 + 3] = acc * rsqrtf(1.f + r * r) / kick_coef(a, run);
+    }
+}
+
+__global__ void k_add4(float4 *dst, const float4 *src, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 s = src[i];
+        float4 d = dst[i];
+        d.x += s.x;
+        d.y += s.y;
+        d.z += s.z;
+        d.w += s.w;
+        dst[i] = d;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_nn_grad_rho(const NNArgs &a, const float *rho4, float *out4, int64_t cells, cudaStream_t st) {
+    const int64_t blocks = (cells + 255) / 256;
+    k_nn_grad_rho<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(a, rho4, out4, cells);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add4(float4 *dst, const float4 *src, int64_t n, cudaStream_t st) {
+    const int64_t blocks = (n + 255) / 256;
+    k_add4<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(dst, src, n);
+    return cudaGetLastError();
+}
 
 int nn_param_count() { return NI * NH + NH + NH * NH + NH + NH * NO + NO; }
 
 size_t nn_packed_bytes() {
     return sizeof(bf16) * (NH * KP1 + 2 * NH * KP2 + 8 * KP2 + NH * KP3) + sizeof(float) * (NH + NH + 8) +
-           sizeof(bf16) * (NH * NI + NH * NH + 16 * NH) + 512;
+           sizeof(bf16) * (NH * NI + NH * NH + 16 * NH + NI * KP2) + 640;
 }
 
 NNWeightsMut nn_carve(void *base) {
@@ -448,6 +517,7 @@ NNWeightsMut nn_carve(void *base) {
     w.w1c = reinterpret_cast<bf16 *>(take(sizeof(bf16) * NH * NI));
     w.w2c = reinterpret_cast<bf16 *>(take(sizeof(bf16) * NH * NH));
     w.w3c = reinterpret_cast<bf16 *>(take(sizeof(bf16) * 16 * NH));
+    w.w1n = reinterpret_cast<bf16 *>(take(sizeof(bf16) * NI * KP2));
     return w;
 }
 

@@ -210,11 +210,13 @@ struct NNWeights {  // packed bf16 operands and FP32 biases (learned.cu)
     const __nv_bfloat16 *w1t, *w2t, *w2n, *w3t, *w3n;
     const float *b1, *b2, *b3;
     const __nv_bfloat16 *w1c, *w2c, *w3c;  // tensor-core (tcgen05) operand layouts
+    const __nv_bfloat16 *w1n;              // [32][136] W1 as [feature][hidden] (input gradient)
 };
 struct NNWeightsMut {
     __nv_bfloat16 *w1t, *w2t, *w2n, *w3t, *w3n;
     float *b1, *b2, *b3;
     __nv_bfloat16 *w1c, *w2c, *w3c;
+    __nv_bfloat16 *w1n;
 };
 
 // Element index of (row r, column k) of an R x K bf16 operand stored as
@@ -228,7 +230,8 @@ __host__ __device__ constexpr int nn_cm_index(int r, int k, int R) {
 struct NNArgs {
     NNWeights w;
     int n;               // mesh cells per side
-    const float *rho;    // painted density [run][n^3] (alpha sum W)
+    const float *rho;    // painted density [run][n^3] (alpha sum W), rho_stride floats per cell
+    int rho_stride;      // 1 (plain mesh; also for 0) or 4 (slot 0 of the interleaved adjoint paint)
     float afeat;         // scale-factor feature
     const float *pref;   // per run 3/2 Om / n^3; output scale = pref * s_scale
     float s_scale;       // n^3 h, so that the output scale is 3/2 Om h
@@ -239,6 +242,13 @@ struct NNArgs {
     float *grad, *gb1, *gb2, *gb3;
     int *err;            // set by the tensor-core kernel when a wait times out
     const __nv_bfloat16 *feat;  // [run][n^3] bf16(asinh(rho - 1)) (tensor-core path)
+    // adjoint through the trajectory: the output cotangent is scaled per run
+    // by the kick factor of table[kick_step * nb + run] (x: K_a, z: K_b, w:
+    // merged; table NULL: 1), the feature cotangent g_x [cells][32] (FP32)
+    // is written when gx != NULL
+    const float4 *table;
+    int kick_step, kick_sel, nb;
+    float *gx;
 };
 
 int nn_param_count();
@@ -255,5 +265,11 @@ cudaError_t launch_nn_residual(float *pred, const float *target, int64_t n, floa
                                cudaStream_t st);
 cudaError_t launch_adam(float *theta, float *grad, float *m, float *v, int np, float lr, float b1, float b2, float eps,
                         float c1, float c2, cudaStream_t st);
+// g_rho(c) = sum_q g_x(c - o_q, q) / sqrt(1 + (rho(c) - 1)^2) / coef(run), written
+// to slot 3 of the interleaved mesh out4; rho from slot 0 of rho4.
+cudaError_t launch_nn_grad_rho(const NNArgs &a, const float *rho4, float *out4, int64_t cells, cudaStream_t st);
+// dst[i] += src[i] over n float4 (the correction and density cotangent into
+// the force / psi meshes).
+cudaError_t launch_add4(float4 *dst, const float4 *src, int64_t n, cudaStream_t st);
 
 }  // namespace pmgb

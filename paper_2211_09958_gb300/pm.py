@@ -198,6 +198,11 @@ class ParticleMesh:
         """Add the network's correction to every force of pm_integrate / pm_kdk_step."""
         self._call("pm_nn_enable", int(bool(enable)))
 
+    def nn_adam_step(self, lr, step):
+        """One Adam step with the parameter gradient in the context (left by
+        adjoint_integrate with the correction on, or by nn_train_step)."""
+        self._call("pm_nn_adam_step", ctypes.c_double(lr), ctypes.c_int64(step))
+
     def nn_predict(self, s, a):
         self._particles(s, "s")
         df = self.new_particles()
