@@ -197,3 +197,44 @@ def evaluate(setup, theta, seeds):
                      "particle_steps_per_s": r["particle_steps_per_s"]}
     fine.close()
     return out
+
+
+def reference_densities(setup, seeds, measure):
+    """Final CIC density contrasts of the reference runs for ``seeds`` (one
+    group), painted on the mesh of the context ``measure``."""
+    fine = setup.fine()
+    s, p = fine.init_lpt(seed=seeds[0])
+    fine.integrate(s, p)
+    d = measure.density(s + lattice_shift(fine, measure))
+    fine.close()
+    return d
+
+
+def train_trajectory(setup, seeds, theta, steps=100, lr=3e-4, lr_final=3e-5, log=None):
+    """Fine-tune the correction through the trajectory: each Adam step runs
+    the corrected coarse simulations of one group of seeds (cycling through
+    ``seeds``), takes the mean squared difference between their final density
+    contrast and the reference's (painted on the coarse mesh), and
+    differentiates it with the reverse-time adjoint of the corrected
+    dynamics.  Returns (theta, losses)."""
+    import numpy as np
+    groups = [seeds[i:i + setup.group] for i in range(0, len(seeds), setup.group)]
+    pm = setup.coarse()
+    pm.nn_set_params(theta)
+    pm.nn_enable(True)
+    targets = [reference_densities(setup, g, pm) for g in groups]
+    losses = []
+    for step in range(1, steps + 1):
+        k = (step - 1) % len(groups)
+        s, p = pm.init_lpt(seed=groups[k][0])
+        f = pm.integrate(s, p)
+        loss, lam = pm.mse_loss(s, targets[k])
+        losses.append(float(np.mean(loss)))
+        pm.adjoint_integrate(s, p, f, lam, torch.zeros_like(p), mu_zero=True)
+        rate = lr * (lr_final / lr) ** ((step - 1) / max(steps - 1, 1))
+        pm.nn_adam_step(rate, step)
+    theta, _ = pm.nn_get_params()
+    pm.close()
+    if log is not None:
+        log.losses += losses
+    return theta, losses

@@ -30,3 +30,15 @@ def test_trained_correction_beats_plain_pm():
     assert corr < 0.5 * plain, (corr, plain)
     sel = ev["k"] <= ev["k_cut"]
     assert np.all(np.abs(ev["corrected"]["rel_err"][sel]) <= np.abs(ev["plain"]["rel_err"][sel]) + 5e-3)
+
+
+def test_trajectory_training_lowers_the_density_loss():
+    """Fine-tuning through the trajectory (final-density MSE against the
+    reference, gradient by the corrected reverse-time adjoint) lowers its
+    loss on the training runs."""
+    from paper_2211_09958_gb300 import learn
+    st = learn.LearnedSetup(n_p=64, n_m=64, box=128.0, n_steps=10, group=4)
+    theta, _ = learn.train(st, list(range(100, 108)), epochs=2, lr=1e-3, lr_final=1e-4)
+    _, losses = learn.train_trajectory(st, list(range(100, 108)), theta, steps=40, lr=6e-4, lr_final=6e-5)
+    assert np.all(np.isfinite(losses))
+    assert np.mean(losses[-6:]) < 0.9 * np.mean(losses[:6]), (losses[:6], losses[-6:])
