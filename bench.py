@@ -185,6 +185,46 @@ def replica_throughput(dist, world, work, steps, times_ms, device="cpu"):
     return t, [world * work * steps / (v / 1e3) for v in t]
 
 
+def timed_steps(pm, stream, steps, step, barrier, profile=False, split=False):
+    """Run `steps` bench steps between barriers, each bracketed by CUDA events
+    on `stream`.  Without `profile` the library runs as a user calls it
+    (integration loops replayed from its CUDA graphs); with `profile` it
+    brackets every launch with its own event pair, which needs eager
+    launches, and the per-kind table {kind: (launches, ms)} is returned.
+    step(ev) runs one step; with `split` it records `ev` between the forward
+    and the adjoint part.  -> (step_ms, forward_ms or None, launches, table)"""
+    import ctypes
+    import torch
+    lib = pm._lib
+    if profile:
+        lib.pm_profile(pm._ctx, 1)
+        lib.pm_profile_read(pm._ctx, None, None, 0)       # drop older records
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    barrier()
+    launches0 = pm.launch_count()
+    for k in range(steps):
+        ev[k][0].record(stream)
+        step(ev[k][1] if split else None)
+        ev[k][2].record(stream)
+    barrier()
+    launches = pm.launch_count() - launches0
+    table = None
+    if profile:
+        nk = lib.pm_profile_kinds(pm._ctx)
+        counts = (ctypes.c_int64 * nk)()
+        kms = (ctypes.c_double * nk)()
+        lib.pm_profile_read(pm._ctx, counts, kms, nk)
+        lib.pm_profile(pm._ctx, 0)
+        table = {lib.pm_profile_name(pm._ctx, i).decode(): (int(counts[i]), float(kms[i])) for i in range(nk)}
+    step_ms = [a.elapsed_time(c) for a, _, c in ev]
+    fwd_ms = [a.elapsed_time(b) for a, b, _ in ev] if split else None
+    return step_ms, fwd_ms, launches, table
+
+
+PROFILED_NOTE = ("a second pass of the same steps with an event pair around every launch (eager launches, "
+                 "no CUDA graphs); source of `kernels` and of the roofline's per-launch time")
+
+
 # ----------------------------------------------------------------- oracle --
 
 def oracle_sample(seed=0):
@@ -336,32 +376,16 @@ def run_ours(args):
         hot_path(noise, target)
     barrier()
 
-    # device-resident timing, with the library's per-kernel event timing on
-    lib = pm._lib
-    lib.pm_profile(pm._ctx, 1)
-    lib.pm_profile_read(pm._ctx, None, None, 0)           # clear warm-up records
-    launches0 = pm.launch_count()
-    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev_m = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # device-resident timing: the production pass gives the value, a second
+    # pass with per-launch events gives the kernel table and the roofline
+    def step(ev):
+        hot_path(noise, target, ev)
+
     with ClockSampler(torch.cuda.current_device()) as clocks:
-        barrier()
-        for k in range(args.steps):
-            ev_a[k].record(stream)
-            hot_path(noise, target, ev_m[k])
-            ev_b[k].record(stream)
-        barrier()
-    launches = pm.launch_count() - launches0
-    nk = lib.pm_profile_kinds(pm._ctx)
-    import ctypes
-    counts = (ctypes.c_int64 * nk)()
-    kms = (ctypes.c_double * nk)()
-    lib.pm_profile_read(pm._ctx, counts, kms, nk)
-    lib.pm_profile(pm._ctx, 0)
-    kernels = {lib.pm_profile_name(pm._ctx, i).decode(): (int(counts[i]), float(kms[i])) for i in range(nk)}
-    step_ms = [a.elapsed_time(b) for a, b in zip(ev_a, ev_b)]
-    fwd_ms = [a.elapsed_time(m) for a, m in zip(ev_a, ev_m)]
+        step_ms, fwd_ms, launches, _ = timed_steps(pm, stream, args.steps, step, barrier, split=True)
+        prof_ms, _, _, kernels = timed_steps(pm, stream, args.steps, step, barrier, profile=True)
     total_ms = float(sum(step_ms))
+    prof_total = float(sum(prof_ms))
 
     # end to end: pinned host inputs in, gradient out, every step
     h_noise = noise.cpu().pin_memory()
@@ -390,7 +414,7 @@ def run_ours(args):
         table = {}
         for kind, (cnt, ms) in kernels.items():
             ab = algorithmic_bytes(kind, npart, ncell, nmodes)
-            ent = {"launches": cnt, "total_ms": round(ms, 3), "share": round(ms / total_ms, 4)}
+            ent = {"launches": cnt, "total_ms": round(ms, 3), "share": round(ms / prof_total, 4)}
             if ab is not None and cnt:
                 ent["gbs"] = round(ab / (ms / cnt / 1e3) / 1e9, 1)
                 ent["frac"] = round(ent["gbs"] / hbm, 3)
@@ -417,6 +441,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": algorithmic_bytes(dom_kind, npart, ncell, nmodes),
                          "traffic": traffic},
             "kernels": table,
+            "profiled": {"ms_per_step": prof_total / args.steps, "pass": PROFILED_NOTE},
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -481,28 +506,12 @@ def run_learned(args):
     for _ in range(args.warmup):
         hot_path(noise)
     barrier()
-    lib = pm._lib
-    lib.pm_profile(pm._ctx, 1)
-    lib.pm_profile_read(pm._ctx, None, None, 0)
-    launches0 = pm.launch_count()
-    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     with ClockSampler(torch.cuda.current_device()) as clocks:
-        barrier()
-        for k in range(args.steps):
-            ev_a[k].record(stream)
-            hot_path(noise)
-            ev_b[k].record(stream)
-        barrier()
-    launches = pm.launch_count() - launches0
-    import ctypes
-    nk = lib.pm_profile_kinds(pm._ctx)
-    counts = (ctypes.c_int64 * nk)()
-    kms = (ctypes.c_double * nk)()
-    lib.pm_profile_read(pm._ctx, counts, kms, nk)
-    lib.pm_profile(pm._ctx, 0)
-    kernels = {lib.pm_profile_name(pm._ctx, i).decode(): (int(counts[i]), float(kms[i])) for i in range(nk)}
-    total_ms = float(sum(a.elapsed_time(b) for a, b in zip(ev_a, ev_b)))
+        step_ms, _, launches, _ = timed_steps(pm, stream, args.steps, lambda ev: hot_path(noise), barrier)
+        prof_ms, _, _, kernels = timed_steps(pm, stream, args.steps, lambda ev: hot_path(noise), barrier,
+                                             profile=True)
+    total_ms = float(sum(step_ms))
+    prof_total = float(sum(prof_ms))
 
     # end to end: noise from pinned host memory in, final displacements out
     h_noise = noise.cpu().pin_memory()
@@ -527,7 +536,7 @@ def run_learned(args):
         flops = 2.0 * (32 * 128 + 128 * 128 + 128 * 3) * cells     # algorithmic MLP flops per evaluation
         cnt, ms = kernels.get("nn_fwd_tc", (0, 0.0))
         achieved = flops / (ms / cnt / 1e3) / 1e12 if cnt else None
-        table = {k: {"launches": c, "total_ms": round(m, 3), "share": round(m / total_ms, 4)}
+        table = {k: {"launches": c, "total_ms": round(m, 3), "share": round(m / prof_total, 4)}
                  for k, (c, m) in kernels.items()}
         line = {
             "metric": LEARNED_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -540,7 +549,7 @@ def run_learned(args):
             "roofline": {"bound": "tensor", "kernel": "nn_fwd_tc", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
                          "peak_source": "measured (bf16, sustained)",
-                         "algorithmic_flops_per_launch": flops, "traffic": None},
+                         "algorithmic_flops_per_launch": flops, "traffic": _ncu_traffic("nn_fwd_tc", w.name)},
             "learned": {
                 "train_runs": args.learn_runs, "epochs": args.learn_epochs, "train_seconds": round(train_s, 1),
                 "k_cut_h_per_mpc": ev["k_cut"],
@@ -549,6 +558,7 @@ def run_learned(args):
                 "reference": "PM on a 4x finer mesh with 4x the steps, same 2LPT start",
             },
             "kernels": table,
+            "profiled": {"ms_per_step": prof_total / args.steps, "pass": PROFILED_NOTE},
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
             "e2e": {"value": world * work * args.steps / (e2e_max / 1e3), "unit": UNIT,
