@@ -164,6 +164,9 @@ def _ncu_traffic(kind, workload):
         d = json.load(fh)
     if d.get("source_digest") != _source_digest():
         return None
+    direct = d.get("direct", {}).get(workload, {}).get(kind)
+    if direct:                                  # captured on this workload itself
+        return float(direct["dram_bytes_per_launch"])
     ent = d.get("kernels", {}).get(kind)
     if not ent:
         return None
@@ -573,6 +576,60 @@ def run_learned(args):
     return 0
 
 
+def run_paint_stress(args):
+    """Paint and read kernels on a clustered state (half of the particles in
+    1 % of the volume) against the 2LPT state of the same workload: the last
+    KDK step and its adjoint, per-launch event timing, K repetitions after W
+    warm-up ones.  Prints one JSON line (a kernel measurement, not a bench
+    line)."""
+    import torch
+    from paper_2211_09958_gb300 import inputs
+    from paper_2211_09958_gb300.pm import ParticleMesh
+
+    w = WORKLOADS[args.workload]
+    t0 = time.time()
+    s_cl = torch.from_numpy(inputs.clustered_displacements(w.n_p, w.box, seed=w.ic_seed)).cuda()[None]
+    gen_s = time.time() - t0
+    pm = ParticleMesh(w.n_p, w.n_m, w.box, w.omega_m, w.sigma8, w.n_steps, w.a_init, w.a_final, w.h, w.n_s)
+    gen = torch.Generator(device=pm.device)
+    gen.manual_seed(w.ic_seed)
+    noise = torch.randn((1, w.n_p, w.n_p, w.n_p), generator=gen, device=pm.device, dtype=torch.float32)
+    s_lpt, p_lpt = pm.init_lpt(noise)
+    if not args.no_autotune:
+        pm.autotune(s_lpt)
+    stream = torch.cuda.current_stream()
+    last = w.n_steps - 1
+    kinds = ("paint_density", "paint_adj", "read_kick_drift", "read_half_kick", "read_adj")
+    out = {}
+    for name, s0 in (("uniform", s_lpt), ("clustered", s_cl)):
+        p0 = p_lpt
+        s, p, f = s0.clone(), p0.clone(), pm.new_particles()
+        lam, mu = torch.randn_like(s), torch.randn_like(p)
+
+        def step(ev):
+            s.copy_(s0)
+            p.copy_(p0)
+            pm.integrate(s, p, last, w.n_steps, f)
+            pm.adjoint_integrate(s, p, f, lam, mu, last, w.n_steps)
+
+        for _ in range(args.warmup):
+            step(None)
+        _, _, _, table = timed_steps(pm, stream, args.steps, step, torch.cuda.synchronize, profile=True)
+        out[name] = {k: table[k] for k in kinds if k in table}
+    res = {}
+    for k in kinds:
+        if k in out["uniform"] and k in out["clustered"]:
+            (cu, mu_), (cc, mc) = out["uniform"][k], out["clustered"][k]
+            res[k] = {"uniform_ms_per_launch": round(mu_ / cu, 4), "clustered_ms_per_launch": round(mc / cc, 4),
+                      "clustered_over_uniform": round((mc / cc) / (mu_ / cu), 3), "launches": cc}
+    print(json.dumps({"measurement": "paint/read kernels on a clustered state (1/2 of the particles in 1 % of "
+                                     "the volume) vs the 2LPT state", "workload": w.name, "steps": args.steps,
+                      "warmup": args.warmup, "tuning": pm.get_tuning(), "host_generation_s": round(gen_s, 1),
+                      "kernels": res}))
+    pm.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -585,7 +642,11 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--learn-runs", type=int, default=32, help="reference runs the correction trains on")
     ap.add_argument("--learn-epochs", type=int, default=3)
+    ap.add_argument("--paint-stress", action="store_true",
+                    help="time the paint and read kernels on a clustered state instead of the bench step")
     args = ap.parse_args()
+    if args.paint_stress:
+        return run_paint_stress(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == LEARNED_WORKLOAD:

@@ -16,8 +16,10 @@
  *   state      displacement s = x - q [Mpc/h], momentum p = a^3 E dx/da
  *   density    delta(c) = alpha sum_i W(x_i - c) - 1, CIC weights W,
  *              alpha = (n_m / n_p)^3, periodic
- *   force      F_j(k) = i k_j (3/2) Om delta(k) / k^2, zero at k = 0 and at
- *              the Nyquist index of axis j; F_i = sum_c W(x_i - c) F(c)
+ *   force      F_j(k) = i D_j(k) (3/2) Om delta(k) / k^2 with the 4-point
+ *              difference D_j = (8 sin k_j h - sin 2 k_j h) / (6 h) (k_j with
+ *              PM_SOLVER_SPECTRAL_GRADIENT), zero at k = 0 and at the Nyquist
+ *              index of axis j; F_i = sum_c W(x_i - c) F(c)
  *   step n     p += K_a[n] F(s); s += Dr[n] p; p += K_b[n] F(s), with
  *              growth-matched factors K(a->b; c) = (g_p(b) - g_p(a)) / g_f(c),
  *              Dr(a->b; c) = (D1(b) - D1(a)) / g_p(c), g_p = a^3 E D1',
@@ -172,6 +174,30 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end,
                          float *s, float *p, const float *f,
                          float *lam, float *mu, double *domega, uint32_t flags);
 
+/* Sparse checkpoints against FP32 reversal drift (a solver variant).  The
+ * adjoint reconstructs the trajectory by reverse time integration (paper:
+ * adjoint method with reverse time integration); in FP32 the reconstructed
+ * states drift from the forward ones by rounding, step after step.  With
+ * every > 0, pm_integrate stores, for each step m = every, 2 every, ...
+ * (0 < m < n_steps) that it runs, the displacement s_m at the start of step m
+ * and the half-step momentum p_{m+1/2} after that step's kick.
+ * pm_adjoint_integrate restores both when it enters step m, so a
+ * reconstructed state drifts over at most `every` steps.  The stored states
+ * are those of the latest pm_integrate: a caller that runs the adjoint of
+ * another trajectory turns checkpoints off first.  pm_kdk_step neither
+ * stores nor restores.
+ *   every  0 = off; values >= n_steps leave no slot and also turn them off
+ *   ckpt   caller-owned device buffer of pm_checkpoint_floats(ctx, every)
+ *          floats, 4-byte aligned, layout [slot][s | p][n_batch][n_p^3][3]
+ *          with slot = m / every - 1; it must outlive its use; NULL allowed
+ *          when there is no slot.
+ * pm_checkpoint_floats returns that size (0 when there is no slot; -1 for
+ * a NULL ctx or every < 0).  pm_set_checkpoints returns PM_EINVAL for
+ * every < 0 or a NULL / misaligned buffer that has slots; it drops the
+ * cached CUDA graphs of the integration loops (they hold the copies). */
+int64_t pm_checkpoint_floats(const pm_ctx *ctx, int32_t every);
+int pm_set_checkpoints(pm_ctx *ctx, int32_t every, float *ckpt);
+
 /* CIC density contrast alpha sum W - 1 of the particles at s.
  *   delta  device [n_batch][n_m^3] output. */
 int pm_density(pm_ctx *ctx, const float *s, float *delta);
@@ -295,8 +321,10 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  * inverse reads the spectrum (own transform, n_m >= 256): 1 per-thread
  * loads, 2 one TMA tensor copy per field into shared memory (default where
  * the driver provides the tensor-map encoder; a copy that does not complete
- * within a bounded wait is reported by the next synchronising call as
- * PM_ECUDA).  [6] is how the z-pass forward of 4 interleaved fields reads its
+ * within a bounded wait is reported as PM_ECUDA by the next call that
+ * synchronises for a host output: pm_adjoint_integrate with domega,
+ * pm_init_lpt_adjoint, pm_mse_loss, pm_power_spectrum, pm_nn_get_params,
+ * pm_profile_read).  [6] is how the z-pass forward of 4 interleaved fields reads its
  * rows (own transform): 1 per-thread strided loads, 2 coalesced 16-byte
  * loads staged through shared memory; default 1.
  *

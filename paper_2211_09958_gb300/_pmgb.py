@@ -16,6 +16,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 PM_OK = 0
 PM_ADJ_MU_ZERO = 1
 ERRORS = {-1: "PM_EINVAL", -2: "PM_ENOMEM", -3: "PM_ECUDA", -4: "PM_ECUFFT", -5: "PM_ERANGE", -6: "PM_ESTATE"}
+PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ECUFFT, PM_ERANGE, PM_ESTATE = -1, -2, -3, -4, -5, -6
 
 _c_double_p = ctypes.POINTER(ctypes.c_double)
 
@@ -79,6 +80,8 @@ _SIGNATURES = {
                                         ctypes.c_int,
                                         _c_double_p]),
     "pm_use_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pm_checkpoint_floats": (ctypes.c_int64, [_P, ctypes.c_int32]),
+    "pm_set_checkpoints": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "pm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pm_profile_kinds": (ctypes.c_int, [_P]),
     "pm_profile_name": (ctypes.c_char_p, [_P, ctypes.c_int]),

@@ -76,6 +76,10 @@ struct pm_ctx {
         int64_t launches;
     };
     std::vector<GraphEntry> graphs;
+    // sparse checkpoints (pm_set_checkpoints): s_m and p_{m+1/2} of the last
+    // forward run at steps m = every, 2 every, ... in a caller-owned buffer
+    int ck_every = 0;
+    float *ck_buf = nullptr;
     // launch shapes of the tunable kernel families: block sizes of paint,
     // read, spectral force/adjoint, z-pass FFT (n >= 256); x-pass pencil width
     int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8, 2, 1};
@@ -477,6 +481,27 @@ int run_graphed(pm_ctx *ctx, int kind, int b, int e, const void *q0, const void 
 
 double a_of(pm_ctx *ctx, int n) { return step_a(ctx->P, n); }
 
+// Checkpoint slot of step n (steps every, 2 every, ... below n_steps), or -1.
+int ck_slot(const pm_ctx *ctx, int n) {
+    if (ctx->ck_every <= 0 || n <= 0 || n % ctx->ck_every) return -1;
+    return n / ctx->ck_every - 1;
+}
+
+int64_t ck_slots(const pm_ctx *ctx, int every) { return every > 0 ? (ctx->P.n_steps - 1) / every : 0; }
+
+// One particle array of all runs: n_batch * n_p^3 * 3 floats.
+int64_t state_floats(const pm_ctx *ctx) { return ctx->g.npart * ctx->P.n_batch * 3; }
+
+// which = 0: s_m, 1: p_{m+1/2}.
+float *ck_ptr(pm_ctx *ctx, int slot, int which) {
+    return ctx->ck_buf + ((int64_t)slot * 2 + which) * state_floats(ctx);
+}
+
+int ck_copy(pm_ctx *ctx, float *dst, const float *src) {
+    PM_CUDA(ctx, cudaMemcpyAsync(dst, src, sizeof(float) * state_floats(ctx), cudaMemcpyDeviceToDevice, ctx->stream));
+    return PM_OK;
+}
+
 // Report (and clear) a device-side error flag (a TMA wait that timed out);
 // call after a stream synchronisation.
 int device_check(pm_ctx *ctx) {
@@ -790,6 +815,22 @@ int pm_use_graphs(pm_ctx *ctx, int enable) {
     return PM_OK;
 }
 
+int64_t pm_checkpoint_floats(const pm_ctx *ctx, int32_t every) {
+    if (!ctx || every < 0) return -1;
+    return ck_slots(ctx, every) * 2 * state_floats(ctx);
+}
+
+int pm_set_checkpoints(pm_ctx *ctx, int32_t every, float *ckpt) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    if (every < 0) return fail(ctx, PM_EINVAL, "every must be >= 0");
+    if (ck_slots(ctx, every) > 0) PM_TRY(check_ptr(ctx, ckpt, "ckpt"));
+    ctx->ck_every = ck_slots(ctx, every) > 0 ? every : 0;
+    ctx->ck_buf = ctx->ck_every ? ckpt : nullptr;
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);  // captured with the old copies
+    ctx->graphs.clear();
+    return PM_OK;
+}
+
 int pm_profile(pm_ctx *ctx, int enable) {
     if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
     ctx->prof = enable != 0;
@@ -807,6 +848,7 @@ int pm_profile_read(pm_ctx *ctx, int64_t *counts, double *ms, int n) {
     if (!ctx || (n > 0 && (!counts || !ms))) return fail(ctx, PM_EINVAL, "bad arguments");
     DeviceGuard guard(ctx->device);
     PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    PM_TRY(device_check(ctx));  // a bounded TMA wait that timed out
     for (int i = 0; i < n; ++i) {
         counts[i] = 0;
         ms[i] = 0.0;
@@ -1116,10 +1158,13 @@ int pm_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, fl
         ra.f = f;
         for (int n = step_begin; n < step_end; ++n) {
             PM_TRY(force_meshes(ctx, s, nullptr, a_of(ctx, n)));
+            const int ck = ck_slot(ctx, n);
+            if (ck >= 0) PM_TRY(ck_copy(ctx, ck_ptr(ctx, ck, 0), s));  // s_n
             ra.kick_step = n;
             ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
             ra.drift_step = n;
             PM_TRY(read_forces(ctx, READ_KICK_DRIFT, ra));
+            if (ck >= 0) PM_TRY(ck_copy(ctx, ck_ptr(ctx, ck, 1), p));  // p_{n+1/2}
         }
         PM_TRY(force_meshes(ctx, s, nullptr, a_of(ctx, step_end)));
         ra.kick_step = step_end - 1;
@@ -1174,6 +1219,11 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
             PM_TRY(read_forces(ctx, READ_ADJ, ra));
         }
         for (int n = last; n >= step_begin; --n) {
+            const int ck = ck_slot(ctx, n);
+            if (ck >= 0) {  // the loop holds (s_n, p_{n+1/2}) here: take the forward run's copies
+                PM_TRY(ck_copy(ctx, s, ck_ptr(ctx, ck, 0)));
+                PM_TRY(ck_copy(ctx, p, ck_ptr(ctx, ck, 1)));
+            }
             PM_TRY(force_meshes(ctx, s, mu, a_of(ctx, n), n, n == step_begin ? KICK_A : KICK_MERGED));
             ReadArgs ra = read_args(ctx, s);
             ra.p = p;
@@ -1257,6 +1307,7 @@ int pm_init_lpt_adjoint(pm_ctx *ctx, const float *noise, uint64_t seed, const fl
         PM_CUDA(ctx, cudaMemcpyAsync(red.data(), ctx->d_lred, sizeof(double) * red.size(), cudaMemcpyDeviceToHost,
                                      ctx->stream));
         PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        PM_TRY(device_check(ctx));  // a bounded TMA wait that timed out
         const double n3 = (double)np * np * np;
         for (int b = 0; b < B; ++b) {
             const HostTables &t = ctx->tabs[b];
@@ -1322,6 +1373,7 @@ int pm_mse_loss(pm_ctx *ctx, const float *s, const float *target, double *loss, 
     std::vector<double> acc(B);
     PM_CUDA(ctx, cudaMemcpyAsync(acc.data(), ctx->d_pk, sizeof(double) * B, cudaMemcpyDeviceToHost, ctx->stream));
     PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    PM_TRY(device_check(ctx));  // a bounded TMA wait that timed out
     const double n3 = std::pow((double)ctx->P.n_m, 3);
     for (int b = 0; b < B; ++b) loss[b] = acc[b] / n3;
     return PM_OK;
@@ -1389,6 +1441,7 @@ int pm_power_spectrum(pm_ctx *ctx, const float *s, double *k_mean, double *power
     PM_CUDA(ctx, cudaMemcpyAsync(acc.data(), ctx->d_pk, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost,
                                  ctx->stream));
     PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    PM_TRY(device_check(ctx));  // a bounded TMA wait that timed out
     const double vol = std::pow(ctx->P.box, 3);
     const double n6 = std::pow((double)ctx->P.n_m, 6);
     for (int b = 0; b < B; ++b)
@@ -1422,6 +1475,7 @@ int pm_nn_get_params(pm_ctx *ctx, float *theta, float *grad) {
     DeviceGuard guard(ctx->device);
     const int np = nn_param_count();
     PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    PM_TRY(device_check(ctx));  // a bounded TMA wait that timed out
     if (theta) PM_CUDA(ctx, cudaMemcpy(theta, ctx->nn_theta, sizeof(float) * np, cudaMemcpyDeviceToHost));
     if (grad) PM_CUDA(ctx, cudaMemcpy(grad, ctx->nn_grad, sizeof(float) * np, cudaMemcpyDeviceToHost));
     return PM_OK;

@@ -39,6 +39,29 @@ def random_displacements(n_p, box, seed, scale=0.3):
     return (rng.standard_normal((n_p ** 3, 3)) * scale * box / n_p).astype(np.float32)
 
 
+def clustered_displacements(n_p, box, seed, frac=0.5, volume=0.01, jitter=0.1):
+    """Stress state for the paint and read kernels: the lattice cube that
+    holds ``frac`` of the particles (side round(n_p frac^(1/3)) sites, corner
+    drawn from the seed, periodic) is pulled towards its centre until it
+    spans ``volume`` of the box; every particle also gets N(0, jitter^2)
+    spacings of noise.  With the defaults half of the particles sit in 1 % of
+    the volume, about 50 times the mean density.  Built from lattice index
+    differences only (no lattice offset enters), float32, shape (n_p^3, 3)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = box / n_p
+    side = max(1, int(round(n_p * frac ** (1.0 / 3.0))))
+    kappa = volume ** (1.0 / 3.0) * n_p / side       # compressed side / lattice side
+    corner = rng.integers(0, n_p, 3)
+    s = rng.standard_normal((n_p ** 3, 3), dtype=np.float32) * np.float32(jitter * h)
+    idx = np.arange(n_p)
+    off = [(idx - corner[d]) % n_p for d in range(3)]
+    cube = (off[0] < side)[:, None, None] & (off[1] < side)[None, :, None] & (off[2] < side)[None, None, :]
+    for d, shape in enumerate(((n_p, 1, 1), (1, n_p, 1), (1, 1, n_p))):
+        shift = ((kappa - 1.0) * (off[d] - (side - 1) / 2.0) * h).astype(np.float32).reshape(shape)
+        s[:, d] += np.where(cube, shift, np.float32(0.0)).ravel()
+    return s
+
+
 def mlp_params(sizes, seed, bias_scale=0.1):
     """Flat float32 parameters of a dense network with layer widths
     ``sizes``: per layer a weight matrix [fan_in][fan_out] drawn N(0, 2 /

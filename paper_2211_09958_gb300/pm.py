@@ -146,6 +146,19 @@ class ParticleMesh:
                    _ptr(mu), _pmgb._dptr(dom), _pmgb.PM_ADJ_MU_ZERO if mu_zero else 0)
         return dom
 
+    def set_checkpoints(self, every):
+        """Sparse checkpoints against FP32 reversal drift: integrate() keeps
+        s_m and p_{m+1/2} at every `every`-th step in a device buffer that
+        this object owns, and adjoint_integrate() restores them.  0 turns
+        them off and frees the buffer.  Returns the buffer (or None)."""
+        n = int(self._lib.pm_checkpoint_floats(self._ctx, int(every)))
+        if n < 0:
+            raise PMError("every must be >= 0")
+        buf = torch.empty(n, dtype=torch.float32, device=self.device) if n > 0 else None
+        self._call("pm_set_checkpoints", int(every), None if buf is None else _ptr(buf))
+        self._ck_buf = buf
+        return buf
+
     def density(self, s):
         self._particles(s, "s")
         d = torch.empty((self.n_batch, self.n_m, self.n_m, self.n_m), dtype=torch.float32, device=self.device)
