@@ -263,6 +263,74 @@ def force_vjp(s, v, setup):
     return term_a + term_b
 
 
+# ------------------------------------------- sampled and reduced cases ----
+# For meshes too large to run whole (the 512^3 / 1024^3 workload): values at
+# chosen cells, and a state whose 3D PM force reduces exactly to 1D.
+
+def lattice_sites(idx, n_p, box, n_m):
+    """Lagrangian positions of the given flat lattice indices (the rule of
+    `lattice`), (len(idx), 3)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    ijk = np.stack([idx // (n_p * n_p), (idx // n_p) % n_p, idx % n_p], axis=1)
+    return ijk * (box / n_p) + 0.5 * box / n_m
+
+
+def density_at(cells, s, setup, s_max):
+    """delta at the given flat mesh cells, each summed one by one over every
+    lattice site whose particle can reach it: with |s| <= s_max per axis the
+    CIC corners of site i along an axis lie within 2 + s_max / h nodes of
+    i n_m / n_p + 1/2, so a window of sites around the cell covers them all."""
+    n_p, n_m, h = setup.n_p, setup.n_m, setup.cell
+    r = n_m / n_p
+    half = int(np.ceil((2.0 + s_max / h) / r)) + 1
+    win = np.arange(-half, half + 1)
+    out = np.empty(len(cells))
+    for j, c in enumerate(np.asarray(cells, dtype=np.int64)):
+        cxyz = (c // (n_m * n_m), (c // n_m) % n_m, c % n_m)
+        ax = [(int(round((cxyz[d] - 0.5) / r)) + win) % n_p for d in range(3)]
+        ii = ((ax[0][:, None, None] * n_p + ax[1][None, :, None]) * n_p + ax[2][None, None, :]).ravel()
+        x = lattice_sites(ii, n_p, setup.box, n_m) + s[ii]
+        acc = 0.0
+        for flat, w, _ in cic_corners(x, n_m, h, setup.order):
+            acc += w[flat == c].sum()
+        out[j] = setup.alpha * acc - 1.0
+    return out
+
+
+def force_uniform_yz(sx, setup):
+    """PM force on a state uniform in y and z: every particle of lattice
+    plane i_x has s = (sx[i_x], 0, 0).  With the half-cell lattice offset and
+    n_m / n_p = 1 or 2, every y and every z node then receives the same CIC
+    weight from each row of particles (n_p / n_m), so the density and the
+    force depend on x alone, F_y = F_z = 0 (D(0) = 0), and the 3D definition
+    above is exactly its 1D restriction:
+        rho_1(c) = (n_m / n_p) sum_i w(u_i - c) - 1
+        F(k) = i D(k) (3/2) Om rho_1(k) / k^2 (zero at k = 0 and Nyquist)
+        F_i = sum_c w(u_i - c) F(c)
+    (3D DFT normalisation: the y and z sums give n_m^2 forward and 1 / n_m^2
+    back).  Returns F_x per lattice plane, (n_p,).  CIC only."""
+    n_p, n_m, h = setup.n_p, setup.n_m, setup.cell
+    if setup.order != 2 or n_m not in (n_p, 2 * n_p):
+        raise ValueError("the 1D reduction holds for CIC with n_m = n_p or 2 n_p")
+    x = np.arange(n_p) * (setup.box / n_p) + 0.5 * h + np.asarray(sx, dtype=np.float64)
+    base, ax = _axis_weights(x / h, 2, h)
+    rho = np.zeros(n_m)
+    for k, (w, _) in enumerate(ax):
+        rho += np.bincount((base + k) % n_m, weights=w, minlength=n_m)
+    rho = (n_m / n_p) * rho - 1.0
+    kx = 2.0 * np.pi / setup.box * np.arange(n_m // 2 + 1)
+    k2 = np.where(kx > 0, kx * kx, 1.0)
+    if setup.solver & DECONVOLVE:
+        k2 = k2 * cic_window(kx, h) ** 2
+    d = kx if setup.solver & SPECTRAL_GRADIENT else gradient_operator(kx, h)
+    mult = np.where((kx > 0) & (np.arange(n_m // 2 + 1) != n_m // 2), 1j * d * 1.5 * setup.cosmo.omega_m / k2, 0.0)
+    fmesh = sfft.irfft(mult * sfft.rfft(rho), n=n_m)
+    out = np.zeros(n_p)
+    for k, (w, _) in enumerate(ax):
+        out += w * fmesh[(base + k) % n_m]
+    return out
+
+
 # ---------------------------------------------------------------- KDK ----
 
 def coefficients(setup):

@@ -8,6 +8,7 @@ import pytest
 
 from oracle import pm
 from oracle.pm import Setup
+from paper_2211_09958_gb300 import inputs
 
 
 def _tent_mesh(x, n, cell):
@@ -334,3 +335,31 @@ def test_tsc_linear_force_converges(ratio):
         f = pm.force(s, st)[:, 0]
         errs.append(abs(f @ s[:, 0] / (s[:, 0] @ s[:, 0]) / (1.5 * 0.3) - 1.0))
     assert errs[0] < 5e-2 and errs[1] < errs[0] / 3.0, errs
+
+
+# ------------------------------------------- sampled and reduced cases ----
+
+@pytest.mark.parametrize("n_p,n_m,box", [(16, 32, 64.0), (16, 16, 48.0), (12, 18, 40.0)])
+def test_density_at_sampled_cells_matches_the_full_mesh(n_p, n_m, box):
+    st = pm.Setup(n_p, n_m, box)
+    s = inputs.random_displacements(n_p, box, seed=31, scale=0.8).astype(np.float64)
+    full = pm.density(s, st).ravel()
+    cells = np.random.default_rng(3).integers(0, n_m ** 3, 40)
+    got = pm.density_at(cells, s, st, np.abs(s).max())
+    np.testing.assert_allclose(got, full[cells], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("n_p,n_m,solver", [(16, 32, 0), (16, 16, 0), (16, 32, 1), (16, 32, 2)])
+def test_plane_wave_force_reduces_to_one_dimension(n_p, n_m, solver):
+    box = 64.0
+    st = pm.Setup(n_p, n_m, box, solver=solver)
+    i = np.arange(n_p)
+    sx = 0.4 * (box / n_p) * np.sin(2 * np.pi * 3 * (i + 0.25) / n_p) + 0.1 * (box / n_p) * np.cos(2 * np.pi * 5 * i / n_p)
+    s = np.zeros((n_p, n_p, n_p, 3))
+    s[..., 0] = sx[:, None, None]
+    f = pm.force(s.reshape(-1, 3), st).reshape(n_p, n_p, n_p, 3)
+    fx = pm.force_uniform_yz(sx, st)
+    scale = np.abs(fx).max()
+    assert scale > 0
+    np.testing.assert_allclose(f[..., 0], np.broadcast_to(fx[:, None, None], f.shape[:3]), rtol=0, atol=1e-12 * scale)
+    assert np.abs(f[..., 1:]).max() < 1e-12 * scale
