@@ -140,6 +140,8 @@ def algorithmic_bytes(kind, npart, ncell, nmodes):
             return nf * (4 * ncell + 8 * nmodes)          # real fields in, half spectra out
         if axis == "z":
             return nf * 8 * nmodes + (4 if nf == 1 else 16) * ncell   # spectra in, real mesh out
+        if direction == "round":                          # fused x pass: density in, 3 fields out; 4 in, 4 out
+            return (8 + 24) * nmodes if nf == 1 else 64 * nmodes
         return nf * 16 * nmodes                             # pencil pass: read + write
     return per.get(kind)
 

@@ -326,7 +326,11 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  * pm_init_lpt_adjoint, pm_mse_loss, pm_power_spectrum, pm_nn_get_params,
  * pm_profile_read).  [6] is how the z-pass forward of 4 interleaved fields reads its
  * rows (own transform): 1 per-thread strided loads, 2 coalesced 16-byte
- * loads staged through shared memory; default 1.
+ * loads staged through shared memory; default 1.  [7] is how a force
+ * evaluation crosses the x axis of the spectrum (own transform): 1 three
+ * launches (forward x pass, Green's function times gradient, inverse x
+ * pass), 2 one fused kernel that takes each x line through all three
+ * without writing the spectrum back in between; default 2.
  *
  * pm_autotune     times every candidate of each family in turn (the others
  *                 held at their current best) on this context's scratch
@@ -336,10 +340,10 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  *                 the fastest.  ms (host, may be NULL) receives the mean
  *                 time in ms of each candidate, [family][3] in the order
  *                 above (0 where not timed).  Synchronises the stream.
- * pm_set_tuning   set all five explicitly (PM_EINVAL for other values)
+ * pm_set_tuning   set all of them explicitly (PM_EINVAL for other values)
  * pm_get_tuning   read them (host int[PM_TUNE_KINDS])
  * Results do not depend on the choice beyond the order of FP32 atomics. */
-#define PM_TUNE_KINDS 7
+#define PM_TUNE_KINDS 8
 int pm_autotune(pm_ctx *ctx, const float *s, float *ms);
 int pm_set_tuning(pm_ctx *ctx, const int *threads);
 int pm_get_tuning(pm_ctx *ctx, int *threads);

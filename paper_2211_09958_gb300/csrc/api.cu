@@ -82,7 +82,7 @@ struct pm_ctx {
     float *ck_buf = nullptr;
     // launch shapes of the tunable kernel families: block sizes of paint,
     // read, spectral force/adjoint, z-pass FFT (n >= 256); x-pass pencil width
-    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8, 2, 1};
+    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8, 2, 1, 2};
     // learned force correction (own-FFT meshes only)
     bool nn_on = false;
     void *nn_packed = nullptr;
@@ -291,6 +291,11 @@ Spec mesh_spec(pm_ctx *ctx) {
                 ctx->d_grad, ctx->d_dec, ctx->tune[2]};
 }
 
+// Multipliers of the fused x round trip: the spectral kernels' tables.
+XRoundArgs xround_args(pm_ctx *ctx) {
+    return XRoundArgs{(float)(2.0 * M_PI / ctx->P.box), ctx->d_grad, ctx->d_dec, ctx->d_pref};
+}
+
 MeshRef lat_ref(pm_ctx *ctx) {
     return MeshRef{ctx->lat, ctx->lat_pad * ctx->P.n_batch, ctx->lat_pad, 2 * (ctx->P.n_p / 2 + 1), 0};
 }
@@ -404,12 +409,23 @@ int force_meshes(pm_ctx *ctx, const float *s, const float *mu, double a = -1.0, 
         pa.mesh = adj ? mesh_ref(ctx) : density_ref(ctx);
         PM_MEMSET(ctx, cudaMemsetAsync(real, 0, sizeof(float) * n3 * nf * ctx->P.n_batch, ctx->stream));
         PM_LAUNCH(ctx, paint_kind(mode), launch_paint(mode, pa, ctx->stream));
-        PM_TRY(own_forward(ctx, real, nf));
-        PM_LAUNCH(ctx, (adj ? "spectral_adj" : "spectral_force"),
-                  launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream));
-        // the correction's adjoint reads the painted (rho, mu) still in r4
-        if (adj && ctx->nn_on && a > 0.0) PM_TRY(correction_adjoint(ctx, a, kick_step, kick_sel));
-        PM_TRY(own_inverse(ctx, ctx->r4, adj ? 4 : 3));
+        const int go = adj ? 4 : 3;
+        if (ctx->tune[7] == 2) {  // z and y forward, fused x round trip, y and z inverse
+            PM_LAUNCH(ctx, own_kind(0, nf), launch_fft_z_fwd(nf, real, ctx->spec, ctx->fg, ctx->stream));
+            PM_LAUNCH(ctx, own_kind(1, nf), launch_fft_pencils(1, false, ctx->spec, 0, nf, ctx->fg, ctx->stream));
+            PM_LAUNCH(ctx, (adj ? "fft_x_round_4" : "fft_x_round_1"),
+                      launch_fft_xround(adj, ctx->spec, ctx->fg, xround_args(ctx), ctx->stream));
+            if (adj && ctx->nn_on && a > 0.0) PM_TRY(correction_adjoint(ctx, a, kick_step, kick_sel));
+            PM_LAUNCH(ctx, own_kind(4, go), launch_fft_pencils(1, true, ctx->spec, 0, go, ctx->fg, ctx->stream));
+            PM_LAUNCH(ctx, own_kind(5, go), launch_fft_z_inv(go, ctx->spec, ctx->r4, ctx->fg, ctx->stream));
+        } else {
+            PM_TRY(own_forward(ctx, real, nf));
+            PM_LAUNCH(ctx, (adj ? "spectral_adj" : "spectral_force"),
+                      launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream));
+            // the correction's adjoint reads the painted (rho, mu) still in r4
+            if (adj && ctx->nn_on && a > 0.0) PM_TRY(correction_adjoint(ctx, a, kick_step, kick_sel));
+            PM_TRY(own_inverse(ctx, ctx->r4, go));
+        }
         if (!adj && ctx->nn_on && a > 0.0) PM_TRY(apply_correction(ctx, a));
         if (adj && ctx->nn_on && a > 0.0) {
             const int64_t n4 = nn_cells(ctx);
@@ -687,13 +703,14 @@ int64_t pm_launch_count(const pm_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 const int kTuneCand[PM_TUNE_KINDS][3] = {{128, 256, 512}, {128, 256, 512}, {128, 256, 512},
                                          {128, 256, 512}, {8, 16, 0},      {1, 2, 0},
-                                         {1, 2, 0}};
+                                         {1, 2, 0},       {1, 2, 0}};
 
 static int set_tuning(pm_ctx *ctx, const int *t) {
     for (int k = 0; k < PM_TUNE_KINDS; ++k)
         if (t[k] <= 0 || (t[k] != kTuneCand[k][0] && t[k] != kTuneCand[k][1] && t[k] != kTuneCand[k][2]))
             return fail(ctx, PM_EINVAL,
-                        "block sizes must be 128, 256 or 512, the x-pass width 8 or 16, the z stagings 1 or 2");
+                        "block sizes must be 128, 256 or 512, the x-pass width 8 or 16, the z stagings and "
+                        "the x round trip 1 or 2");
     for (int k = 0; k < PM_TUNE_KINDS; ++k) ctx->tune[k] = t[k];
     ctx->fg.zthreads = ctx->tune[3];
     ctx->fg.xwidth = ctx->tune[4];
@@ -757,6 +774,22 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
             return launch_fft_pencils(0, true, ctx->spec, 0, 4, ctx->fg, ctx->stream);
         }
         if (kind == 6) return launch_fft_z_fwd(4, ctx->r4, ctx->spec, ctx->fg, ctx->stream);
+        if (kind == 7) {  // the x side of a force and an adjoint evaluation
+            if (ctx->tune[7] == 2) {
+                if ((e = launch_fft_xround(false, ctx->spec, ctx->fg, xround_args(ctx), ctx->stream)) != cudaSuccess)
+                    return e;
+                return launch_fft_xround(true, ctx->spec, ctx->fg, xround_args(ctx), ctx->stream);
+            }
+            for (int adj = 0; adj < 2 && e == cudaSuccess; ++adj) {
+                if ((e = launch_fft_pencils(0, false, ctx->spec, 0, adj ? 4 : 1, ctx->fg, ctx->stream)) != cudaSuccess)
+                    return e;
+                if ((e = launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream)) !=
+                    cudaSuccess)
+                    return e;
+                e = launch_fft_pencils(0, true, ctx->spec, 0, adj ? 4 : 3, ctx->fg, ctx->stream);
+            }
+            return e;
+        }
         if (kind == 5) {
             if ((e = launch_fft_z_inv(3, ctx->spec, ctx->r4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
             return launch_fft_z_inv(4, ctx->spec, ctx->r4, ctx->fg, ctx->stream);
@@ -771,7 +804,8 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
     rc = force_meshes(ctx, s, nullptr);
     for (int kind = 0; kind < PM_TUNE_KINDS && rc == PM_OK; ++kind) {
         if ((kind == 3 && !(ctx->own && ctx->P.n_m >= 256)) || (kind == 4 && !ctx->own) ||
-            (kind == 5 && !(ctx->own && ctx->zmaps[0].valid)) || (kind == 6 && !ctx->own)) {
+            (kind == 5 && !(ctx->own && ctx->zmaps[0].valid)) || (kind == 6 && !ctx->own) ||
+            (kind == 7 && !ctx->own)) {
             if (ms) ms[3 * kind] = ms[3 * kind + 1] = ms[3 * kind + 2] = 0.f;
             continue;
         }

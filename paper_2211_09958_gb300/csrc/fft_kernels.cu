@@ -498,6 +498,197 @@ cudaError_t pencil_l(float2 *data, const PencilGeom &pg, int width, int n, int64
     }
 }
 
+// ------------------------------------------------------ fused x round trip --
+//
+// The x pass is the last forward transform and the first inverse one, with
+// the Green's-function multiply between them, so one kernel takes each x
+// pencil (8 kz columns of one y row) through all three without writing the
+// spectrum back in between.  Thread (r, w) of M1 x 8 runs the forward
+// four-step FFT of column w and keeps X[k] for k = k2 + M2 k1, k2 = r + M1 j,
+// in registers (k1 in bit-reversed order).  An inverse transform starts from
+// that state:
+//   x[m1 + M1 m2] = sum_k2 e^{2 pi i k2 m2 / M2} e^{2 pi i k2 m1 / L}
+//                   sum_k1 Y[k2 + M2 k1] e^{2 pi i k1 m1 / M1},
+// an M1-point FFT over k1 in registers, a twiddle, one shared-memory exchange
+// and an M2-point FFT over k2, stored to rows m1 + M1 m2.
+//
+// Multipliers (the spectral kernels' definitions, with g = pref / k^2 times
+// the per-axis deconvolution factors, 0 at k = 0 and in the kz padding):
+//   force    F_j = i D_j g delta.  D_y and D_z are constant along an x line,
+//            so F_y = i D_y phi and F_z = i D_z phi with phi = IFFT_x(g delta):
+//            two inverse transforms (phi and F_x) give the three fields.
+//   adjoint  psi = -i g (D_x u_x + D_y u_y + D_z u_z) and the force from
+//            delta as above: four forward and three inverse transforms.
+// Fields are read before they are overwritten (in place: force 0 -> 0, 1, 2;
+// adjoint 0..3 -> 0..3).
+
+// Forward x FFT of one pencil column: X[j][i] = X[k2 + M2 bitrev(i)], k2 = r + M1 j.
+template <int L>
+__device__ __forceinline__ void xr_forward(const float2 *src, int64_t ls, float2 *ys, int r, int w,
+                                           float2 (&X)[msplit(L) / lsplit(L)][lsplit(L)],
+                                           const float2 *__restrict__ tw) {
+    constexpr int M1 = lsplit(L), M2 = msplit(L), W = kPencil, YP = M2 * W + W;
+    float2 v[M2];
+#pragma unroll
+    for (int n2 = 0; n2 < M2; ++n2) v[n2] = src[(r + M1 * n2) * ls];
+    reg_fft<M2, false>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) ys[r * YP + k2 * W + w] = cmul(v[bitrev(k2, ilog2(M2))], __ldg(tw + r * k2 * (1024 / L)));
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < M2 / M1; ++j) {
+        const int k2 = r + M1 * j;
+#pragma unroll
+        for (int n1 = 0; n1 < M1; ++n1) X[j][n1] = ys[n1 * YP + k2 * W + w];
+        reg_fft<M1, false>(X[j]);
+    }
+    __syncthreads();
+}
+
+// Inverse x FFT of Y, Y[j][k1] = Y[k2 + M2 k1] in natural k1 order (the
+// first FFT runs in place on it), to rows of dst0 (times i s0 when scaled)
+// and, with TWO, also dst1 times i s1.
+template <int L, bool TWO>
+__device__ __forceinline__ void xr_inverse(float2 (&Y)[msplit(L) / lsplit(L)][lsplit(L)], float2 *dst0, float2 *dst1,
+                                           float s0, float s1, bool scaled, int64_t ls, float2 *ys, int r, int w,
+                                           const float2 *__restrict__ tw) {
+    constexpr int M1 = lsplit(L), M2 = msplit(L), W = kPencil, YP = M2 * W + W;
+#pragma unroll
+    for (int j = 0; j < M2 / M1; ++j) {
+        const int k2 = r + M1 * j;
+        reg_fft<M1, true>(Y[j]);
+#pragma unroll
+        for (int m1 = 0; m1 < M1; ++m1) {
+            float2 t = __ldg(tw + k2 * m1 * (1024 / L));
+            t.y = -t.y;
+            ys[m1 * YP + k2 * W + w] = cmul(Y[j][bitrev(m1, ilog2(M1))], t);
+        }
+    }
+    __syncthreads();
+    float2 g[M2];
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) g[k2] = ys[r * YP + k2 * W + w];
+    reg_fft<M2, true>(g);
+#pragma unroll
+    for (int m2 = 0; m2 < M2; ++m2) {
+        const float2 x = g[bitrev(m2, ilog2(M2))];
+        const int64_t off = (r + M1 * m2) * ls;
+        dst0[off] = scaled ? make_float2(-s0 * x.y, s0 * x.x) : x;
+        if (TWO) dst1[off] = make_float2(-s1 * x.y, s1 * x.x);
+    }
+    __syncthreads();
+}
+
+template <int L, bool ADJ>
+__global__ void __launch_bounds__(lsplit(L) * kPencil, 1) k_fft_xround(float2 *spec, FftGeom fg, XRoundArgs xa) {
+    constexpr int M1 = lsplit(L), M2 = msplit(L), W = kPencil, J = M2 / M1;
+    extern __shared__ float4 smraw[];
+    float2 *ys = reinterpret_cast<float2 *>(smraw);
+    const int tid = threadIdx.x, w = tid % W, r = tid / W;
+    const int kzblocks = fg.zc / W;
+    const int64_t p = blockIdx.x;
+    const int y = (int)(p % L);
+    const int64_t outer = p / L;  // run * (zc / 8) + kz block
+    const int run = (int)(outer / kzblocks);
+    const int iz = (int)(outer % kzblocks) * W + w;
+    const int64_t ls = (int64_t)L * W;
+    float2 *base = spec + outer * ((int64_t)L * L * W) + (int64_t)y * W + w;
+    const int64_t fs = fg.fstride;
+    const float kyz2 = xa.kf * xa.kf * (float)((y < L / 2 ? y : y - L) * (y < L / 2 ? y : y - L) + iz * iz);
+    const float dyz = iz > L / 2 ? 0.f : __ldg(xa.pref + run) * __ldg(xa.dec + y) * __ldg(xa.dec + iz);
+    const float gy = __ldg(xa.grad + y), gz = iz > L / 2 ? 0.f : __ldg(xa.grad + iz);
+    // g of mode k2 + M2 k1 (k2 = r + M1 j) and D_x there
+    auto gmode = [&](int j, int k1, float &gx) -> float {
+        const int ix = r + M1 * j + M2 * k1;
+        const int nx = ix < L / 2 ? ix : ix - L;
+        const float k2 = xa.kf * xa.kf * (float)(nx * nx) + kyz2;
+        gx = __ldg(xa.grad + ix);
+        return k2 > 0.f ? dyz * __ldg(xa.dec + ix) / k2 : 0.f;
+    };
+    // X[j][i] holds mode k1 = bitrev(i); Y[j][k1] is built in natural order
+    float2 X[J][M1], Y[J][M1];
+    if (ADJ) {
+        // psi = -i g (D_x u_x + D_y u_y + D_z u_z) from the three cotangent fields
+        xr_forward<L>(base + fs, ls, ys, r, w, X, fg.tw);
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+            for (int k1 = 0; k1 < M1; ++k1) {
+                float gx;
+                gmode(j, k1, gx);
+                const float2 u = X[j][bitrev(k1, ilog2(M1))];
+                Y[j][k1] = make_float2(gx * u.x, gx * u.y);
+            }
+        xr_forward<L>(base + 2 * fs, ls, ys, r, w, X, fg.tw);
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+            for (int k1 = 0; k1 < M1; ++k1) {
+                const float2 u = X[j][bitrev(k1, ilog2(M1))];
+                Y[j][k1] = make_float2(Y[j][k1].x + gy * u.x, Y[j][k1].y + gy * u.y);
+            }
+        xr_forward<L>(base + 3 * fs, ls, ys, r, w, X, fg.tw);
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+            for (int k1 = 0; k1 < M1; ++k1) {
+                float gx;
+                const float g = gmode(j, k1, gx);
+                const float2 u = X[j][bitrev(k1, ilog2(M1))];
+                const float2 a = make_float2(Y[j][k1].x + gz * u.x, Y[j][k1].y + gz * u.y);
+                Y[j][k1] = make_float2(g * a.y, -g * a.x);  // -i g a
+            }
+        xr_inverse<L, false>(Y, base + 3 * fs, nullptr, 0.f, 0.f, false, ls, ys, r, w, fg.tw);
+    }
+    // the force from delta (field 0): phi = IFFT_x(g delta) -> F_y, F_z; then F_x
+    xr_forward<L>(base, ls, ys, r, w, X, fg.tw);
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+        for (int k1 = 0; k1 < M1; ++k1) {
+            float gx;
+            const float g = gmode(j, k1, gx);
+            const float2 d = X[j][bitrev(k1, ilog2(M1))];
+            Y[j][k1] = make_float2(g * d.x, g * d.y);
+        }
+    xr_inverse<L, true>(Y, base + fs, base + 2 * fs, gy, gz, true, ls, ys, r, w, fg.tw);
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+        for (int k1 = 0; k1 < M1; ++k1) {
+            float gx;
+            const float g = gmode(j, k1, gx) * gx;
+            const float2 d = X[j][bitrev(k1, ilog2(M1))];
+            Y[j][k1] = make_float2(-g * d.y, g * d.x);  // i D_x g delta
+        }
+    xr_inverse<L, false>(Y, base, nullptr, 0.f, 0.f, false, ls, ys, r, w, fg.tw);
+}
+
+template <int L, bool ADJ>
+cudaError_t xround_l(float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
+    constexpr int M1 = lsplit(L), M2 = msplit(L);
+    const size_t smem = sizeof(float2) * M1 * (M2 * kPencil + kPencil);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_xround<L, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (int64_t)fg.nb * (fg.zc / kPencil) * L;
+    k_fft_xround<L, ADJ><<<(unsigned)blocks, M1 * kPencil, smem, st>>>(spec, fg, xa);
+    return cudaGetLastError();
+}
+
+template <bool ADJ>
+cudaError_t xround_n(float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
+    switch (fg.n) {
+        case 16: return xround_l<16, ADJ>(spec, fg, xa, st);
+        case 32: return xround_l<32, ADJ>(spec, fg, xa, st);
+        case 64: return xround_l<64, ADJ>(spec, fg, xa, st);
+        case 128: return xround_l<128, ADJ>(spec, fg, xa, st);
+        case 256: return xround_l<256, ADJ>(spec, fg, xa, st);
+        case 512: return xround_l<512, ADJ>(spec, fg, xa, st);
+        case 1024: return xround_l<1024, ADJ>(spec, fg, xa, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 // Copy between the blocked spectrum (field 0) and a plain
 // [run][x][y][n/2 + 1] half spectrum.
 __global__ void k_spec_copy(float2 *blocked, float2 *plain, FftGeom fg, bool to_plain) {
@@ -611,6 +802,15 @@ cudaError_t launch_fft_pencils(int axis, bool inverse, float2 *spec, int f0, int
     const int64_t blocks = (int64_t)nf * fg.nb * (fg.zc / kPencil) * pg.nmid;
     return inverse ? pencil_l<true>(base, pg, width, n, blocks, fg.tw, st)
                    : pencil_l<false>(base, pg, width, n, blocks, fg.tw, st);
+}
+
+// Fused x round trip of the spectrum: forward x pass, spectral multiply,
+// inverse x pass (force: field 0 -> fields 0..2; adjoint: fields 0..3 ->
+// 0..3), replacing launch_fft_pencils(0, false, ...), the spectral kernel and
+// launch_fft_pencils(0, true, ...).
+cudaError_t launch_fft_xround(bool adj, float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
+    if (!xa.grad || !xa.dec || !xa.pref || !own_fft_supported(fg.n)) return cudaErrorInvalidValue;
+    return adj ? xround_n<true>(spec, fg, xa, st) : xround_n<false>(spec, fg, xa, st);
 }
 
 }  // namespace pmgb

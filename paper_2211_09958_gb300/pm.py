@@ -234,14 +234,15 @@ class ParticleMesh:
         return loss.value
 
     # ------------------------------------------------------- autotuner --
-    TUNE_FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x", "z_staging", "z_fwd_staging")
+    TUNE_FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x", "z_staging", "z_fwd_staging", "x_round")
 
     def autotune(self, s):
         """Pick the fastest launch shape per kernel family on particles s;
         returns (chosen {family: value}, times [family][candidate] ms; the
         block-size families try 128, 256, 512 threads, fft_x widths 8, 16,
         z_staging 1 (loads) and 2 (TMA), z_fwd_staging 1 (strided loads) and
-        2 (coalesced, staged))."""
+        2 (coalesced, staged), x_round 1 (x pass, spectral multiply and
+        inverse x pass as three launches) and 2 (one fused kernel))."""
         self._particles(s, "s")
         ms = np.zeros((len(self.TUNE_FAMILIES), 3), np.float32)
         self._call("pm_autotune", _ptr(s), ms.ctypes.data_as(ctypes.c_void_p))
@@ -252,10 +253,11 @@ class ParticleMesh:
         self._call("pm_get_tuning", t.ctypes.data_as(ctypes.c_void_p))
         return dict(zip(self.TUNE_FAMILIES, (int(v) for v in t)))
 
-    def set_tuning(self, paint=256, read=256, spectral=256, fft_z=256, fft_x=8, z_staging=None, z_fwd_staging=1):
+    def set_tuning(self, paint=256, read=256, spectral=256, fft_z=256, fft_x=8, z_staging=None, z_fwd_staging=1,
+                   x_round=2):
         if z_staging is None:
             z_staging = self.get_tuning()["z_staging"]
-        t = np.array([paint, read, spectral, fft_z, fft_x, z_staging, z_fwd_staging], np.int32)
+        t = np.array([paint, read, spectral, fft_z, fft_x, z_staging, z_fwd_staging, x_round], np.int32)
         self._call("pm_set_tuning", t.ctypes.data_as(ctypes.c_void_p))
 
     def use_graphs(self, enable=True):

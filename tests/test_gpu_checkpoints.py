@@ -14,6 +14,11 @@ forward runs agree to rounding, not bit for bit: 1e-5 of the spacing):
     spacing of the forward one (a single reverse drift of rounding), far below
     the drift of the unchecked reversal;
   * gradients with checkpoints match the FP64 oracle at the parity bounds;
+  * dL/dOm of the dynamics with steps uniform in ln a: a small sum of large
+    cancelling per-step terms, some weighted by the early, small momenta
+    whose FP32 reconstruction drifts most (up to ~1e-3 of the sum of the
+    terms' magnitudes without checkpoints); with a checkpoint at every step
+    it meets the oracle at 1e-4 of that sum, the bound of the parity tests;
   * bad arguments are rejected and leave the context usable.
 """
 
@@ -133,4 +138,29 @@ def test_bad_checkpoint_arguments_are_rejected():
     assert pm._lib.pm_set_checkpoints(pm._ctx, 2, ctypes.c_void_p(bad.data_ptr() + 2)) == _pmgb.PM_EINVAL
     _, s0, p0 = _ic(pm, 6)
     pm.integrate(s0, p0)                                                  # still usable
+    pm.close()
+
+
+@pytest.mark.parametrize("n_p,n_m,solver", [(16, 16, 4), (16, 32, 6)])
+def test_checkpoints_remove_the_drift_from_the_omega_gradient(n_p, n_m, solver):
+    from oracle.cosmology import kdk_coefficients_domega
+    from paper_2211_09958_gb300.pm import ParticleMesh
+    box, steps = 4.0 * n_p, 4
+    pm = ParticleMesh(n_p, n_m, box, 0.3, 0.8, steps, solver=solver)
+    pm.set_checkpoints(1)
+    noise = inputs.white_noise(n_p, 9)
+    rng = np.random.default_rng(3)
+    lam0 = rng.standard_normal((n_p ** 3, 3)).astype(np.float32)
+    mu0 = rng.standard_normal((n_p ** 3, 3)).astype(np.float32)
+    s, p = pm.init_lpt(torch.from_numpy(noise).cuda()[None])
+    f = pm.integrate(s, p)
+    lam, mu = torch.from_numpy(lam0).cuda()[None], torch.from_numpy(mu0).cuda()[None]
+    dom = pm.adjoint_integrate(s, p, f, lam, mu)[0]
+    st = opm.Setup(n_p, n_m, box, Cosmology(0.3, 0.8), n_steps=steps, solver=solver)
+    rs, rp, rf = opm.simulate(noise.astype(np.float64), st)
+    _, _, _, _, grads = opm.adjoint_integrate(rs, rp, rf, lam0.astype(np.float64), mu0.astype(np.float64), st)
+    o_dom = opm.dynamics_domega(grads, st)
+    d = kdk_coefficients_domega(st.cosmo, st.a_init, st.a_final, st.n_steps, bool(solver & 4))
+    cond = abs(grads["omega_m_direct"]) + sum(abs(np.dot(grads[k], d[k])) for k in ("K_a", "Dr", "K_b"))
+    assert abs(dom - o_dom) <= 1e-4 * cond, (dom, o_dom, cond)
     pm.close()
