@@ -291,6 +291,10 @@ Spec mesh_spec(pm_ctx *ctx) {
                 ctx->d_grad, ctx->d_dec, ctx->tune[2]};
 }
 
+// Whether a force (adj = false) or adjoint evaluation takes the fused x
+// round trip: x_round tuning 2 = both, 3 = the force only.
+bool x_fused(const pm_ctx *ctx, bool adj) { return ctx->tune[7] == 2 || (ctx->tune[7] == 3 && !adj); }
+
 // Multipliers of the fused x round trip: the spectral kernels' tables.
 XRoundArgs xround_args(pm_ctx *ctx) {
     return XRoundArgs{(float)(2.0 * M_PI / ctx->P.box), ctx->d_grad, ctx->d_dec, ctx->d_pref};
@@ -410,7 +414,7 @@ int force_meshes(pm_ctx *ctx, const float *s, const float *mu, double a = -1.0, 
         PM_MEMSET(ctx, cudaMemsetAsync(real, 0, sizeof(float) * n3 * nf * ctx->P.n_batch, ctx->stream));
         PM_LAUNCH(ctx, paint_kind(mode), launch_paint(mode, pa, ctx->stream));
         const int go = adj ? 4 : 3;
-        if (ctx->tune[7] == 2) {  // z and y forward, fused x round trip, y and z inverse
+        if (x_fused(ctx, adj)) {  // z and y forward, fused x round trip, y and z inverse
             PM_LAUNCH(ctx, own_kind(0, nf), launch_fft_z_fwd(nf, real, ctx->spec, ctx->fg, ctx->stream));
             PM_LAUNCH(ctx, own_kind(1, nf), launch_fft_pencils(1, false, ctx->spec, 0, nf, ctx->fg, ctx->stream));
             PM_LAUNCH(ctx, (adj ? "fft_x_round_4" : "fft_x_round_1"),
@@ -703,14 +707,14 @@ int64_t pm_launch_count(const pm_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 const int kTuneCand[PM_TUNE_KINDS][3] = {{128, 256, 512}, {128, 256, 512}, {128, 256, 512},
                                          {128, 256, 512}, {8, 16, 0},      {1, 2, 0},
-                                         {1, 2, 0},       {1, 2, 0}};
+                                         {1, 2, 0},       {1, 2, 3}};
 
 static int set_tuning(pm_ctx *ctx, const int *t) {
     for (int k = 0; k < PM_TUNE_KINDS; ++k)
         if (t[k] <= 0 || (t[k] != kTuneCand[k][0] && t[k] != kTuneCand[k][1] && t[k] != kTuneCand[k][2]))
             return fail(ctx, PM_EINVAL,
-                        "block sizes must be 128, 256 or 512, the x-pass width 8 or 16, the z stagings and "
-                        "the x round trip 1 or 2");
+                        "block sizes must be 128, 256 or 512, the x-pass width 8 or 16, the z stagings 1 or 2, "
+                        "the x round trip 1, 2 or 3");
     for (int k = 0; k < PM_TUNE_KINDS; ++k) ctx->tune[k] = t[k];
     ctx->fg.zthreads = ctx->tune[3];
     ctx->fg.xwidth = ctx->tune[4];
@@ -775,12 +779,11 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
         }
         if (kind == 6) return launch_fft_z_fwd(4, ctx->r4, ctx->spec, ctx->fg, ctx->stream);
         if (kind == 7) {  // the x side of a force and an adjoint evaluation
-            if (ctx->tune[7] == 2) {
-                if ((e = launch_fft_xround(false, ctx->spec, ctx->fg, xround_args(ctx), ctx->stream)) != cudaSuccess)
-                    return e;
-                return launch_fft_xround(true, ctx->spec, ctx->fg, xround_args(ctx), ctx->stream);
-            }
             for (int adj = 0; adj < 2 && e == cudaSuccess; ++adj) {
+                if (x_fused(ctx, adj != 0)) {
+                    e = launch_fft_xround(adj != 0, ctx->spec, ctx->fg, xround_args(ctx), ctx->stream);
+                    continue;
+                }
                 if ((e = launch_fft_pencils(0, false, ctx->spec, 0, adj ? 4 : 1, ctx->fg, ctx->stream)) != cudaSuccess)
                     return e;
                 if ((e = launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream)) !=

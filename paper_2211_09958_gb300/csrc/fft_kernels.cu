@@ -579,8 +579,20 @@ __device__ __forceinline__ void xr_inverse(float2 (&Y)[msplit(L) / lsplit(L)][ls
     __syncthreads();
 }
 
+// The force variant on lines of 512 and more points does not keep the
+// forward result: its second inverse transform re-runs the forward one from
+// the input pencil (just read, so from L2), which halves the registers and
+// lets two blocks share an SM.  (The adjoint variant's psi accumulator would
+// still spill; it keeps one block per SM.)
 template <int L, bool ADJ>
-__global__ void __launch_bounds__(lsplit(L) * kPencil, 1) k_fft_xround(float2 *spec, FftGeom fg, XRoundArgs xa) {
+struct XRoundShape {
+    static constexpr bool RELOAD = L >= 512 && !ADJ;
+    static constexpr int MINB = RELOAD ? 2 : 1;
+};
+
+template <int L, bool ADJ>
+__global__ void __launch_bounds__(lsplit(L) * kPencil, XRoundShape<L, ADJ>::MINB)
+    k_fft_xround(float2 *spec, FftGeom fg, XRoundArgs xa) {
     constexpr int M1 = lsplit(L), M2 = msplit(L), W = kPencil, J = M2 / M1;
     extern __shared__ float4 smraw[];
     float2 *ys = reinterpret_cast<float2 *>(smraw);
@@ -651,7 +663,8 @@ __global__ void __launch_bounds__(lsplit(L) * kPencil, 1) k_fft_xround(float2 *s
             const float2 d = X[j][bitrev(k1, ilog2(M1))];
             Y[j][k1] = make_float2(g * d.x, g * d.y);
         }
-    xr_inverse<L, true>(Y, base + fs, base + 2 * fs, gy, gz, true, ls, ys, r, w, fg.tw);
+    xr_inverse<L, true>(Y, base + fs, base + 2 * fs, gy, gz, true, ls, ys, r, w, fg.tw);  // F_y, F_z
+    if (XRoundShape<L, ADJ>::RELOAD) xr_forward<L>(base, ls, ys, r, w, X, fg.tw);  // delta again (field 0 is intact)
 #pragma unroll
     for (int j = 0; j < J; ++j)
 #pragma unroll

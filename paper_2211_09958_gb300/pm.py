@@ -242,7 +242,8 @@ class ParticleMesh:
         block-size families try 128, 256, 512 threads, fft_x widths 8, 16,
         z_staging 1 (loads) and 2 (TMA), z_fwd_staging 1 (strided loads) and
         2 (coalesced, staged), x_round 1 (x pass, spectral multiply and
-        inverse x pass as three launches) and 2 (one fused kernel))."""
+        inverse x pass as three launches), 2 (one fused kernel) and 3 (fused
+        for the force, three launches for the adjoint))."""
         self._particles(s, "s")
         ms = np.zeros((len(self.TUNE_FAMILIES), 3), np.float32)
         self._call("pm_autotune", _ptr(s), ms.ctypes.data_as(ctypes.c_void_p))

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x", "z_staging", "z_fwd_staging", "x_round")
 CANDIDATES = {"paint": (128, 256, 512), "read": (128, 256, 512), "spectral": (128, 256, 512),
               "fft_z": (128, 256, 512), "fft_x": (8, 16), "z_staging": (1, 2), "z_fwd_staging": (1, 2),
-              "x_round": (1, 2)}
+              "x_round": (1, 2, 3)}
 DEFAULT = {"paint": 256, "read": 256, "spectral": 256, "fft_z": 256, "fft_x": 8, "z_staging": 2, "z_fwd_staging": 1,
            "x_round": 2}
 
