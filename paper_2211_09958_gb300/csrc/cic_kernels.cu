@@ -46,11 +46,27 @@ __global__ void __launch_bounds__(T) k_paint(PaintArgs a) {
     float *base = a.mesh.ptr + (int64_t)b * a.mesh.bstride;
     constexpr int NF = MODE == PAINT_ADJ ? 4 : 1;
     const bool il = NF == 4 && a.mesh.il == 4;
+    // density, CIC: the two z corners are adjacent floats unless the stencil
+    // wraps; when both sit in one 16-byte aligned group of four they go in a
+    // single vector reduction (the other two lanes add zero)
+    const int z0 = st.n[2][0];
+    const bool zpair = NF == 1 && K == 2 && st.n[2][1] == z0 + 1 && (z0 & 3) != 3;
 #pragma unroll
     for (int ox = 0; ox < K; ++ox)
 #pragma unroll
         for (int oy = 0; oy < K; ++oy) {
             const int64_t row = ((int64_t)st.n[0][ox] * nm + st.n[1][oy]) * zs;
+            if (zpair) {
+                float *grp = base + row + (z0 & ~3);
+                if ((reinterpret_cast<uintptr_t>(grp) & 15) == 0) {
+                    const float wxy = st.w[0][ox] * st.w[1][oy] * wv[0];
+                    const float lo = wxy * st.w[2][0], hi = wxy * st.w[2][1];
+                    const int lane = z0 & 3;  // 0, 1 or 2: lo at lane, hi at lane + 1
+                    red_add_v4(grp, lane == 0 ? lo : 0.f, lane == 1 ? lo : (lane == 0 ? hi : 0.f),
+                               lane == 2 ? lo : (lane == 1 ? hi : 0.f), lane == 2 ? hi : 0.f);
+                    continue;
+                }
+            }
 #pragma unroll
             for (int oz = 0; oz < K; ++oz) {
                 const float w = st.w[0][ox] * st.w[1][oy] * st.w[2][oz];
