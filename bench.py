@@ -373,7 +373,10 @@ def run_ours(args):
             dist.barrier()
 
     tuning = pm.get_tuning()
-    if not args.no_autotune:                              # untimed: the library's own launch-shape tuner
+    if args.tuning:                                       # fixed launch shapes (e.g. those a plain run picked)
+        pm.set_tuning(**{**tuning, **args.tuning})
+        tuning = pm.get_tuning()
+    elif not args.no_autotune:                            # untimed: the library's own launch-shape tuner
         s_t, _ = pm.init_lpt(noise)
         tuning, _ = pm.autotune(s_t)
         del s_t
@@ -493,7 +496,10 @@ def run_learned(args):
     noise = torch.randn((pm.n_batch, w.n_p, w.n_p, w.n_p), generator=gen, device=dev, dtype=torch.float32)
     stream = torch.cuda.current_stream()
     tuning = pm.get_tuning()
-    if not args.no_autotune:
+    if args.tuning:
+        pm.set_tuning(**{**tuning, **args.tuning})
+        tuning = pm.get_tuning()
+    elif not args.no_autotune:
         s_t, _ = pm.init_lpt(noise)
         tuning, _ = pm.autotune(s_t)
         del s_t
@@ -632,6 +638,15 @@ def run_paint_stress(args):
     return 0
 
 
+def _tuning_arg(text):
+    """'family=value,...' -> {family: int}."""
+    out = {}
+    for item in text.split(","):
+        k, _, v = item.partition("=")
+        out[k.strip()] = int(v)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -642,6 +657,8 @@ def main():
     ap.add_argument("--sim-steps", type=int, default=0, help="override the number of KDK steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--tuning", type=_tuning_arg, default=None,
+                    help="fixed launch shapes instead of the autotuner, e.g. paint=512,read=128,x_round=3")
     ap.add_argument("--learn-runs", type=int, default=32, help="reference runs the correction trains on")
     ap.add_argument("--learn-epochs", type=int, default=3)
     ap.add_argument("--paint-stress", action="store_true",
