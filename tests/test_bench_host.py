@@ -1,0 +1,64 @@
+"""Host side of the benchmark: the JSON line of the reference arm (the FP64
+oracle on the CPU), the algorithmic byte model behind the roofline, the
+fixed-tuning argument and the DRAM traffic lookup.  No GPU."""
+
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+N, M = 512 ** 3, 1024 ** 3
+K = 1024 * 1024 * 520          # modes per field on the blocked 1024^3 spectrum
+
+
+def test_reference_arm_prints_the_contract_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["dtype"] == "f64"
+    assert line["config"]["workload"] == "pm512_mesh1024"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_algorithmic_bytes_per_launch():
+    ab = lambda kind: bench.algorithmic_bytes(kind, N, M, K)  # noqa: E731
+    assert ab("paint_density") == 12 * N + 4 * M            # s in; one field out
+    assert ab("paint_adj") == 24 * N + 16 * M               # s, mu in; four fields out
+    assert ab("fft_z_fwd_4") == 4 * (4 * M + 8 * K)         # reals in, half spectra out
+    assert ab("fft_z_inv_3") == 3 * 8 * K + 16 * M          # spectra in, 4-slot mesh out
+    assert ab("fft_z_inv_1") == 8 * K + 4 * M
+    assert ab("fft_y_fwd_4") == 4 * 16 * K                  # pencil pass: read + write
+    assert ab("spectral_force") == 32 * K and ab("spectral_adj") == 64 * K
+    assert ab("fft_x_round_1") == 32 * K and ab("fft_x_round_4") == 64 * K
+    assert ab("no_such_kernel") is None
+    # the fused x round trip saves two spectrum round trips per evaluation
+    assert ab("fft_x_fwd_1") + ab("spectral_force") + ab("fft_x_inv_3") - ab("fft_x_round_1") == 64 * K
+    assert ab("fft_x_fwd_4") + ab("spectral_adj") + ab("fft_x_inv_4") - ab("fft_x_round_4") == 128 * K
+
+
+def test_tuning_argument():
+    assert bench._tuning_arg("paint=512,read=128,x_round=3") == {"paint": 512, "read": 128, "x_round": 3}
+
+
+def test_traffic_lookup_needs_the_current_sources(monkeypatch):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    with open(path) as fh:
+        digest = json.load(fh)["source_digest"]
+    monkeypatch.setattr(bench, "_source_digest", lambda: digest)
+    direct = bench._ncu_traffic("paint_adj", "pm512_mesh1024")
+    assert direct is not None and direct > bench.algorithmic_bytes("paint_adj", N, M, K)
+    assert bench._ncu_traffic("no_such_kernel", "pm512_mesh1024") is None
+    monkeypatch.setattr(bench, "_source_digest", lambda: "changed")
+    assert bench._ncu_traffic("paint_adj", "pm512_mesh1024") is None
