@@ -297,7 +297,8 @@ bool x_fused(const pm_ctx *ctx, bool adj) { return ctx->tune[7] == 2 || (ctx->tu
 
 // Multipliers of the fused x round trip: the spectral kernels' tables.
 XRoundArgs xround_args(pm_ctx *ctx) {
-    return XRoundArgs{(float)(2.0 * M_PI / ctx->P.box), ctx->d_grad, ctx->d_dec, ctx->d_pref};
+    return XRoundArgs{(float)(2.0 * M_PI / ctx->P.box), ctx->d_grad, ctx->d_dec, ctx->d_pref,
+                      (float)(ctx->P.n_m / (12.0 * ctx->P.box)), (ctx->P.solver & PM_SOLVER_SPECTRAL_GRADIENT) ? 0 : 1};
 }
 
 MeshRef lat_ref(pm_ctx *ctx) {

@@ -518,19 +518,18 @@ cudaError_t pencil_l(float2 *data, const PencilGeom &pg, int width, int n, int64
 //            so F_y = i D_y phi and F_z = i D_z phi with phi = IFFT_x(g delta):
 //            two inverse transforms (phi and F_x) give the three fields.
 //   adjoint  psi = -i g (D_x u_x + D_y u_y + D_z u_z) and the force from
-//            delta as above: four forward and three inverse transforms.
+//            delta as above.  With the 4-point difference gradient, psi takes
+//            one forward transform of a line built in real space (see the
+//            kernel); with the exact spectral gradient, three accumulated ones.
 // Fields are read before they are overwritten (in place: force 0 -> 0, 1, 2;
 // adjoint 0..3 -> 0..3).
 
 // Forward x FFT of one pencil column: X[j][i] = X[k2 + M2 bitrev(i)], k2 = r + M1 j.
 template <int L>
-__device__ __forceinline__ void xr_forward(const float2 *src, int64_t ls, float2 *ys, int r, int w,
-                                           float2 (&X)[msplit(L) / lsplit(L)][lsplit(L)],
-                                           const float2 *__restrict__ tw) {
+__device__ __forceinline__ void xr_forward_regs(float2 (&v)[msplit(L)], float2 *ys, int r, int w,
+                                                float2 (&X)[msplit(L) / lsplit(L)][lsplit(L)],
+                                                const float2 *__restrict__ tw) {
     constexpr int M1 = lsplit(L), M2 = msplit(L), W = kPencil, YP = M2 * W + W;
-    float2 v[M2];
-#pragma unroll
-    for (int n2 = 0; n2 < M2; ++n2) v[n2] = src[(r + M1 * n2) * ls];
     reg_fft<M2, false>(v);
 #pragma unroll
     for (int k2 = 0; k2 < M2; ++k2) ys[r * YP + k2 * W + w] = cmul(v[bitrev(k2, ilog2(M2))], __ldg(tw + r * k2 * (1024 / L)));
@@ -543,6 +542,18 @@ __device__ __forceinline__ void xr_forward(const float2 *src, int64_t ls, float2
         reg_fft<M1, false>(X[j]);
     }
     __syncthreads();
+}
+
+// The same from thread (r, w)'s points x = r + M1 n2 of column w in global memory.
+template <int L>
+__device__ __forceinline__ void xr_forward(const float2 *src, int64_t ls, float2 *ys, int r, int w,
+                                           float2 (&X)[msplit(L) / lsplit(L)][lsplit(L)],
+                                           const float2 *__restrict__ tw) {
+    constexpr int M1 = lsplit(L), M2 = msplit(L);
+    float2 v[M2];
+#pragma unroll
+    for (int n2 = 0; n2 < M2; ++n2) v[n2] = src[(r + M1 * n2) * ls];
+    xr_forward_regs<L>(v, ys, r, w, X, tw);
 }
 
 // Inverse x FFT of Y, Y[j][k1] = Y[k2 + M2 k1] in natural k1 order (the
@@ -579,19 +590,21 @@ __device__ __forceinline__ void xr_inverse(float2 (&Y)[msplit(L) / lsplit(L)][ls
     __syncthreads();
 }
 
-// The force variant on lines of 512 and more points does not keep the
-// forward result: its second inverse transform re-runs the forward one from
-// the input pencil (just read, so from L2), which halves the registers and
-// lets two blocks share an SM.  (The adjoint variant's psi accumulator would
-// still spill; it keeps one block per SM.)
-template <int L, bool ADJ>
+// Lines of 512 and more points do not keep the forward result: the force's
+// second inverse transform re-runs the forward one from the input pencil
+// (just read, so from L2), which halves the registers and lets two blocks
+// share an SM.  With the 4-point difference gradient (FD) the adjoint builds
+// psi from one forward transform (below) and takes the same form; with the
+// exact spectral gradient it accumulates over three forward transforms and
+// keeps one block per SM.
+template <int L, bool ADJ, bool FD>
 struct XRoundShape {
-    static constexpr bool RELOAD = L >= 512 && !ADJ;
+    static constexpr bool RELOAD = L >= 512 && (!ADJ || FD);
     static constexpr int MINB = RELOAD ? 2 : 1;
 };
 
-template <int L, bool ADJ>
-__global__ void __launch_bounds__(lsplit(L) * kPencil, XRoundShape<L, ADJ>::MINB)
+template <int L, bool ADJ, bool FD>
+__global__ void __launch_bounds__(lsplit(L) * kPencil, XRoundShape<L, ADJ, FD>::MINB)
     k_fft_xround(float2 *spec, FftGeom fg, XRoundArgs xa) {
     constexpr int M1 = lsplit(L), M2 = msplit(L), W = kPencil, J = M2 / M1;
     extern __shared__ float4 smraw[];
@@ -619,7 +632,42 @@ __global__ void __launch_bounds__(lsplit(L) * kPencil, XRoundShape<L, ADJ>::MINB
     };
     // X[j][i] holds mode k1 = bitrev(i); Y[j][k1] is built in natural order
     float2 X[J][M1], Y[J][M1];
-    if (ADJ) {
+    if (ADJ && FD) {
+        // psi = -i g sum_j D_j u_j = -g FFT_x(S_x u_x + i (D_y u_y + D_z u_z)): S_x is the periodic
+        // 4-point difference along the line, whose Fourier symbol is i D_x, and D_y, D_z are
+        // constant along it, so one forward transform of a line built in real space does it.
+        // u_x (field 1) is staged in shared memory as [x][column] for the stencil.
+#pragma unroll
+        for (int n2 = 0; n2 < M2; ++n2) {
+            const int x = r + M1 * n2;
+            ys[x * W + w] = base[fs + x * ls];
+        }
+        __syncthreads();
+        float2 v[M2];
+#pragma unroll
+        for (int n2 = 0; n2 < M2; ++n2) {
+            const int x = r + M1 * n2;
+            const float2 a1 = ys[((x + 1) & (L - 1)) * W + w], b1 = ys[((x - 1) & (L - 1)) * W + w];
+            const float2 a2 = ys[((x + 2) & (L - 1)) * W + w], b2 = ys[((x - 2) & (L - 1)) * W + w];
+            const float sx = xa.inv12h * (8.f * (a1.x - b1.x) - (a2.x - b2.x));
+            const float sy = xa.inv12h * (8.f * (a1.y - b1.y) - (a2.y - b2.y));
+            const float2 uy = base[2 * fs + x * ls], uz = base[3 * fs + x * ls];
+            const float tx = gy * uy.x + gz * uz.x, ty = gy * uy.y + gz * uz.y;
+            v[n2] = make_float2(sx - ty, sy + tx);  // S_x u_x + i t
+        }
+        __syncthreads();  // the stencil reads are done: the transform reuses the buffer
+        xr_forward_regs<L>(v, ys, r, w, X, fg.tw);
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+            for (int k1 = 0; k1 < M1; ++k1) {
+                float gx;
+                const float g = gmode(j, k1, gx);
+                const float2 a = X[j][bitrev(k1, ilog2(M1))];
+                Y[j][k1] = make_float2(-g * a.x, -g * a.y);
+            }
+        xr_inverse<L, false>(Y, base + 3 * fs, nullptr, 0.f, 0.f, false, ls, ys, r, w, fg.tw);
+    } else if (ADJ) {
         // psi = -i g (D_x u_x + D_y u_y + D_z u_z) from the three cotangent fields
         xr_forward<L>(base + fs, ls, ys, r, w, X, fg.tw);
 #pragma unroll
@@ -664,7 +712,7 @@ __global__ void __launch_bounds__(lsplit(L) * kPencil, XRoundShape<L, ADJ>::MINB
             Y[j][k1] = make_float2(g * d.x, g * d.y);
         }
     xr_inverse<L, true>(Y, base + fs, base + 2 * fs, gy, gz, true, ls, ys, r, w, fg.tw);  // F_y, F_z
-    if (XRoundShape<L, ADJ>::RELOAD) xr_forward<L>(base, ls, ys, r, w, X, fg.tw);  // delta again (field 0 is intact)
+    if (XRoundShape<L, ADJ, FD>::RELOAD) xr_forward<L>(base, ls, ys, r, w, X, fg.tw);  // delta again (field 0 is intact)
 #pragma unroll
     for (int j = 0; j < J; ++j)
 #pragma unroll
@@ -677,27 +725,34 @@ __global__ void __launch_bounds__(lsplit(L) * kPencil, XRoundShape<L, ADJ>::MINB
     xr_inverse<L, false>(Y, base, nullptr, 0.f, 0.f, false, ls, ys, r, w, fg.tw);
 }
 
-template <int L, bool ADJ>
+template <int L, bool ADJ, bool FD>
 cudaError_t xround_l(float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
     constexpr int M1 = lsplit(L), M2 = msplit(L);
-    const size_t smem = sizeof(float2) * M1 * (M2 * kPencil + kPencil);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_xround<L, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sizeof(float2) * M1 * (M2 * kPencil + kPencil);  // >= L * 8 for the stencil stage
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fft_xround<L, ADJ, FD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)fg.nb * (fg.zc / kPencil) * L;
-    k_fft_xround<L, ADJ><<<(unsigned)blocks, M1 * kPencil, smem, st>>>(spec, fg, xa);
+    k_fft_xround<L, ADJ, FD><<<(unsigned)blocks, M1 * kPencil, smem, st>>>(spec, fg, xa);
     return cudaGetLastError();
+}
+
+template <int L, bool ADJ>
+cudaError_t xround_fd(float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
+    if (ADJ && xa.fd) return xround_l<L, ADJ, ADJ>(spec, fg, xa, st);
+    return xround_l<L, ADJ, false>(spec, fg, xa, st);
 }
 
 template <bool ADJ>
 cudaError_t xround_n(float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
     switch (fg.n) {
-        case 16: return xround_l<16, ADJ>(spec, fg, xa, st);
-        case 32: return xround_l<32, ADJ>(spec, fg, xa, st);
-        case 64: return xround_l<64, ADJ>(spec, fg, xa, st);
-        case 128: return xround_l<128, ADJ>(spec, fg, xa, st);
-        case 256: return xround_l<256, ADJ>(spec, fg, xa, st);
-        case 512: return xround_l<512, ADJ>(spec, fg, xa, st);
-        case 1024: return xround_l<1024, ADJ>(spec, fg, xa, st);
+        case 16: return xround_fd<16, ADJ>(spec, fg, xa, st);
+        case 32: return xround_fd<32, ADJ>(spec, fg, xa, st);
+        case 64: return xround_fd<64, ADJ>(spec, fg, xa, st);
+        case 128: return xround_fd<128, ADJ>(spec, fg, xa, st);
+        case 256: return xround_fd<256, ADJ>(spec, fg, xa, st);
+        case 512: return xround_fd<512, ADJ>(spec, fg, xa, st);
+        case 1024: return xround_fd<1024, ADJ>(spec, fg, xa, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -180,11 +180,14 @@ bool encode_z_inv_maps(float2 *spec, const FftGeom &fg, ZInvMap maps[3]);
 // gs = 4 or 3: spectrum fields -> 4-slot interleaved real mesh; gs = 1: plain real mesh.
 cudaError_t launch_fft_z_inv(int gs, const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st);
 // Multipliers of the fused x round trip (launch_fft_xround): the spectral
-// kernels' gradient and deconvolution tables, kf = 2 pi / box and the
-// per-run prefactor (3/2) Om / n^3.
+// kernels' gradient and deconvolution tables, kf = 2 pi / box, the per-run
+// prefactor (3/2) Om / n^3, and for the stencil form of the adjoint's psi
+// 1 / (12 h) and whether the gradient is the 4-point difference.
 struct XRoundArgs {
     float kf;
     const float *grad, *dec, *pref;
+    float inv12h;  // 1 / (12 h): the 4-point difference stencil along x
+    int fd;        // the gradient is the 4-point difference (not the spectral i k)
 };
 cudaError_t launch_fft_xround(bool adj, float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st);
 cudaError_t launch_fft_pencils(int axis, bool inverse, float2 *spec, int f0, int nf, const FftGeom &fg,
