@@ -29,9 +29,9 @@ pm         CIC mass assignment / interpolation, spectral Poisson force,
            adjoint, the density-MSE loss and the power-spectrum estimator
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
-against closed forms, brute-force definitions, finite differences or
-invariants, except the exact bit pattern of the Philox stream, which is
-pinned only statistically ("parity unpinned" for its bits).
+against closed forms, brute-force definitions, finite differences,
+invariants or, for the Philox4x32-10 round function, the generator's
+published known-answer vectors (bit for bit).
 """
 
 from .cosmology import Cosmology, growth, kdk_coefficients, linear_power  # noqa: F401

@@ -11,7 +11,8 @@ lattice site, followed by the Box-Muller transform.           [reading]
   z  = sqrt(-2 ln u1) cos(2 pi u2)
 
 The round function and constants are the published ones; this file is written
-from that definition.  Bit pattern: parity unpinned (pinned statistically).
+from that definition.  Pinned bit for bit against the generator's published
+known-answer vectors; the Gaussian field it yields is pinned statistically.
 """
 
 import numpy as np
