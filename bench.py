@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -69,11 +70,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"pm_bench_clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -465,7 +465,7 @@ def run_ours(args):
 
 def run_learned(args):
     """The learned-correction workload: train the network on reference runs
-    (untimed), judge its P(k) gain, then time the corrected forward
+    (untimed), evaluate its P(k) gain, then time the corrected forward
     integration of a batch of 4 runs (2LPT + 40 corrected KDK steps)."""
     rank, local_rank, world = _dist_env()
     w = WORKLOADS[args.workload]

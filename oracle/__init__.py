@@ -16,7 +16,7 @@ discretize-then-optimize choice, i.e. gradients that run backward along the
 same discrete trajectory as the forward integrator (Statement of Need).  It
 prints no equations, so every formula here is a reading of that prose in the
 standard comoving PM form; each reading is marked ``[reading]`` where it is
-made and collected in DESIGN.md.
+made.
 
 Modules
 -------

@@ -12,7 +12,7 @@ with more time steps:
              sample (s, T = F_fine(s) - F_coarse(s), a_n)
   loss       force matching, mean over particles of |dF(s) - T|^2
              (pm_nn_train_step), Adam
-  judge      the P(k) of the final density of the corrected coarse run
+  evaluate   the P(k) of the final density of the corrected coarse run
              against the reference, next to the plain coarse run and plain PM
              at 2x the coarse mesh, all measured on one mesh
 

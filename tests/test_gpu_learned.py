@@ -159,7 +159,7 @@ def test_corrected_integration_parity():
     assert calls[0] == pm.n_steps + 1
     # A bf16 rounding decision that FP32 and FP64 accumulation take
     # differently changes one hidden activation of one cell by 2^-8 relative;
-    # the particles near that cell then drift apart, so the benchmark spec's bound
+    # the particles near that cell then drift apart, so the state bound
     # (1e-4 of the spacing) holds for 99.9 % of the particles and a 10x
     # looser one for all of them.
     spacing = pm.box / pm.n_p

@@ -4,7 +4,7 @@ correction, include/pmgb.h pm_nn_*; training in paper_2211_09958_gb300/learn.py)
 Workload (small version of the 128^3 / 128^3 / 40-step one): 64^3 particles
 on a 64^3 mesh in a 128 Mpc/h box, 20 KDK steps from a = 1/64; reference PM
 on a 4x finer mesh (256^3) with 4x the steps; the network trained on 16
-seeded reference runs, judged on 4 other seeds by the P(k) of the final
+seeded reference runs, evaluated on 4 other seeds by the P(k) of the final
 density, all measured on the reference mesh, up to half the coarse mesh's
 Nyquist frequency.  Plain PM there is ~29 % low; the correction must take
 at least half of that error away, and no bin may get worse than plain PM.

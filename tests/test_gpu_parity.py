@@ -4,7 +4,7 @@ Inputs come from the seeded generators of ``paper_2211_09958_gb300.inputs``
 and reach both sides as the same float32 values.  Tolerances (FP32 vs FP64,
 non-bit-exact because floating-point atomics add in arbitrary order):
   * particle state: max |ds| <= 1e-4 of the mean inter-particle spacing
-    (spec bound), max |dp| <= 1e-4 of max |p| (the same relative
+    (the target accuracy of the method's state), max |dp| <= 1e-4 of max |p| (the same relative
     bound on the momentum scale; the largest errors sit with the largest
     momenta, in collapsed regions)
   * reversal (forward then reverse, both FP32): |ds| <= 1e-4 of the spacing
@@ -14,7 +14,7 @@ non-bit-exact because floating-point atomics add in arbitrary order):
   * force: max |dF| <= 2e-5 of max |F| (FP32 paint/FFT/read rounding,
     ~1e-7 per operation times the log2(n^3) FFT depth and the 8-corner sums)
   * density: 1e-5 of alpha (sums of at most a few dozen FP32 weights)
-  * power spectrum: 1e-3 relative per bin (spec 0.1 %)
+  * power spectrum: 1e-3 relative per bin (the 0.1 % target accuracy of P(k))
   * gradients: relative L2 <= 1e-3 and cosine >= 0.9999; sigma8 derivative
     within 1e-3 relative.  dL/dOm is a sum of contributions (initial
     conditions, force prefactor, each KDK factor) that are ~100x larger than
