@@ -147,12 +147,17 @@ def algorithmic_bytes(kind, npart, ncell, nmodes):
 
 
 def _source_digest():
+    """Digest of the library sources that hold device code (kernels and the
+    headers they include): a DRAM traffic capture stays valid while these
+    are unchanged.  Host-only orchestration files do not enter."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2211_09958_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cpp", ".h")):
+        if f.endswith((".cu", ".cuh", ".cpp", ".h")):
             with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+                text = fh.read()
+            if b"__global__" in text or b"__device__" in text:
+                h.update(text)
     return h.hexdigest()[:16]
 
 

@@ -349,6 +349,19 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms);
 int pm_set_tuning(pm_ctx *ctx, const int *threads);
 int pm_get_tuning(pm_ctx *ctx, int *threads);
 
+/* Test hook for the failure path of the bounded device waits.  Sets, on the
+ * context stream, the error flag a kernel sets when its wait runs out,
+ * without making any kernel wait:
+ *   which = 0  the z-pass inverse's TMA copy of the spectrum; reported by
+ *              the calls listed under tuning family [5]
+ *   which = 1  the learned correction's MMA completion; reported by
+ *              pm_nn_predict and pm_nn_enable
+ * The reporting call returns PM_ECUDA and clears the flag; the context stays
+ * usable.  Returns PM_EINVAL for another `which`.  Returns PM_ESTATE when the
+ * context has no such wait: no library FFT (0), or no network parameters
+ * set (1). */
+int pm_inject_wait_timeout(pm_ctx *ctx, int which);
+
 /* Device-kernel launch counter since pm_create (for benchmarking). */
 int64_t pm_launch_count(const pm_ctx *ctx);
 

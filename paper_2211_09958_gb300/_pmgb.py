@@ -82,6 +82,7 @@ _SIGNATURES = {
     "pm_use_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
     "pm_checkpoint_floats": (ctypes.c_int64, [_P, ctypes.c_int32]),
     "pm_set_checkpoints": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "pm_inject_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int]),
     "pm_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "pm_profile_kinds": (ctypes.c_int, [_P]),
     "pm_profile_name": (ctypes.c_char_p, [_P, ctypes.c_int]),

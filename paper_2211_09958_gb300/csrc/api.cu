@@ -853,6 +853,18 @@ int pm_use_graphs(pm_ctx *ctx, int enable) {
     return PM_OK;
 }
 
+int pm_inject_wait_timeout(pm_ctx *ctx, int which) {
+    if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
+    if (which != 0 && which != 1) return fail(ctx, PM_EINVAL, "which must be 0 (spectrum copy) or 1 (correction MMA)");
+    int *flag = which == 0 ? ctx->d_err : ctx->nn_err;
+    if (!flag)
+        return fail(ctx, PM_ESTATE, which == 0 ? "this context has no bounded copy wait (library FFT not in use)"
+                                               : "set the network parameters first");
+    DeviceGuard guard(ctx->device);
+    PM_CUDA(ctx, cudaMemsetAsync(flag, 1, sizeof(int), ctx->stream));  // any non-zero word: timed out
+    return PM_OK;
+}
+
 int64_t pm_checkpoint_floats(const pm_ctx *ctx, int32_t every) {
     if (!ctx || every < 0) return -1;
     return ck_slots(ctx, every) * 2 * state_floats(ctx);
