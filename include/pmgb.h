@@ -4,11 +4,11 @@
  * The library implements the hot path of the differentiable cosmological
  * particle-mesh method of pmwd (arXiv:2211.09958): a PM force evaluation per
  * time step inside growth-factor kick-drift-kick (KDK) integration (paper,
- * Summary: "particle-mesh (PM) simulation"), and the adjoint method that
- * integrates backward in time by reversing the trajectory instead of storing
- * it (Summary; Statement of Need: adjoint method, reverse time integration,
- * discretize-then-optimize).  The paper prints no equations; the operations
- * below are its prose written in the standard comoving PM form:
+ * Summary), and the adjoint method that integrates backward in time by
+ * reversing the trajectory instead of storing it (Summary; Statement of Need:
+ * adjoint method, reverse time integration, discretize-then-optimize).  The
+ * paper prints no equations; the operations below are its prose written in
+ * the standard comoving PM form:
  *
  *   units      box L [Mpc/h], H0 = 1, flat LCDM, E(a)^2 = Om a^-3 + 1 - Om
  *   lattice    q_i = i L / n_p + h / 2 (half a mesh cell h = L / n_m off the

@@ -1,10 +1,11 @@
 """Learned PM force correction, FP64 reference (test infrastructure only).
 
-The paper names "spatiotemporal optimization of the PM gravity solver" as
-ongoing work built on pmwd (Statement of Need) without describing it, so the
-network here is a design choice [reading]: a per-cell multilayer perceptron
-on the coarse CIC density mesh that predicts a force correction on the same
-mesh, added to the PM force meshes before the CIC read.
+The paper names a learned, space- and time-dependent optimisation of the PM
+gravity solver as ongoing work built on pmwd (Statement of Need) without
+describing it, so the network here is a design choice [reading]: a per-cell
+multilayer perceptron on the coarse CIC density mesh that predicts a force
+correction on the same mesh, added to the PM force meshes before the CIC
+read.
 
   features   asinh(rho(c + o) - 1) for the 27 offsets o in {-1, 0, 1}^3
              (periodic; rho = alpha sum W, so rho - 1 is the density

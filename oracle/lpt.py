@@ -1,9 +1,10 @@
 """Linear field and 2LPT initial conditions, and their adjoint (FP64, test
 infrastructure only).
 
-The paper constrains "the initial conditions of the Universe" together with
-the physical parameters (Statement of Need) and differentiates with respect to
-cosmological parameters (Summary).  It gives no formulas; readings:
+The paper treats the initial conditions of the cosmic density field as
+parameters to be inferred together with the physical parameters (Statement of
+Need) and differentiates with respect to cosmological parameters (Summary).
+It gives no formulas; readings:
 
 * delta_L(k) = omega(k) sqrt(P(|k|) / V_c), V_c = (L / n_p)^3, omega the
   unnormalised DFT of unit white noise on the n_p^3 lattice, delta_L(0) = 0

@@ -4,9 +4,10 @@
 Paper: pmwd is a cosmological particle-mesh (PM) simulation (Summary) whose
 gradients come from the adjoint method with reverse time integration
 (Summary; Statement of Need) and follow the same discrete trajectory as the
-forward integrator (Statement of Need, "discretize-then-optimize").  The
-paper prints no equations; the readings below are the standard comoving PM
-ones.                                                             [reading]
+forward integrator (Statement of Need: the adjoint of the discretised
+equations, not a discretised continuous adjoint).  The paper prints no
+equations; the readings below are the standard comoving PM ones.
+[reading]
 
 Geometry: box L, n_m^3 mesh with nodes at c h, h = L / n_m, periodic;
 n_p^3 particles on the lattice q = i L / n_p + h / 2, i.e. half a mesh cell
