@@ -62,3 +62,16 @@ def test_traffic_lookup_needs_the_current_sources(monkeypatch):
     assert bench._ncu_traffic("no_such_kernel", "pm512_mesh1024") is None
     monkeypatch.setattr(bench, "_source_digest", lambda: "changed")
     assert bench._ncu_traffic("paint_adj", "pm512_mesh1024") is None
+
+
+def test_workloads_of_the_bench():
+    from paper_2211_09958_gb300.configs import WORKLOADS
+    w = WORKLOADS[bench.DEFAULT_WORKLOAD]
+    assert (w.n_p, w.n_m, w.box, w.n_steps, w.n_batch) == (512, 1024, 1000.0, 100, 1)
+    assert w.n_m ** 3 * 4 > 129e6                      # every mesh field exceeds the 129 MB L2
+    small = WORKLOADS["pm32_mesh64"]
+    assert (small.n_p, small.n_m, small.n_steps) == (32, 64, 10)
+    batch = WORKLOADS["batch32_pm64_mesh128"]
+    assert (batch.n_batch, batch.n_p, batch.n_m, batch.n_steps) == (32, 64, 128, 20)
+    learned = WORKLOADS[bench.LEARNED_WORKLOAD]
+    assert (learned.n_p, learned.n_m, learned.n_steps) == (128, 128, 40)

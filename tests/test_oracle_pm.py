@@ -339,9 +339,10 @@ def test_tsc_linear_force_converges(ratio):
 
 # ------------------------------------------- sampled and reduced cases ----
 
-@pytest.mark.parametrize("n_p,n_m,box", [(16, 32, 64.0), (16, 16, 48.0), (12, 18, 40.0)])
-def test_density_at_sampled_cells_matches_the_full_mesh(n_p, n_m, box):
-    st = pm.Setup(n_p, n_m, box)
+@pytest.mark.parametrize("n_p,n_m,box,solver", [(16, 32, 64.0, 0), (16, 16, 48.0, 0), (12, 18, 40.0, 0),
+                                                (16, 32, 64.0, 8)])
+def test_density_at_sampled_cells_matches_the_full_mesh(n_p, n_m, box, solver):
+    st = pm.Setup(n_p, n_m, box, solver=solver)
     s = inputs.random_displacements(n_p, box, seed=31, scale=0.8).astype(np.float64)
     full = pm.density(s, st).ravel()
     cells = np.random.default_rng(3).integers(0, n_m ** 3, 40)
