@@ -364,3 +364,24 @@ def test_plane_wave_force_reduces_to_one_dimension(n_p, n_m, solver):
     assert scale > 0
     np.testing.assert_allclose(f[..., 0], np.broadcast_to(fx[:, None, None], f.shape[:3]), rtol=0, atol=1e-12 * scale)
     assert np.abs(f[..., 1:]).max() < 1e-12 * scale
+
+
+def test_four_point_stencil_is_the_gradient_symbol():
+    # The fused x round trip builds the adjoint's psi from one forward
+    # transform: the periodic stencil S f = [8 (f(x+h) - f(x-h)) - (f(x+2h) - f(x-2h))] / 12h
+    # has the Fourier symbol i D(k) of the gradient reading, so
+    # -i g sum_j D_j u_j(k) = -g FFT_x(S_x u_x + i (D_y u_y + D_z u_z)).
+    n, box = 64, 128.0
+    h = box / n
+    rng = np.random.default_rng(11)
+    ux, uy, uz = (rng.standard_normal(n) + 1j * rng.standard_normal(n) for _ in range(3))
+    k = 2 * np.pi / box * np.fft.fftfreq(n, 1.0 / n)
+    dx = pm.gradient_operator(k, h)
+    dy, dz = pm.gradient_operator(2 * np.pi / box * 5, h), pm.gradient_operator(2 * np.pi / box * -7, h)
+    stencil = (8 * (np.roll(ux, -1) - np.roll(ux, 1)) - (np.roll(ux, -2) - np.roll(ux, 2))) / (12 * h)
+    np.testing.assert_allclose(np.fft.fft(stencil), 1j * dx * np.fft.fft(ux), rtol=0, atol=1e-12 * np.abs(np.fft.fft(ux)).max())
+    g = rng.uniform(0.5, 2.0, n)                        # any real multiplier (Green's function, windows)
+    lhs = -1j * g * (dx * np.fft.fft(ux) + dy * np.fft.fft(uy) + dz * np.fft.fft(uz))
+    rhs = -g * np.fft.fft(stencil + 1j * (dy * uy + dz * uz))
+    np.testing.assert_allclose(rhs, lhs, rtol=0, atol=1e-12 * np.abs(lhs).max())
+    assert abs(pm.gradient_operator(np.pi / h, h)) < 1e-12   # the symbol vanishes at the Nyquist index
