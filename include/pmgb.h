@@ -331,7 +331,7 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  * launches (forward x pass, Green's function times gradient, inverse x
  * pass), 2 one fused kernel that takes each x line through all three
  * without writing the spectrum back in between, 3 the fused kernel for the
- * force and the three launches for the adjoint; default 2.
+ * force and the three launches for the adjoint; default 2 (3 for n_m >= 512).
  *
  * pm_autotune     times every candidate of each family in turn (the others
  *                 held at their current best) on this context's scratch

@@ -992,6 +992,7 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
         ctx->fg.tmaps = ctx->zmaps;
         ctx->fg.ztma = encode_z_inv_maps(ctx->spec, ctx->fg, ctx->zmaps) ? 1 : 0;
         ctx->tune[5] = ctx->fg.ztma ? 2 : 1;
+        ctx->tune[7] = ctx->P.n_m >= 512 ? 3 : 2;  // the fused adjoint spills on lines of 512+ points
     } else if (cudaMalloc(&ctx->mesh, sizeof(float) * (size_t)ctx->mesh_pad * B * kMeshFields) != cudaSuccess) {
         cudaGetLastError();
         fail(ctx, PM_ENOMEM, "cannot allocate the FFT meshes");
