@@ -44,6 +44,7 @@ class ParticleMesh:
             rc = self._lib.pm_create(ctypes.byref(self.cfg), ctypes.byref(self._ctx))
         if rc != _pmgb.PM_OK:
             raise PMError(f"pm_create: {_pmgb.ERRORS.get(rc, rc)}: {self._lib.pm_last_error(None).decode()}")
+        self._x_round_default = self.get_tuning()["x_round"]      # 2, or 3 on meshes of 512 and more
 
     # ------------------------------------------------------------ helpers --
     @property
@@ -255,9 +256,14 @@ class ParticleMesh:
         return dict(zip(self.TUNE_FAMILIES, (int(v) for v in t)))
 
     def set_tuning(self, paint=256, read=256, spectral=256, fft_z=256, fft_x=8, z_staging=None, z_fwd_staging=1,
-                   x_round=2):
+                   x_round=None):
+        """Fix the launch shapes; a family not named takes the context's
+        default (z_staging keeps its current value, x_round the mesh-size
+        default the context was created with)."""
         if z_staging is None:
             z_staging = self.get_tuning()["z_staging"]
+        if x_round is None:
+            x_round = self._x_round_default
         t = np.array([paint, read, spectral, fft_z, fft_x, z_staging, z_fwd_staging, x_round], np.int32)
         self._call("pm_set_tuning", t.ctypes.data_as(ctypes.c_void_p))
 
