@@ -49,6 +49,30 @@ def test_bbks_limits():
     assert np.all(np.diff(t) < 0)
 
 
+def test_bbks_series_and_asymptote():
+    # The BBKS fit (Bardeen, Bond, Kaiser & Szalay 1986, ApJ 304, 15, App. G):
+    # T(q) = ln(1 + 2.34 q)/(2.34 q) [1 + 3.89 q + (16.1 q)^2 + (5.46 q)^3 + (6.71 q)^4]^(-1/4),
+    # q = k / (Om h).  Expanded by hand: near q = 0 the slope is -(2.34/2 + 3.89/4) and the q^2
+    # coefficient 2.34^2/3 + (2.34/2)(3.89/4) - 16.1^2/4 + (5/32) 3.89^2; for q >> 1,
+    # T -> ln(1 + 2.34 q)/(2.34 q) / (6.71 q) * (1 - 5.46^3 / (4 * 6.71^4 q)).  Each coefficient
+    # enters one of these, so a wrong one, a wrong exponent or a wrong log argument fails.
+    om, h = 0.3, 0.7
+    q = np.linspace(1e-4, 2e-3, 60)
+    co = np.polynomial.polynomial.polyfit(q, C.bbks_transfer(q * om * h, om, h), 7)
+    assert abs(co[0] - 1.0) < 1e-12
+    assert abs(co[1] - (-(2.34 / 2 + 3.89 / 4))) < 1e-8
+    c2 = 2.34 ** 2 / 3 + (2.34 / 2) * (3.89 / 4) - 16.1 ** 2 / 4 + 5 / 32 * 3.89 ** 2
+    assert abs(co[2] - c2) < 1e-6 * abs(c2)
+    for qq in (1e5, 1e6):
+        x = 2.34 * qq
+        asym = np.log1p(x) / x / (6.71 * qq) * (1 - 5.46 ** 3 / (4 * 6.71 ** 4 * qq))
+        assert abs(C.bbks_transfer(qq * om * h, om, h) / asym - 1) < 1e-10
+    # k enters only through Gamma = Om h
+    k = np.logspace(-3, 1, 9)
+    np.testing.assert_allclose(C.bbks_transfer(k, 0.3, 0.7), C.bbks_transfer(k * 0.25 * 0.8 / 0.21, 0.25, 0.8),
+                               rtol=1e-13)
+
+
 @pytest.mark.parametrize("cosmo", [C.Cosmology(), C.Cosmology(0.25, 0.9, 0.7, 0.96)])
 def test_sigma8_normalisation_independent_quadrature(cosmo):
     amp = C.power_amplitude(cosmo)
