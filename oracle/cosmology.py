@@ -161,11 +161,16 @@ def bbks_transfer(k, om, h):
 
 
 def tophat_window(x):
+    """W(x) = 3 (sin x - x cos x) / x^3.  Below x = 0.1 the closed form loses
+    about eps / x^2 to cancellation, so there it takes the Taylor series
+    W = sum_m (-1)^m 6 (m + 1) x^(2m) / (2m + 3)!, through m = 4 (the next
+    term is below 1e-18)."""
     x = np.asarray(x, dtype=np.float64)
-    small = np.abs(x) < 1e-2
+    small = np.abs(x) < 0.1
     xs = np.where(small, 1.0, x)
     big = 3.0 * (np.sin(xs) - xs * np.cos(xs)) / xs ** 3
-    series = 1.0 - x * x / 10.0 + x ** 4 / 280.0
+    x2 = x * x
+    series = 1.0 + x2 * (-1.0 / 10.0 + x2 * (1.0 / 280.0 + x2 * (-1.0 / 15120.0 + x2 / 1330560.0)))
     return np.where(small, series, big)
 
 

@@ -288,7 +288,8 @@ def density_at(cells, s, setup, s_max):
     out = np.empty(len(cells))
     for j, c in enumerate(np.asarray(cells, dtype=np.int64)):
         cxyz = (c // (n_m * n_m), (c // n_m) % n_m, c % n_m)
-        ax = [(int(round((cxyz[d] - 0.5) / r)) + win) % n_p for d in range(3)]
+        # each site once, also when the window is wider than the lattice
+        ax = [np.unique((int(round((cxyz[d] - 0.5) / r)) + win) % n_p) for d in range(3)]
         ii = ((ax[0][:, None, None] * n_p + ax[1][None, :, None]) * n_p + ax[2][None, None, :]).ravel()
         x = lattice_sites(ii, n_p, setup.box, n_m) + s[ii]
         acc = 0.0

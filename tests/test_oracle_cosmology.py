@@ -87,9 +87,19 @@ def test_sigma8_normalisation_independent_quadrature(cosmo):
 
 
 def test_tophat_series_matches_closed_form():
-    x = np.array([5e-3, 9e-3, 1.1e-2, 0.5])
+    x = np.array([5e-3, 9e-3, 1.1e-2, 0.09, 0.11, 0.5])
     direct = 3 * (np.sin(x) - x * np.cos(x)) / x ** 3
     np.testing.assert_allclose(C.tophat_window(x), direct, rtol=1e-9)
+
+
+def test_tophat_window_to_double_precision():
+    # The closed form evaluated in 50-digit arithmetic, on both sides of the
+    # switch to the small-x series (where the closed form cancels in FP64).
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    x = np.array([1e-4, 3e-3, 9.9e-3, 1.01e-2, 0.099, 0.101, 0.3, 2.0, 7.5])
+    ref = np.array([float(3 * (mp.sin(mp.mpf(v)) - mp.mpf(v) * mp.cos(mp.mpf(v))) / mp.mpf(v) ** 3) for v in x])
+    np.testing.assert_allclose(C.tophat_window(x), ref, rtol=2e-14)
 
 
 @pytest.mark.parametrize("n_steps", [1, 7, 50])

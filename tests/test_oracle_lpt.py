@@ -78,6 +78,26 @@ def test_initial_momentum_is_growth_rate_times_displacement():
     assert d2 < 0 and abs(d2 / d1 ** 2 + 3 / 7) < 1e-3     # matter era
 
 
+def test_initial_momentum_is_the_time_derivative_of_the_displacement():
+    # p = a^3 E(a) ds/da with s(a) = D1(a) s1 + D2(a) s2: central differences
+    # of the 2LPT displacement in a_init, on the same noise, give p at both
+    # orders (g1 = a^3 E D1', g2 = a^3 E D2').
+    noise = np.random.default_rng(4).standard_normal((8, 8, 8))
+    a0, eps = 1.0 / 64, 1e-6
+    st = Setup(8, 16, 64.0, a_init=a0)
+    _, p = lpt.initial_conditions(noise, st)
+    s_up, _ = lpt.initial_conditions(noise, Setup(8, 16, 64.0, a_init=a0 + eps))
+    s_dn, _ = lpt.initial_conditions(noise, Setup(8, 16, 64.0, a_init=a0 - eps))
+    e = np.sqrt(st.cosmo.omega_m * a0 ** -3 + 1 - st.cosmo.omega_m)
+    p_fd = a0 ** 3 * e * (s_up - s_dn) / (2 * eps)
+    np.testing.assert_allclose(p_fd, p, rtol=0, atol=1e-7 * np.abs(p).max())
+    # the second order alone: its share of p is ~D1, so check it separately
+    s1, s2, _ = lpt.lpt_fields(lpt.linear_field(noise, st), st)
+    g2 = lpt_growth(st.cosmo, a0)[3]
+    g2_fd = a0 ** 3 * e * (lpt_growth(st.cosmo, a0 + eps)[1] - lpt_growth(st.cosmo, a0 - eps)[1]) / (2 * eps)
+    assert abs(g2 / g2_fd - 1) < 1e-7, (g2, g2_fd)
+
+
 def _ic_objective(noise, st, lam, mu):
     s, p = lpt.initial_conditions(noise, st)
     return np.sum(lam * s) + np.sum(mu * p)

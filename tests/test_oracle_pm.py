@@ -350,6 +350,44 @@ def test_density_at_sampled_cells_matches_the_full_mesh(n_p, n_m, box, solver):
     np.testing.assert_allclose(got, full[cells], rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("n_p,n_m,box", [(24, 24, 48.0), (12, 24, 48.0), (6, 6, 12.0)])
+def test_density_at_reaches_far_displaced_particles(n_p, n_m, box):
+    # One particle thrown several cells from its site (and, on the 6^3
+    # lattice, a window wider than the lattice): the cells its CIC corners
+    # land on must still see it.
+    st = pm.Setup(n_p, n_m, box)
+    h = st.cell
+    s = inputs.random_displacements(n_p, box, seed=5, scale=0.2).astype(np.float64)
+    i = (3 * n_p + 3) * n_p + 4
+    s[i] = [5.9 * h, -5.9 * h, 0.3 * h]                 # corners 6 and 7 cells from the site
+    cells = np.array([flat[0] for flat, _, _ in pm.cic_corners(pm.positions(s, st)[i][None], n_m, h)])
+    full = pm.density(s, st).ravel()
+    got = pm.density_at(cells, s, st, np.abs(s).max())
+    np.testing.assert_allclose(got, full[cells], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [8, 12])
+def test_every_spectral_multiplier_gives_a_real_field(n):
+    # irfftn returns a real field for any input, so a multiplier that breaks
+    # Hermitian symmetry would be silently projected.  On the rfft grid the
+    # symmetry M(-k) = conj M(k) constrains the n_z = 0 and n_z = n/2 planes:
+    # check it there for the force multipliers (every solver variant) and the
+    # 2LPT and linear-field multipliers.
+    from oracle import lpt
+    box = 3.0 * n
+    mults = []
+    for solver in (0, 1, 2, 8, 3):
+        mults += pm.gradient_green_multipliers(n, box, 0.3, solver)
+    s1, phi, s2 = lpt.lpt_multipliers(n, box)
+    mults += s1 + phi + s2 + [lpt.linear_multiplier(Setup(n, n, box))]
+    neg = (-np.arange(n)) % n
+    for m in mults:
+        m = np.broadcast_to(m, (n, n, n // 2 + 1))
+        for z in (0, n // 2):
+            plane = m[:, :, z]
+            np.testing.assert_array_equal(plane[np.ix_(neg, neg)], np.conj(plane))
+
+
 @pytest.mark.parametrize("n_p,n_m,solver", [(16, 32, 0), (16, 16, 0), (16, 32, 1), (16, 32, 2)])
 def test_plane_wave_force_reduces_to_one_dimension(n_p, n_m, solver):
     box = 64.0
