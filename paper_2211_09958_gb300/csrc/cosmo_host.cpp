@@ -162,8 +162,14 @@ double bbks_transfer(double k, double om, double h) {
 }
 
 namespace {
+// 3 (sin x - x cos x) / x^3.  The closed form cancels below x ~ 0.1 (relative
+// error ~ eps / x^2), so there it is summed as its Taylor series
+// sum_m (-1)^m 6 (m + 1) x^(2m) / (2m + 3)!, m = 0..4.
 double tophat(double x) {
-    if (std::fabs(x) < 1e-2) return 1.0 - x * x / 10.0 + x * x * x * x / 280.0;
+    if (std::fabs(x) < 0.1) {
+        const double y = x * x;
+        return 1.0 - y / 10.0 + y * y / 280.0 - y * y * y / 15120.0 + y * y * y * y / 1330560.0;
+    }
     return 3.0 * (std::sin(x) - x * std::cos(x)) / (x * x * x);
 }
 }  // namespace
