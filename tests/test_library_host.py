@@ -38,8 +38,9 @@ def test_every_declared_symbol_is_exported(lib):
         assert n in _pmgb._SIGNATURES, n
 
 
-@pytest.mark.parametrize("field,value", [("n_p", 3), ("n_m", 2), ("n_batch", 0), ("n_steps", 0), ("box", -1.0),
-                                         ("a_init", 2.0)])
+@pytest.mark.parametrize("field,value", [("n_p", 3), ("n_p", 15), ("n_p", 8192), ("n_m", 2), ("n_m", 8194),
+                                         ("n_batch", 0), ("n_steps", 0), ("box", -1.0), ("box", float("nan")),
+                                         ("a_init", 2.0), ("a_final", 0.01), ("h", 0.0), ("solver", 16)])
 def test_create_rejects_bad_config(lib, field, value):
     cfg = _pmgb.make_config(8, 16, 32.0, 0.3, 0.8, 4)
     setattr(cfg, field, value)
@@ -47,6 +48,24 @@ def test_create_rejects_bad_config(lib, field, value):
     rc = lib.pm_create(ctypes.byref(cfg), ctypes.byref(out))
     assert rc == -1 and not out.value
     assert lib.pm_last_error(None)
+
+
+def test_create_rejects_too_many_particles_before_allocating(lib):
+    # 4096^3 particles x 3 floats x 6 runs exceeds the 2^40 element limit
+    cfg = _pmgb.make_config(4096, 64, 1000.0, [0.3] * 6, [0.8] * 6, 4)
+    out = ctypes.c_void_p()
+    assert lib.pm_create(ctypes.byref(cfg), ctypes.byref(out)) == _pmgb.PM_ERANGE and not out.value
+    assert b"too many particles" in lib.pm_last_error(None)
+
+
+def test_null_arguments_are_rejected(lib):
+    out = ctypes.c_void_p()
+    assert lib.pm_create(None, ctypes.byref(out)) == _pmgb.PM_EINVAL and not out.value
+    cfg = _pmgb.make_config(8, 16, 32.0, 0.3, 0.8, 4)
+    assert lib.pm_create(ctypes.byref(cfg), None) == _pmgb.PM_EINVAL
+    assert lib.pm_destroy(None) == _pmgb.PM_OK                   # destroying nothing is harmless
+    assert lib.pm_set_tuning(None, None) == _pmgb.PM_EINVAL
+    assert lib.pm_set_checkpoints(None, 1, None) == _pmgb.PM_EINVAL
 
 
 def test_create_rejects_bad_cosmology(lib):
