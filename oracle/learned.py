@@ -23,8 +23,11 @@ nearest even) before each product; products accumulate in FP64 here.  In the
 backward pass the activation cotangents and the per-cell output cotangent
 are rounded to bfloat16 before the weight-gradient products.
 
-Parity status: pinned by central finite differences of the unrounded FP64
-loss (tests/test_oracle_learned.py).
+Parity status: the arithmetic (forward, loss gradient, the correction's
+VJPs, the corrected adjoint) is pinned by central finite differences of the
+unrounded FP64 maps, and the bf16 rounding by its ties-to-even definition
+(tests/test_oracle_learned.py).  Parity unpinned: the architecture above
+(features, sizes, output scale), a design choice the paper does not fix.
 """
 
 import itertools
