@@ -152,7 +152,14 @@ int pm_init_lpt_adjoint(pm_ctx *ctx, const float *noise, uint64_t seed,
 int pm_force(pm_ctx *ctx, const float *s, float *f);
 
 /* kdk_step -- one KDK step n (0 <= n < n_steps) in place:
- * (s_n, p_n, f = F(s_n)) -> (s_{n+1}, p_{n+1}, F(s_{n+1})). */
+ * (s_n, p_n, f = F(s_n)) -> (s_{n+1}, p_{n+1}, F(s_{n+1})):
+ * p += K_a F(s_n), s += Dr p, p += K_b F(s_{n+1}), the growth-matched
+ * kick and drift factors of pm_host_coefficients.  This is the discrete time
+ * step whose trajectory the adjoint differentiates and reverses (paper,
+ * Statement of Need: gradients along the same discrete trajectory as the
+ * forward integrator; Summary: reverse time integration).
+ *   s, p, f  device [n_batch][n_p^3][3], read and overwritten.
+ * Returns PM_EINVAL for a step outside 0 .. n_steps - 1 or a NULL array. */
 int pm_kdk_step(pm_ctx *ctx, int32_t step, float *s, float *p, float *f);
 
 /* integrate -- steps [step_begin, step_end) in place: (s, p) at
@@ -198,11 +205,19 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end,
 int64_t pm_checkpoint_floats(const pm_ctx *ctx, int32_t every);
 int pm_set_checkpoints(pm_ctx *ctx, int32_t every, float *ckpt);
 
-/* CIC density contrast alpha sum W - 1 of the particles at s.
- *   delta  device [n_batch][n_m^3] output. */
+/* pm_density -- CIC density contrast alpha sum_i W(x_i - c) - 1 of the
+ * particles at s, the mesh the PM force starts from (paper, Summary: a
+ * particle-mesh simulation) and the field that density losses and the power
+ * spectrum (paper, Statement of Need: fields and summary statistics as
+ * outputs) are computed on.  W is the CIC (or, with solver flag 8, TSC)
+ * assignment; alpha = (n_m / n_p)^3.
+ *   s      device [n_batch][n_p^3][3] input
+ *   delta  device [n_batch][n_m^3] output (x slowest, z fastest). */
 int pm_density(pm_ctx *ctx, const float *s, float *delta);
 
-/* Adjoint of pm_density: ds = sum_c ddelta(c) d delta(c)/ds.
+/* Adjoint of pm_density: ds = sum_c ddelta(c) d delta(c)/ds, the first step
+ * of the adjoint of any loss on the final density (paper, Summary: gradients
+ * by the adjoint method).  Uses the one-sided CIC weight slopes -1/h, +1/h.
  *   ddelta device [n_batch][n_m^3] input; ds [n_batch][n_p^3][3] output. */
 int pm_density_adjoint(pm_ctx *ctx, const float *s, const float *ddelta, float *ds);
 
@@ -222,8 +237,11 @@ int pm_mse_loss(pm_ctx *ctx, const float *s, const float *target, double *loss, 
  * this is an interface convenience.
  *
  * Needs no context.  Computes the same loss and adjoint seed as
- * pm_mse_loss for the geometry (n_p, n_m, n_batch, box) on the given CUDA
- * stream (void* cudaStream_t, NULL = legacy default stream), asynchronously.
+ * pm_mse_loss of a context with cloud-in-cell assignment (this entry point
+ * has no solver flags: it never paints with TSC) for the geometry (n_p, n_m,
+ * n_batch, box) on the given CUDA stream (void* cudaStream_t, NULL = legacy
+ * default stream), asynchronously.  n_p and n_m follow pm_create's rules
+ * (even, n_p 2..4096, n_m 4..4096).
  *   s       device [n_batch][n_p^3][3] displacements
  *   target  device [n_batch][n_m^3]
  *   loss    device [n_batch] doubles (8-byte aligned) output
@@ -237,7 +255,10 @@ int pm_mse_loss(pm_ctx *ctx, const float *s, const float *target, double *loss, 
  * host threads) race on it and give wrong results.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress, once per
  * device, with that device current); make that first call before any stream
- * capture.  Returns PM_OK, PM_EINVAL (bad size, NULL or misaligned pointer),
+ * capture.  The looked-up address is cached for the life of the process: a
+ * cudaDeviceReset makes it stale, so do not call this entry point on a
+ * device after resetting it.
+ * Returns PM_OK, PM_EINVAL (bad size, NULL or misaligned pointer),
  * PM_ERANGE or PM_ECUDA; there is no error message for this entry point. */
 int pm_mse_loss_noalloc(int32_t n_p, int32_t n_m, int32_t n_batch, double box, const float *s,
                         const float *target, double *loss, float *dlds, void *stream);

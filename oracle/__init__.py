@@ -31,7 +31,7 @@ pm         CIC mass assignment / interpolation, spectral Poisson force,
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute-force definitions, finite differences,
 invariants or, for the Philox4x32-10 round function, the generator's
-published known-answer vectors (bit for bit).  ``tests/oracle_mutants.py``
+published known-answer vectors (bit for bit).  ``tests/test_oracle_mutants.py``
 plants plausible mistakes one at a time and checks that each fails a pin.
 Parity unpinned: the learned correction's architecture (features, layer
 sizes, output scale), which is a design choice, not part of the method;

@@ -1,5 +1,6 @@
 // pm_mse_loss_noalloc: the density-MSE loss and its adjoint seed (the work
-// of pm_mse_loss) for callers that cannot allocate device memory.
+// of pm_mse_loss with cloud-in-cell assignment) for callers that cannot
+// allocate device memory.
 //
 // Some callers cannot call cudaMalloc: code whose device memory is all
 // reserved up front by another allocator (a framework's caching pool, a
@@ -31,6 +32,9 @@ float *g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once
 // per device (the host-side symbol is only a stand-in, never a device address).
+// The cached address belongs to the device's current context: after a
+// cudaDeviceReset in this process it is stale, so callers must not reset a
+// device and then call this entry point again.
 cudaError_t scratch_address(float **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -57,7 +61,10 @@ __global__ void k_loss_out(const double *acc, double *loss, int nb, double inv_c
 extern "C" int pm_mse_loss_noalloc(int32_t n_p, int32_t n_m, int32_t n_batch, double box, const float *s,
                                    const float *target, double *loss, float *dlds, void *stream) {
     using namespace pmgb;
-    if (n_p < 2 || n_p % 2 || n_m < 4 || n_m % 2 || n_batch < 1 || !(box > 0)) return PM_EINVAL;
+    // the same size rules as pm_create (n_p, n_m even and at most 4096), checked
+    // before n_p^3 is formed so that it cannot overflow
+    if (n_p < 2 || n_p % 2 || n_p > 4096 || n_m < 4 || n_m % 2 || n_m > 4096 || n_batch < 1 || !(box > 0))
+        return PM_EINVAL;
     if (!s || !target || !loss) return PM_EINVAL;
     if ((uintptr_t)s % 4 || (uintptr_t)target % 4 || (uintptr_t)loss % 8 || (dlds && (uintptr_t)dlds % 4))
         return PM_EINVAL;

@@ -7,11 +7,14 @@ one, and properties that hold at any size:
   * density: 96 sampled cells of the 2LPT state, each summed in FP64 over
     the lattice sites that can reach it (oracle.pm.density_at); bound
     1e-5 of max(alpha, 1 + delta) per cell, as in the small-size test;
-  * force on a plane wave along x (uniform in y and z): the exact PM force
-    reduces to a 1D problem along x (oracle.pm.force_uniform_yz, pinned
-    against the 3D oracle on the CPU).  F_x of every particle matches it
-    within 2e-5 of max |F| (the small-size force bound); F_y, F_z vanish
-    to 1e-5 of it;
+  * force on a plane wave along x, y or z (uniform across the other two
+    axes): the exact PM force reduces to a 1D problem along the wave
+    (oracle.pm.force_uniform_yz, pinned against the 3D oracle on the CPU;
+    the cubic symmetry of box, lattice and mesh makes it the same function
+    for every axis).  The force component along the wave matches it within
+    2e-5 of max |F| (the small-size force bound) for every particle; the
+    other two vanish to 1e-5 of it.  Each orientation sends non-zero modes
+    through the 1024-point transforms of its own axis;
   * momentum conservation on the 2LPT state: with the same assignment for
     paint and read and an odd gradient multiplier (zero at k = 0 and at the
     Nyquist indices), sum_i F_i = 0 exactly; FP32 rounding leaves
@@ -69,24 +72,34 @@ def test_full_size_density_on_sampled_cells(full):
     assert err.max() < 1e-5, err.max()
 
 
-def test_full_size_plane_wave_force(full):
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_full_size_plane_wave_force(full, axis):
+    # a plane wave along x, y or z: the state is uniform across the other two
+    # axes, so each orientation puts non-zero modes through the 1024-point
+    # transforms of its own axis (the same 1D reduction holds by the cubic
+    # symmetry of box, lattice and mesh)
     pm, st, _, _ = full
     n_p, h_p = W.n_p, W.box / W.n_p
     i = np.arange(n_p)
     sx = (0.4 * h_p * np.sin(2 * np.pi * 8 * (i + 0.25) / n_p) + 0.1 * h_p * np.cos(2 * np.pi * 21 * i / n_p))
     sx = sx.astype(np.float32)
+    shape = [1, 1, 1]
+    shape[axis] = n_p
     s = torch.zeros((1, n_p, n_p, n_p, 3), dtype=torch.float32, device=pm.device)
-    s[..., 0] = torch.from_numpy(sx).to(pm.device)[:, None, None]
-    f = pm.pm_force(s.reshape(1, -1, 3)).reshape(n_p, n_p * n_p, 3)
+    s[0, ..., axis] = torch.from_numpy(sx).to(pm.device).reshape(shape)
+    f = pm.pm_force(s.reshape(1, -1, 3)).reshape(n_p, n_p, n_p, 3)
+    f = f.movedim(axis, 0).reshape(n_p, n_p * n_p, 3)
     ref = opm.force_uniform_yz(sx.astype(np.float64), st)
     scale = np.abs(ref).max()
-    fx = f[..., 0]
-    spread = (fx.max(dim=1).values - fx.min(dim=1).values).max().item()
-    assert spread < 2e-5 * scale, spread / scale                        # F_x depends on x alone
-    assert f[..., 1:].abs().max().item() < 1e-5 * scale
-    plane = fx[:, 0].double().cpu().numpy()
-    print(f"plane wave: spread {spread / scale:.3e}, |F_yz| {f[..., 1:].abs().max().item() / scale:.3e}, "
-          f"|F_x - ref| {np.abs(plane - ref).max() / scale:.3e} of max |F|")
+    fa = f[..., axis]
+    others = [j for j in range(3) if j != axis]
+    spread = (fa.max(dim=1).values - fa.min(dim=1).values).max().item()
+    assert spread < 2e-5 * scale, spread / scale                        # F_axis depends on that axis alone
+    assert f[..., others].abs().max().item() < 1e-5 * scale
+    plane = fa[:, 0].double().cpu().numpy()
+    print(f"plane wave along axis {axis}: spread {spread / scale:.3e}, "
+          f"|F_other| {f[..., others].abs().max().item() / scale:.3e}, "
+          f"|F - ref| {np.abs(plane - ref).max() / scale:.3e} of max |F|")
     assert np.abs(plane - ref).max() < 2e-5 * scale, np.abs(plane - ref).max() / scale
 
 

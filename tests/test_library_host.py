@@ -111,3 +111,20 @@ def test_unknown_solver_flag_is_rejected(lib):
     out = ctypes.c_void_p()
     assert lib.pm_create(ctypes.byref(cfg), ctypes.byref(out)) == -1
     assert b"solver" in lib.pm_last_error(None)
+
+
+def test_noalloc_rejects_bad_arguments_before_any_device_work(lib):
+    # every rejection of the allocation-free loss returns before the entry
+    # point touches a device, so fake (never dereferenced) pointers serve
+    s, t = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000)
+    loss_ok, loss_odd = ctypes.c_void_p(0x30000), ctypes.c_void_p(0x30004)
+    f = lib.pm_mse_loss_noalloc
+    assert f(8, 16, 65, 32.0, s, t, loss_ok, None, None) == -5          # more runs than loss slots
+    assert f(64, 256, 1, 64.0, s, t, loss_ok, None, None) == -5         # 256^3 cells exceed the scratch
+    assert f(8, 16, 1, 32.0, s, t, loss_odd, None, None) == -1          # loss not 8-byte aligned
+    assert f(8, 16, 1, 32.0, s, None, loss_ok, None, None) == -1        # NULL target
+    assert f(8, 16, 1, 32.0, None, t, loss_ok, None, None) == -1        # NULL displacements
+    assert f(8, 16, 1, 32.0, s, t, None, None, None) == -1              # NULL loss
+    assert f(1 << 21, 16, 1, 32.0, s, t, loss_ok, None, None) == -1     # n_p beyond pm_create's 4096
+    assert f(7, 16, 1, 32.0, s, t, loss_ok, None, None) == -1           # odd n_p
+    assert f(8, 16, 1, 0.0, s, t, loss_ok, None, None) == -1            # box <= 0

@@ -1,4 +1,5 @@
-"""Mutation check of the oracle's pins (run by hand; not collected by pytest).
+"""Mutation check of the oracle's pins (slow: collected by pytest, run only
+with ``--runslow``; about 30 s per mutant, 30 minutes in all).
 
 Each entry plants one plausible mistake in the oracle -- a dropped term, a
 wrong sign, index, exponent or prefactor -- in a temporary copy of the
@@ -7,8 +8,8 @@ there and reports whether at least one of them failed.  A mutant that
 survives marks a piece of the oracle that nothing pins.  The working tree is
 never modified.
 
-    python tests/oracle_mutants.py            # every mutant (about 30 s each)
-    python tests/oracle_mutants.py "D sign"   # named ones
+    python -m pytest tests/test_oracle_mutants.py --runslow -q   # every mutant
+    python tests/test_oracle_mutants.py "D sign"                 # named ones, by hand
 
 Expected survivor: "out scale", the output scale of the learned correction,
 which is part of the network's design rather than of the method.
@@ -19,6 +20,8 @@ import shutil
 import subprocess
 import sys
 import tempfile
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -100,30 +103,35 @@ def _copy_repo(dst):
     shutil.copytree(ROOT, dst, ignore=skip)
 
 
+def _pins_fail(repo, path, old, new):
+    """Plant one mistake in the copy at ``repo``, run the pin tests there and
+    restore the file; returns (True if a pin failed, the last output line),
+    or (None, message) when the original text is not found exactly once."""
+    target = os.path.join(repo, path)
+    text = open(target).read()
+    if text.count(old) != 1:
+        return None, f"the original text occurs {text.count(old)} times"
+    xdist = ["-n", "8"] if _have_xdist() else []
+    open(target, "w").write(text.replace(old, new))
+    try:
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *xdist,
+                            *PIN_TESTS], cwd=repo, capture_output=True, text=True, timeout=1800)
+    finally:
+        open(target, "w").write(text)
+    return r.returncode != 0, (r.stdout.strip().splitlines() or [""])[-1]
+
+
 def run(names=()):
     survivors = []
     with tempfile.TemporaryDirectory() as tmp:
         repo = os.path.join(tmp, "repo")
         _copy_repo(repo)
-        xdist = ["-n", "8"] if _have_xdist() else []
         for path, old, new, label in MUTANTS:
             if names and label not in names:
                 continue
-            target = os.path.join(repo, path)
-            text = open(target).read()
-            if text.count(old) != 1:
-                print(f"stale     {label}: the original text occurs {text.count(old)} times")
-                survivors.append(label)
-                continue
-            open(target, "w").write(text.replace(old, new))
-            try:
-                r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *xdist,
-                                    *PIN_TESTS], cwd=repo, capture_output=True, text=True, timeout=1800)
-            finally:
-                open(target, "w").write(text)
-            tail = (r.stdout.strip().splitlines() or [""])[-1]
-            print(f"{'killed   ' if r.returncode else 'SURVIVED '} {label}: {tail}", flush=True)
-            if r.returncode == 0:
+            killed, tail = _pins_fail(repo, path, old, new)
+            print(f"{'killed   ' if killed else 'SURVIVED '} {label}: {tail}", flush=True)
+            if not killed:
                 survivors.append(label)
     unexpected = sorted(set(survivors) - EXPECTED_SURVIVORS)
     print("survivors:", survivors, "unexpected:", unexpected)
@@ -136,6 +144,23 @@ def _have_xdist():
         return True
     except ImportError:
         return False
+
+
+@pytest.fixture(scope="module")
+def repo_copy(tmp_path_factory):
+    repo = str(tmp_path_factory.mktemp("mutants") / "repo")
+    _copy_repo(repo)
+    return repo
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("path,old,new,label", MUTANTS, ids=[m[3] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(repo_copy, path, old, new, label):
+    killed, tail = _pins_fail(repo_copy, path, old, new)
+    assert killed is not None, tail
+    if label in EXPECTED_SURVIVORS:
+        pytest.skip(f"{label} is part of the network's design, which nothing in the method fixes")
+    assert killed, f"{label} survived: {tail}"
 
 
 if __name__ == "__main__":

@@ -2,8 +2,9 @@
 callers that cannot call cudaMalloc (memory fully reserved by another
 allocator, or loops that cannot take cudaMalloc's device-wide
 synchronisation).  It is called through the C ABI and must agree with the
-existing pm_mse_loss on two calls in a row (the second with different
-inputs, so leftovers of the first call in the shared scratch would show).
+existing pm_mse_loss on two calls in a row (the first larger than the
+second, with different inputs, so leftovers of the first call in the shared
+scratch would show), and on the two shapes that fill the scratch exactly.
 Kept in a file that pytest collects last."""
 
 import ctypes
@@ -30,20 +31,34 @@ def _noalloc(lib, n_p, n_m, box, s, target, want_grad=True):
     return loss.cpu().numpy(), dlds
 
 
-def test_noalloc_matches_pm_mse_loss_twice():
+def _compare(lib, n_p, n_m, box, nb, seed):
     from paper_2211_09958_gb300.pm import ParticleMesh
-    lib = _pmgb.load()
-    n_p, n_m, box = 16, 32, 64.0
-    pm = ParticleMesh(n_p, n_m, box, 0.3, 0.8, 2)
-    for call in range(2):
-        s = torch.from_numpy(inputs.random_displacements(n_p, box, seed=40 + call, scale=0.7 + 0.3 * call))[None].cuda()
-        target = torch.from_numpy(inputs.target_field(n_m, 50 + call))[None].cuda()
-        ref_loss, ref_g = pm.mse_loss(s, target)
-        loss, g = _noalloc(lib, n_p, n_m, box, s, target)
-        assert abs(loss[0] - ref_loss[0]) <= 1e-5 * abs(ref_loss[0]), (call, loss, ref_loss)
-        scale = torch.max(torch.abs(ref_g)).item()
-        assert torch.max(torch.abs(g - ref_g)).item() <= 1e-4 * scale, call
+    s = torch.from_numpy(np.stack([inputs.random_displacements(n_p, box, seed=seed + b, scale=0.7)
+                                   for b in range(nb)])).cuda()
+    target = torch.from_numpy(np.stack([inputs.target_field(n_m, seed + 100 + b) for b in range(nb)])).cuda()
+    pm = ParticleMesh(n_p, n_m, box, [0.3] * nb, [0.8] * nb, 2)
+    ref_loss, ref_g = pm.mse_loss(s, target)
     pm.close()
+    loss, g = _noalloc(lib, n_p, n_m, box, s, target)
+    np.testing.assert_allclose(loss, ref_loss, rtol=1e-5)
+    scale = torch.max(torch.abs(ref_g)).item()
+    assert torch.max(torch.abs(g - ref_g)).item() <= 1e-4 * scale
+
+
+def test_noalloc_matches_pm_mse_loss_twice():
+    # a large first call (2 runs of 64^3 cells) leaves the shared scratch full
+    # of its density; the smaller second call must clear what it reads
+    lib = _pmgb.load()
+    _compare(lib, 32, 64, 128.0, 2, seed=40)
+    _compare(lib, 16, 32, 64.0, 1, seed=41)
+
+
+def test_noalloc_fills_the_scratch_exactly():
+    # the two shapes that use all 2^21 cells: one 128^3 mesh, and 64 runs of
+    # 32^3 (where the per-run loss sums follow the mesh region)
+    lib = _pmgb.load()
+    _compare(lib, 64, 128, 128.0, 1, seed=80)
+    _compare(lib, 8, 32, 32.0, 64, seed=90)
 
 
 def test_noalloc_batched_and_limits():
