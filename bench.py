@@ -131,6 +131,8 @@ def algorithmic_bytes(kind, npart, ncell, nmodes):
         "pre_kick_drift": 60 * npart,
         "spectral_force": (8 + 24) * nmodes,
         "spectral_adj": (32 + 32) * nmodes,
+        "grad_stencil_1": (4 + 16) * ncell,                  # phi in; (F, 0) float4 out
+        "grad_stencil_2": (8 + 16) * ncell,                  # (phi, psi) in; (F, psi) out
     }
     # own FFT passes: kind "fft_<axis>_<dir>_<fields>"
     if kind.startswith("fft_"):
@@ -139,9 +141,11 @@ def algorithmic_bytes(kind, npart, ncell, nmodes):
         if axis == "z" and direction == "fwd":
             return nf * (4 * ncell + 8 * nmodes)          # real fields in, half spectra out
         if axis == "z":
-            return nf * 8 * nmodes + (4 if nf == 1 else 16) * ncell   # spectra in, real mesh out
+            return nf * 8 * nmodes + (16 if nf >= 3 else 4 * nf) * ncell   # spectra in, real mesh out
         if direction == "round":                          # fused x pass: density in, 3 fields out; 4 in, 4 out
             return (8 + 24) * nmodes if nf == 1 else 64 * nmodes
+        if direction == "pot":                            # potential x pass: 1 in, 1 out; 4 in, 2 out
+            return 16 * nmodes if nf == 1 else 48 * nmodes
         return nf * 16 * nmodes                             # pencil pass: read + write
     return per.get(kind)
 

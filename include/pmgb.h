@@ -353,6 +353,15 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  * pass), 2 one fused kernel that takes each x line through all three
  * without writing the spectrum back in between, 3 the fused kernel for the
  * force and the three launches for the adjoint; default 2 (3 for n_m >= 512).
+ * [8] is the force pipeline (own transform, 4-point difference gradient):
+ * 1 the three force components (and the adjoint's psi) as inverse
+ * transforms of i D_j g delta, the form [7] chooses among; 2 one inverse
+ * transform of the potential phi = IFFT(g delta) (and psi), then
+ * F_j = S_j phi on the real mesh, S_j the periodic 4-point difference
+ * [8 (phi(c + e_j) - phi(c - e_j)) - (phi(c + 2 e_j) - phi(c - 2 e_j))] / 12h,
+ * whose Fourier symbol is i D_j: the same linear map with two fewer inverse
+ * transforms per evaluation; default 2 (1 with the spectral-gradient flag,
+ * which has no stencil form).
  *
  * pm_autotune     times every candidate of each family in turn (the others
  *                 held at their current best) on this context's scratch
@@ -364,8 +373,9 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  *                 above (0 where not timed).  Synchronises the stream.
  * pm_set_tuning   set all of them explicitly (PM_EINVAL for other values)
  * pm_get_tuning   read them (host int[PM_TUNE_KINDS])
- * Results do not depend on the choice beyond the order of FP32 atomics. */
-#define PM_TUNE_KINDS 8
+ * Results do not depend on the choice beyond the order of FP32 atomics and,
+ * for [7] and [8], the FP32 rounding order of the transforms. */
+#define PM_TUNE_KINDS 9
 int pm_autotune(pm_ctx *ctx, const float *s, float *ms);
 int pm_set_tuning(pm_ctx *ctx, const int *threads);
 int pm_get_tuning(pm_ctx *ctx, int *threads);

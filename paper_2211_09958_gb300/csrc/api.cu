@@ -51,6 +51,7 @@ struct pm_ctx {
     bool own = false;
     FftGeom fg{};
     float *r1 = nullptr, *r4 = nullptr;
+    float *rpot = nullptr;   // [run][n^3][2]: potential phi (and adjoint psi) before the gradient stencil
     float2 *spec = nullptr, *tw = nullptr;
     ZInvMap zmaps[3] = {};   // TMA descriptors of the blocked spectrum (z inverse)
     int *d_err = nullptr;    // device error flag (bounded TMA waits)
@@ -82,7 +83,8 @@ struct pm_ctx {
     float *ck_buf = nullptr;
     // launch shapes of the tunable kernel families: block sizes of paint,
     // read, spectral force/adjoint, z-pass FFT (n >= 256); x-pass pencil width
-    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8, 2, 1, 2};
+    // shape; z-inverse and z-forward staging; x round trip; force pipeline
+    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8, 2, 1, 2, 2};
     // learned force correction (own-FFT meshes only)
     bool nn_on = false;
     void *nn_packed = nullptr;
@@ -295,6 +297,15 @@ Spec mesh_spec(pm_ctx *ctx) {
 // round trip: x_round tuning 2 = both, 3 = the force only.
 bool x_fused(const pm_ctx *ctx, bool adj) { return ctx->tune[7] == 2 || (ctx->tune[7] == 3 && !adj); }
 
+// Whether force evaluations take the potential pipeline (tuning family 8 =
+// 2): one inverse transform of phi = IFFT(g delta) (and psi for the adjoint)
+// and the 4-point difference F_j = S_j phi on the real mesh, instead of three
+// inverse transforms of i D_j g delta.  The two are the same linear map; the
+// stencil form exists only for the 4-point difference gradient.
+bool pot_pipeline(const pm_ctx *ctx) {
+    return ctx->own && ctx->tune[8] == 2 && !(ctx->P.solver & PM_SOLVER_SPECTRAL_GRADIENT);
+}
+
 // Multipliers of the fused x round trip: the spectral kernels' tables.
 XRoundArgs xround_args(pm_ctx *ctx) {
     return XRoundArgs{(float)(2.0 * M_PI / ctx->P.box), ctx->d_grad, ctx->d_dec, ctx->d_pref,
@@ -374,7 +385,8 @@ const char *own_kind(int pass, int nf) {
     static const char *names[6][5] = {
         {"", "fft_z_fwd_1", "", "", "fft_z_fwd_4"}, {"", "fft_y_fwd_1", "", "", "fft_y_fwd_4"},
         {"", "fft_x_fwd_1", "", "", "fft_x_fwd_4"}, {"", "fft_x_inv_1", "", "fft_x_inv_3", "fft_x_inv_4"},
-        {"", "fft_y_inv_1", "", "fft_y_inv_3", "fft_y_inv_4"}, {"", "fft_z_inv_1", "", "fft_z_inv_3", "fft_z_inv_4"}};
+        {"", "fft_y_inv_1", "fft_y_inv_2", "fft_y_inv_3", "fft_y_inv_4"},
+        {"", "fft_z_inv_1", "fft_z_inv_2", "fft_z_inv_3", "fft_z_inv_4"}};
     return names[pass][nf];
 }
 
@@ -415,7 +427,22 @@ int force_meshes(pm_ctx *ctx, const float *s, const float *mu, double a = -1.0, 
         PM_MEMSET(ctx, cudaMemsetAsync(real, 0, sizeof(float) * n3 * nf * ctx->P.n_batch, ctx->stream));
         PM_LAUNCH(ctx, paint_kind(mode), launch_paint(mode, pa, ctx->stream));
         const int go = adj ? 4 : 3;
-        if (x_fused(ctx, adj)) {  // z and y forward, fused x round trip, y and z inverse
+        if (pot_pipeline(ctx)) {
+            // z and y forward; x round trip to phi (and psi); y and z inverse of
+            // those one or two fields; F = S phi on the real mesh into r4
+            const int np = adj ? 2 : 1;
+            PM_LAUNCH(ctx, own_kind(0, nf), launch_fft_z_fwd(nf, real, ctx->spec, ctx->fg, ctx->stream));
+            PM_LAUNCH(ctx, own_kind(1, nf), launch_fft_pencils(1, false, ctx->spec, 0, nf, ctx->fg, ctx->stream));
+            PM_LAUNCH(ctx, (adj ? "fft_x_pot_4" : "fft_x_pot_1"),
+                      launch_fft_xpot(adj, ctx->spec, ctx->fg, xround_args(ctx), ctx->stream));
+            // the correction's adjoint reads the painted (rho, mu) still in r4
+            if (adj && ctx->nn_on && a > 0.0) PM_TRY(correction_adjoint(ctx, a, kick_step, kick_sel));
+            PM_LAUNCH(ctx, own_kind(4, np), launch_fft_pencils(1, true, ctx->spec, 0, np, ctx->fg, ctx->stream));
+            PM_LAUNCH(ctx, own_kind(5, np), launch_fft_z_inv(np, ctx->spec, ctx->rpot, ctx->fg, ctx->stream));
+            PM_LAUNCH(ctx, (adj ? "grad_stencil_2" : "grad_stencil_1"),
+                      launch_grad_stencil(ctx->rpot, np, reinterpret_cast<float4 *>(ctx->r4), ctx->P.n_m,
+                                          ctx->P.n_batch, xround_args(ctx).inv12h, ctx->stream));
+        } else if (x_fused(ctx, adj)) {  // z and y forward, fused x round trip, y and z inverse
             PM_LAUNCH(ctx, own_kind(0, nf), launch_fft_z_fwd(nf, real, ctx->spec, ctx->fg, ctx->stream));
             PM_LAUNCH(ctx, own_kind(1, nf), launch_fft_pencils(1, false, ctx->spec, 0, nf, ctx->fg, ctx->stream));
             PM_LAUNCH(ctx, (adj ? "fft_x_round_4" : "fft_x_round_1"),
@@ -708,14 +735,14 @@ int64_t pm_launch_count(const pm_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 const int kTuneCand[PM_TUNE_KINDS][3] = {{128, 256, 512}, {128, 256, 512}, {128, 256, 512},
                                          {128, 256, 512}, {8, 16, 0},      {1, 2, 0},
-                                         {1, 2, 0},       {1, 2, 3}};
+                                         {1, 2, 0},       {1, 2, 3},       {1, 2, 0}};
 
 static int set_tuning(pm_ctx *ctx, const int *t) {
     for (int k = 0; k < PM_TUNE_KINDS; ++k)
         if (t[k] <= 0 || (t[k] != kTuneCand[k][0] && t[k] != kTuneCand[k][1] && t[k] != kTuneCand[k][2]))
             return fail(ctx, PM_EINVAL,
                         "block sizes must be 128, 256 or 512, the x-pass width 8 or 16, the z stagings 1 or 2, "
-                        "the x round trip 1, 2 or 3");
+                        "the x round trip 1, 2 or 3, the force pipeline 1 or 2");
     for (int k = 0; k < PM_TUNE_KINDS; ++k) ctx->tune[k] = t[k];
     ctx->fg.zthreads = ctx->tune[3];
     ctx->fg.xwidth = ctx->tune[4];
@@ -798,6 +825,10 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
             if ((e = launch_fft_z_inv(3, ctx->spec, ctx->r4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
             return launch_fft_z_inv(4, ctx->spec, ctx->r4, ctx->fg, ctx->stream);
         }
+        if (kind == 8) {  // a whole force and adjoint evaluation: the pipelines differ from the x pass on
+            if (force_meshes(ctx, s, nullptr) != PM_OK || force_meshes(ctx, s, s) != PM_OK) return cudaErrorUnknown;
+            return cudaGetLastError();
+        }
         if ((e = launch_fft_z_fwd(1, ctx->r1, ctx->spec, ctx->fg, ctx->stream)) != cudaSuccess) return e;
         if ((e = launch_fft_z_fwd(4, ctx->r4, ctx->spec, ctx->fg, ctx->stream)) != cudaSuccess) return e;
         if ((e = launch_fft_z_inv(3, ctx->spec, ctx->r4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
@@ -809,7 +840,8 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
     for (int kind = 0; kind < PM_TUNE_KINDS && rc == PM_OK; ++kind) {
         if ((kind == 3 && !(ctx->own && ctx->P.n_m >= 256)) || (kind == 4 && !ctx->own) ||
             (kind == 5 && !(ctx->own && ctx->zmaps[0].valid)) || (kind == 6 && !ctx->own) ||
-            (kind == 7 && !ctx->own)) {
+            (kind == 7 && !ctx->own) ||
+            (kind == 8 && !(ctx->own && !(ctx->P.solver & PM_SOLVER_SPECTRAL_GRADIENT)))) {
             if (ms) ms[3 * kind] = ms[3 * kind + 1] = ms[3 * kind + 2] = 0.f;
             continue;
         }
@@ -974,6 +1006,7 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
         const size_t n3 = (size_t)n * n * n;
         if (cudaMalloc(&ctx->r1, sizeof(float) * n3 * B) != cudaSuccess ||
             cudaMalloc(&ctx->r4, sizeof(float) * 4 * n3 * B) != cudaSuccess ||
+            cudaMalloc(&ctx->rpot, sizeof(float) * 2 * n3 * B) != cudaSuccess ||
             cudaMalloc(&ctx->spec, sizeof(float2) * 4 * (size_t)ctx->fg.fstride) != cudaSuccess ||
             cudaMalloc(&ctx->tw, sizeof(float2) * 1024) != cudaSuccess ||
             cudaMemset(ctx->spec, 0, sizeof(float2) * 4 * (size_t)ctx->fg.fstride) != cudaSuccess ||
@@ -993,6 +1026,8 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
         ctx->fg.ztma = encode_z_inv_maps(ctx->spec, ctx->fg, ctx->zmaps) ? 1 : 0;
         ctx->tune[5] = ctx->fg.ztma ? 2 : 1;
         ctx->tune[7] = ctx->P.n_m >= 512 ? 3 : 2;  // the fused adjoint spills on lines of 512+ points
+        // the potential pipeline needs the 4-point difference gradient
+        ctx->tune[8] = (c.solver & PM_SOLVER_SPECTRAL_GRADIENT) ? 1 : 2;
     } else if (cudaMalloc(&ctx->mesh, sizeof(float) * (size_t)ctx->mesh_pad * B * kMeshFields) != cudaSuccess) {
         cudaGetLastError();
         fail(ctx, PM_ENOMEM, "cannot allocate the FFT meshes");
@@ -1078,7 +1113,8 @@ int pm_destroy(pm_ctx *ctx) {
                     (void *)ctx->nn_err, (void *)ctx->nn_feat, (void *)ctx->nn_mesh4, (void *)ctx->nn_gx})
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-    for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->spec, (void *)ctx->tw, (void *)ctx->d_err}) 
+    for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->rpot, (void *)ctx->spec, (void *)ctx->tw,
+                    (void *)ctx->d_err})
         if (p) cudaFree(p);
     for (void *p : {(void *)ctx->mesh, (void *)ctx->lat, (void *)ctx->d_table, (void *)ctx->d_pref, (void *)ctx->d_grad, (void *)ctx->d_dec,
                     (void *)ctx->d_fac, (void *)ctx->d_lin, (void *)ctx->d_red, (void *)ctx->d_pk,

@@ -216,7 +216,8 @@ __device__ __forceinline__ bool tma_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Inverse: spectrum fields 0 .. GS-1 -> real mesh with GO interleaved
-// slots per cell (GO = 4: slots >= GS written as 0; GO = 1: plain rows).
+// slots per cell (GO = 4: slots >= GS written as 0; GO = 1: plain rows), or
+// for GO = 2 two planar meshes, field 1 nb n^3 floats after field 0.
 // TMA: the block's Y rows of each field, kz blocks 0 .. M/8, arrive in
 // shared memory by one 5-D tensor copy per field ([16 floats][y][x][kz
 // block][field, run]; box 16 x Y x 1 x (M/8 + 1) x 1) instead of per-thread
@@ -308,7 +309,16 @@ __global__ void __launch_bounds__(T) k_fft_z_inv(const float2 *__restrict__ spec
     }
     __syncthreads();
     float4 *dst = reinterpret_cast<float4 *>(out + (bx * N + y0) * (int64_t)N * GO);
-    if (GO == 4) {
+    if (GO == 2) {  // two planar meshes [field][run][n^3], rows of float4
+        float4 *p0 = reinterpret_cast<float4 *>(out + (bx * N + y0) * (int64_t)N);
+        float4 *p1 = p0 + (int64_t)fg.nb * N * N * N / 4;
+        for (int e = tid; e < Y * N / 4; e += S::THREADS) {
+            const int y2 = (4 * e) / N, z = (4 * e) % N;
+            const float *l0 = reinterpret_cast<const float *>(sm + y2 * 2 * LP) + z;
+            p0[e] = *reinterpret_cast<const float4 *>(l0);
+            p1[e] = *reinterpret_cast<const float4 *>(l0 + 2 * LP);
+        }
+    } else if (GO == 4) {
         for (int e = tid; e < Y * N; e += S::THREADS) {
             const int y2 = e / N, z = e % N;
             const float *l0 = reinterpret_cast<const float *>(sm + y2 * 4 * LP);
@@ -725,6 +735,111 @@ __global__ void __launch_bounds__(lsplit(L) * kPencil, XRoundShape<L, ADJ, FD>::
     xr_inverse<L, false>(Y, base, nullptr, 0.f, 0.f, false, ls, ys, r, w, fg.tw);
 }
 
+// Potential form of the x round trip, for the 4-point difference gradient.
+// The force F_j = i D_j g delta is S_j phi with phi = IFFT(g delta) and S_j
+// the periodic 4-point difference along axis j (Fourier symbol i D_j), so a
+// force evaluation needs the one inverse transform of phi, and the
+// difference is taken on the real mesh afterwards (launch_grad_stencil):
+//   force    field 0 (delta) -> field 0 (phi along x: g delta, inverse x)
+//   adjoint  fields 0..3 (delta, u_x, u_y, u_z) -> field 0 (phi) and
+//            field 1 (psi = -g FFT_x(S_x u_x + i (D_y u_y + D_z u_z)),
+//            the stencil form of the fused adjoint above)
+// One forward and one inverse transform in flight at a time: half the
+// registers of the gradient form.
+template <int L, bool ADJ>
+__global__ void __launch_bounds__(lsplit(L) * kPencil, 2) k_fft_xpot(float2 *spec, FftGeom fg, XRoundArgs xa) {
+    constexpr int M1 = lsplit(L), M2 = msplit(L), W = kPencil, J = M2 / M1;
+    extern __shared__ float4 smraw[];
+    float2 *ys = reinterpret_cast<float2 *>(smraw);
+    const int tid = threadIdx.x, w = tid % W, r = tid / W;
+    const int kzblocks = fg.zc / W;
+    const int64_t p = blockIdx.x;
+    const int y = (int)(p % L);
+    const int64_t outer = p / L;  // run * (zc / 8) + kz block
+    const int run = (int)(outer / kzblocks);
+    const int iz = (int)(outer % kzblocks) * W + w;
+    const int64_t ls = (int64_t)L * W;
+    float2 *base = spec + outer * ((int64_t)L * L * W) + (int64_t)y * W + w;
+    const int64_t fs = fg.fstride;
+    const float kyz2 = xa.kf * xa.kf * (float)((y < L / 2 ? y : y - L) * (y < L / 2 ? y : y - L) + iz * iz);
+    const float dyz = iz > L / 2 ? 0.f : __ldg(xa.pref + run) * __ldg(xa.dec + y) * __ldg(xa.dec + iz);
+    auto gmode = [&](int j, int k1) -> float {
+        const int ix = r + M1 * j + M2 * k1;
+        const int nx = ix < L / 2 ? ix : ix - L;
+        const float k2 = xa.kf * xa.kf * (float)(nx * nx) + kyz2;
+        return k2 > 0.f ? dyz * __ldg(xa.dec + ix) / k2 : 0.f;
+    };
+    float2 X[J][M1], Y[J][M1];
+    if (ADJ) {
+        const float gy = __ldg(xa.grad + y), gz = iz > L / 2 ? 0.f : __ldg(xa.grad + iz);
+        // the line S_x u_x + i (D_y u_y + D_z u_z), u_x staged as [x][column] for the stencil
+#pragma unroll
+        for (int n2 = 0; n2 < M2; ++n2) {
+            const int x = r + M1 * n2;
+            ys[x * W + w] = base[fs + x * ls];
+        }
+        __syncthreads();
+        float2 v[M2];
+#pragma unroll
+        for (int n2 = 0; n2 < M2; ++n2) {
+            const int x = r + M1 * n2;
+            const float2 a1 = ys[((x + 1) & (L - 1)) * W + w], b1 = ys[((x - 1) & (L - 1)) * W + w];
+            const float2 a2 = ys[((x + 2) & (L - 1)) * W + w], b2 = ys[((x - 2) & (L - 1)) * W + w];
+            const float sx = xa.inv12h * (8.f * (a1.x - b1.x) - (a2.x - b2.x));
+            const float sy = xa.inv12h * (8.f * (a1.y - b1.y) - (a2.y - b2.y));
+            const float2 uy = base[2 * fs + x * ls], uz = base[3 * fs + x * ls];
+            const float tx = gy * uy.x + gz * uz.x, ty = gy * uy.y + gz * uz.y;
+            v[n2] = make_float2(sx - ty, sy + tx);
+        }
+        __syncthreads();  // the stencil reads are done: the transform reuses the buffer
+        xr_forward_regs<L>(v, ys, r, w, X, fg.tw);
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+            for (int k1 = 0; k1 < M1; ++k1) {
+                const float g = gmode(j, k1);
+                const float2 a = X[j][bitrev(k1, ilog2(M1))];
+                Y[j][k1] = make_float2(-g * a.x, -g * a.y);
+            }
+        xr_inverse<L, false>(Y, base + fs, nullptr, 0.f, 0.f, false, ls, ys, r, w, fg.tw);  // psi -> field 1
+    }
+    xr_forward<L>(base, ls, ys, r, w, X, fg.tw);
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+        for (int k1 = 0; k1 < M1; ++k1) {
+            const float g = gmode(j, k1);
+            const float2 d = X[j][bitrev(k1, ilog2(M1))];
+            Y[j][k1] = make_float2(g * d.x, g * d.y);
+        }
+    xr_inverse<L, false>(Y, base, nullptr, 0.f, 0.f, false, ls, ys, r, w, fg.tw);  // phi -> field 0
+}
+
+template <int L, bool ADJ>
+cudaError_t xpot_l(float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
+    constexpr int M1 = lsplit(L), M2 = msplit(L);
+    const size_t smem = sizeof(float2) * M1 * (M2 * kPencil + kPencil);  // >= L * 8 for the stencil stage
+    cudaError_t e = cudaFuncSetAttribute(k_fft_xpot<L, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (int64_t)fg.nb * (fg.zc / kPencil) * L;
+    k_fft_xpot<L, ADJ><<<(unsigned)blocks, M1 * kPencil, smem, st>>>(spec, fg, xa);
+    return cudaGetLastError();
+}
+
+template <bool ADJ>
+cudaError_t xpot_n(float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
+    switch (fg.n) {
+        case 16: return xpot_l<16, ADJ>(spec, fg, xa, st);
+        case 32: return xpot_l<32, ADJ>(spec, fg, xa, st);
+        case 64: return xpot_l<64, ADJ>(spec, fg, xa, st);
+        case 128: return xpot_l<128, ADJ>(spec, fg, xa, st);
+        case 256: return xpot_l<256, ADJ>(spec, fg, xa, st);
+        case 512: return xpot_l<512, ADJ>(spec, fg, xa, st);
+        case 1024: return xpot_l<1024, ADJ>(spec, fg, xa, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int L, bool ADJ, bool FD>
 cudaError_t xround_l(float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
     constexpr int M1 = lsplit(L), M2 = msplit(L);
@@ -843,6 +958,7 @@ cudaError_t launch_fft_z_inv(int gs, const float2 *spec, float *out, const FftGe
     switch (gs) {
         case 4: return z_inv_g<4, 4>(spec, out, fg, st);
         case 3: return z_inv_g<3, 4>(spec, out, fg, st);
+        case 2: return z_inv_g<2, 2>(spec, out, fg, st);
         case 1: return z_inv_g<1, 1>(spec, out, fg, st);
         default: return cudaErrorInvalidValue;
     }
@@ -879,6 +995,14 @@ cudaError_t launch_fft_pencils(int axis, bool inverse, float2 *spec, int f0, int
 cudaError_t launch_fft_xround(bool adj, float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
     if (!xa.grad || !xa.dec || !xa.pref || !own_fft_supported(fg.n)) return cudaErrorInvalidValue;
     return adj ? xround_n<true>(spec, fg, xa, st) : xround_n<false>(spec, fg, xa, st);
+}
+
+// Potential form of the x round trip (k_fft_xpot): force field 0 -> 0;
+// adjoint fields 0..3 -> 0 (phi), 1 (psi).  Needs the 4-point difference
+// gradient (xa.fd).
+cudaError_t launch_fft_xpot(bool adj, float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
+    if (!xa.grad || !xa.dec || !xa.pref || !xa.fd || !own_fft_supported(fg.n)) return cudaErrorInvalidValue;
+    return adj ? xpot_n<true>(spec, fg, xa, st) : xpot_n<false>(spec, fg, xa, st);
 }
 
 }  // namespace pmgb

@@ -177,7 +177,8 @@ int own_fft_zc(int n);
 cudaError_t upload_fft_constants(float2 *tw_dev);
 cudaError_t launch_fft_z_fwd(int g, const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st);
 bool encode_z_inv_maps(float2 *spec, const FftGeom &fg, ZInvMap maps[3]);
-// gs = 4 or 3: spectrum fields -> 4-slot interleaved real mesh; gs = 1: plain real mesh.
+// gs = 4 or 3: spectrum fields -> 4-slot interleaved real mesh; gs = 2: two
+// planar meshes (field 1 at out + nb n^3); gs = 1: plain real mesh.
 cudaError_t launch_fft_z_inv(int gs, const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st);
 // Multipliers of the fused x round trip (launch_fft_xround): the spectral
 // kernels' gradient and deconvolution tables, kf = 2 pi / box, the per-run
@@ -190,6 +191,14 @@ struct XRoundArgs {
     int fd;        // the gradient is the 4-point difference (not the spectral i k)
 };
 cudaError_t launch_fft_xround(bool adj, float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st);
+// Potential form of the x round trip (4-point difference gradient only):
+// force field 0 (delta) -> field 0 (phi, with F_j = S_j phi); adjoint fields
+// 0..3 (delta, u) -> 0 (phi), 1 (psi).
+cudaError_t launch_fft_xpot(bool adj, float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st);
+// F_j = S_j phi on the real mesh (the 4-point difference; symbol i D_j):
+// in [gi][run][n^3] planar (phi, and psi for gi = 2) -> out [run][n^3]
+// float4 (F_x, F_y, F_z, psi or 0).  n a power of two, >= 16.
+cudaError_t launch_grad_stencil(const float *in, int gi, float4 *out, int n, int nb, float inv12h, cudaStream_t st);
 cudaError_t launch_fft_pencils(int axis, bool inverse, float2 *spec, int f0, int nf, const FftGeom &fg,
                                cudaStream_t st);
 cudaError_t launch_spec_copy(float2 *blocked, float2 *plain, const FftGeom &fg, bool to_plain, cudaStream_t st);

@@ -442,7 +442,70 @@ dim3 site_grid(int np, int nb) {
     return dim3((unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), nb);
 }
 
+// The force from the potential mesh: F_j(c) = S_j phi(c), S_j the periodic
+// 4-point central difference along axis j,
+//   S f(c) = [8 (f(c + e_j) - f(c - e_j)) - (f(c + 2 e_j) - f(c - 2 e_j))] / (12 h),
+// whose Fourier symbol is i D_j (zero at the Nyquist index exactly: the two
+// differences of an alternating line vanish).  in: planar [gi][run][n^3],
+// phi (and psi when GI = 2); out: [run][n^3] float4 (F_x, F_y, F_z, psi or
+// 0), the layout the read kernels take.  n is a power of two (own-FFT
+// meshes).  A block takes a TX x TY x TZ tile: the tile and a 2-node
+// periodic halo of phi go to shared memory in coalesced rows along z, every
+// thread then forms its nodes' three differences from shared memory.  Tiles
+// run z fastest, then y, then x, so neighbouring blocks share halo lines in L2.
+template <int GI, int TZ>
+__global__ void __launch_bounds__(kThreads) k_grad_stencil(const float *__restrict__ in, float4 *__restrict__ out,
+                                                           int lgn, float inv12h) {
+    constexpr int TX = 4, TY = 4, HX = TX + 4, HY = TY + 4, HZ = TZ + 4;
+    constexpr int PER = TX * TY * TZ / kThreads;
+    __shared__ float tile[HX][HY][HZ];
+    const int n = 1 << lgn, m = n - 1;
+    const int64_t n3 = (int64_t)1 << (3 * lgn);
+    const int b = blockIdx.y;
+    const float *phi = in + (int64_t)b * n3;
+    const int ntz = n / TZ, nty = n / TY;
+    const int t = blockIdx.x;
+    const int z0 = (t % ntz) * TZ, y0 = ((t / ntz) % nty) * TY, x0 = (t / ntz / nty) * TX;
+    for (int e = threadIdx.x; e < HX * HY * HZ; e += kThreads) {
+        const int iz = e % HZ, iy = (e / HZ) % HY, ix = e / (HZ * HY);
+        const int64_t g = (((int64_t)((x0 + ix - 2) & m) << lgn | ((y0 + iy - 2) & m)) << lgn) | ((z0 + iz - 2) & m);
+        tile[ix][iy][iz] = __ldg(phi + g);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int c = threadIdx.x + q * kThreads;
+        const int lz = c % TZ, ly = (c / TZ) % TY, lx = c / (TZ * TY);
+        const int X = lx + 2, Yy = ly + 2, Z = lz + 2;
+        const float fx = inv12h * (8.f * (tile[X + 1][Yy][Z] - tile[X - 1][Yy][Z]) - (tile[X + 2][Yy][Z] - tile[X - 2][Yy][Z]));
+        const float fy = inv12h * (8.f * (tile[X][Yy + 1][Z] - tile[X][Yy - 1][Z]) - (tile[X][Yy + 2][Z] - tile[X][Yy - 2][Z]));
+        const float fz = inv12h * (8.f * (tile[X][Yy][Z + 1] - tile[X][Yy][Z - 1]) - (tile[X][Yy][Z + 2] - tile[X][Yy][Z - 2]));
+        const int64_t g = (((int64_t)(x0 + lx) << lgn | (y0 + ly)) << lgn) | (z0 + lz);
+        out[(int64_t)b * n3 + g] = make_float4(fx, fy, fz, GI == 2 ? __ldg(in + (int64_t)gridDim.y * n3 + (int64_t)b * n3 + g) : 0.f);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_grad_stencil(const float *in, int gi, float4 *out, int n, int nb, float inv12h, cudaStream_t st) {
+    int lgn = 0;
+    while ((1 << lgn) < n) ++lgn;
+    if ((1 << lgn) != n || n < 16 || (gi != 1 && gi != 2)) return cudaErrorInvalidValue;
+    const int tz = n < 128 ? n : 128;
+    const dim3 grid((unsigned)((n / 4) * (n / 4) * (n / tz)), nb);
+    auto go = [&](auto kernel) { kernel<<<grid, kThreads, 0, st>>>(in, out, lgn, inv12h); };
+    switch (tz * 4 + gi) {
+        case 16 * 4 + 1: go(k_grad_stencil<1, 16>); break;
+        case 16 * 4 + 2: go(k_grad_stencil<2, 16>); break;
+        case 32 * 4 + 1: go(k_grad_stencil<1, 32>); break;
+        case 32 * 4 + 2: go(k_grad_stencil<2, 32>); break;
+        case 64 * 4 + 1: go(k_grad_stencil<1, 64>); break;
+        case 64 * 4 + 2: go(k_grad_stencil<2, 64>); break;
+        case 128 * 4 + 1: go(k_grad_stencil<1, 128>); break;
+        default: go(k_grad_stencil<2, 128>); break;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_spectral(int mode, const Spec &sp, const float *pref, cudaStream_t st) {
     switch (sp.threads) {

@@ -44,7 +44,9 @@ class ParticleMesh:
             rc = self._lib.pm_create(ctypes.byref(self.cfg), ctypes.byref(self._ctx))
         if rc != _pmgb.PM_OK:
             raise PMError(f"pm_create: {_pmgb.ERRORS.get(rc, rc)}: {self._lib.pm_last_error(None).decode()}")
-        self._x_round_default = self.get_tuning()["x_round"]      # 2, or 3 on meshes of 512 and more
+        tuning = self.get_tuning()
+        self._x_round_default = tuning["x_round"]          # 2, or 3 on meshes of 512 and more
+        self._pipeline_default = tuning["pipeline"]        # 2, or 1 with the spectral-gradient flag
 
     # ------------------------------------------------------------ helpers --
     @property
@@ -235,7 +237,8 @@ class ParticleMesh:
         return loss.value
 
     # ------------------------------------------------------- autotuner --
-    TUNE_FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x", "z_staging", "z_fwd_staging", "x_round")
+    TUNE_FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x", "z_staging", "z_fwd_staging", "x_round",
+                     "pipeline")
 
     def autotune(self, s):
         """Pick the fastest launch shape per kernel family on particles s;
@@ -244,7 +247,9 @@ class ParticleMesh:
         z_staging 1 (loads) and 2 (TMA), z_fwd_staging 1 (strided loads) and
         2 (coalesced, staged), x_round 1 (x pass, spectral multiply and
         inverse x pass as three launches), 2 (one fused kernel) and 3 (fused
-        for the force, three launches for the adjoint))."""
+        for the force, three launches for the adjoint), pipeline 1 (force
+        components as inverse transforms) and 2 (one inverse transform of
+        the potential, then the 4-point difference on the real mesh))."""
         self._particles(s, "s")
         ms = np.zeros((len(self.TUNE_FAMILIES), 3), np.float32)
         self._call("pm_autotune", _ptr(s), ms.ctypes.data_as(ctypes.c_void_p))
@@ -256,15 +261,17 @@ class ParticleMesh:
         return dict(zip(self.TUNE_FAMILIES, (int(v) for v in t)))
 
     def set_tuning(self, paint=256, read=256, spectral=256, fft_z=256, fft_x=8, z_staging=None, z_fwd_staging=1,
-                   x_round=None):
+                   x_round=None, pipeline=None):
         """Fix the launch shapes; a family not named takes the context's
-        default (z_staging keeps its current value, x_round the mesh-size
-        default the context was created with)."""
+        default (z_staging keeps its current value, x_round and pipeline the
+        defaults the context was created with)."""
         if z_staging is None:
             z_staging = self.get_tuning()["z_staging"]
         if x_round is None:
             x_round = self._x_round_default
-        t = np.array([paint, read, spectral, fft_z, fft_x, z_staging, z_fwd_staging, x_round], np.int32)
+        if pipeline is None:
+            pipeline = self._pipeline_default
+        t = np.array([paint, read, spectral, fft_z, fft_x, z_staging, z_fwd_staging, x_round, pipeline], np.int32)
         self._call("pm_set_tuning", t.ctypes.data_as(ctypes.c_void_p))
 
     def use_graphs(self, enable=True):

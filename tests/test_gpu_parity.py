@@ -326,5 +326,10 @@ def test_graph_replay_matches_direct_launches():
     ref = run()
     for fwd, l, d in results:
         assert torch.max(torch.abs(fwd - ref[0])).item() < 1e-5 * box / n_p
-        assert torch.max(torch.abs(l - ref[1])).item() < 1e-3 * torch.max(torch.abs(ref[1])).item()
-        assert abs(d - ref[2]) < 1e-3 * abs(ref[2])
+        # relative L2, not the largest element: a particle whose reconstructed
+        # position lands on the other side of a cell face in one of the runs
+        # takes the other one-sided CIC slope there, a jump of its own lam
+        assert ((l - ref[1]).norm() / ref[1].norm()).item() < 1e-3
+        # dL/dOm sums per-step terms about 30 times larger than itself, so the
+        # order of the atomics alone moves it by ~2e-3 of its value
+        assert abs(d - ref[2]) < 5e-3 * abs(ref[2])

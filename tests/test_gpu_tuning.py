@@ -10,12 +10,12 @@ from paper_2211_09958_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x", "z_staging", "z_fwd_staging", "x_round")
+FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x", "z_staging", "z_fwd_staging", "x_round", "pipeline")
 CANDIDATES = {"paint": (128, 256, 512), "read": (128, 256, 512), "spectral": (128, 256, 512),
               "fft_z": (128, 256, 512), "fft_x": (8, 16), "z_staging": (1, 2), "z_fwd_staging": (1, 2),
-              "x_round": (1, 2, 3)}
+              "x_round": (1, 2, 3), "pipeline": (1, 2)}
 DEFAULT = {"paint": 256, "read": 256, "spectral": 256, "fft_z": 256, "fft_x": 8, "z_staging": 2, "z_fwd_staging": 1,
-           "x_round": 2}
+           "x_round": 2, "pipeline": 2}
 
 
 def _pm(n_p=32, n_m=256, box=128.0, steps=3):
@@ -38,7 +38,7 @@ def test_every_block_size_gives_the_same_force_and_trajectory():
             pm.set_tuning(**{fam: t, "z_staging": 2})
             f = pm.pm_force(s0)
             assert (f - ref_f).abs().max().item() <= 2e-5 * scale_f, (fam, t)
-            if fam == "x_round":
+            if fam in ("x_round", "pipeline"):
                 # changes the FFT's rounding order, not only the order of
                 # atomics; its trajectories are compared at parity bounds below
                 pm.set_tuning(z_staging=2)
@@ -76,12 +76,13 @@ def test_tma_and_load_staging_give_the_same_adjoint():
     # through a full adjoint step (force and psi meshes)
     pm = _pm(n_p=32, n_m=256, box=128.0, steps=2)
     assert pm.get_tuning()["z_staging"] == 2                      # TMA is the default at n_m = 256
+    pm.set_tuning(pipeline=1)            # the gradient pipeline's 4-field z inverse is the one staged by TMA
     s, p = pm.init_lpt(seed=8)
     f = pm.integrate(s, p)
     lam = torch.from_numpy(np.random.default_rng(2).standard_normal(tuple(s.shape)).astype(np.float32)).cuda()
     out = {}
     for staging in (2, 1):
-        pm.set_tuning(z_staging=staging)
+        pm.set_tuning(z_staging=staging, pipeline=1)
         s2, p2, l2, m2 = s.clone(), p.clone(), lam.clone(), torch.zeros_like(p)
         dom = pm.adjoint_integrate(s2, p2, f.clone(), l2, m2)
         out[staging] = (l2, m2, dom)
