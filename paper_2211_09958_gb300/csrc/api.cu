@@ -306,6 +306,12 @@ bool pot_pipeline(const pm_ctx *ctx) {
     return ctx->own && ctx->tune[8] == 2 && !(ctx->P.solver & PM_SOLVER_SPECTRAL_GRADIENT);
 }
 
+// Whether the CIC read takes the force straight from the potential mesh (the
+// difference formed per corner in the read kernel) instead of from the float4
+// force mesh of the stencil pass: the potential pipeline with CIC assignment
+// and without the learned correction (which adds to the force mesh).
+bool pot_read(const pm_ctx *ctx) { return pot_pipeline(ctx) && ctx->g.order == 2 && !ctx->nn_on; }
+
 // Multipliers of the fused x round trip: the spectral kernels' tables.
 XRoundArgs xround_args(pm_ctx *ctx) {
     return XRoundArgs{(float)(2.0 * M_PI / ctx->P.box), ctx->d_grad, ctx->d_dec, ctx->d_pref,
@@ -368,6 +374,20 @@ ReadArgs read_args(pm_ctx *ctx, float *s) {
     a.red_bstride = 2 * (ctx->P.n_steps + 1);
     a.drift_step = -1;
     a.threads = ctx->tune[1];
+    return a;
+}
+
+// Read arguments after a force evaluation (force_meshes): with the
+// potential read, the potential (and psi) meshes instead of the force mesh.
+ReadArgs force_read_args(pm_ctx *ctx, float *s) {
+    ReadArgs a = read_args(ctx, s);
+    if (pot_read(ctx)) {
+        a.pot = ctx->rpot;
+        int lgn = 0;
+        while ((1 << lgn) < ctx->P.n_m) ++lgn;
+        a.lgn = lgn;
+        a.inv12h = xround_args(ctx).inv12h;
+    }
     return a;
 }
 
@@ -439,9 +459,10 @@ int force_meshes(pm_ctx *ctx, const float *s, const float *mu, double a = -1.0, 
             if (adj && ctx->nn_on && a > 0.0) PM_TRY(correction_adjoint(ctx, a, kick_step, kick_sel));
             PM_LAUNCH(ctx, own_kind(4, np), launch_fft_pencils(1, true, ctx->spec, 0, np, ctx->fg, ctx->stream));
             PM_LAUNCH(ctx, own_kind(5, np), launch_fft_z_inv(np, ctx->spec, ctx->rpot, ctx->fg, ctx->stream));
-            PM_LAUNCH(ctx, (adj ? "grad_stencil_2" : "grad_stencil_1"),
-                      launch_grad_stencil(ctx->rpot, np, reinterpret_cast<float4 *>(ctx->r4), ctx->P.n_m,
-                                          ctx->P.n_batch, xround_args(ctx).inv12h, ctx->stream));
+            if (!pot_read(ctx))
+                PM_LAUNCH(ctx, (adj ? "grad_stencil_2" : "grad_stencil_1"),
+                          launch_grad_stencil(ctx->rpot, np, reinterpret_cast<float4 *>(ctx->r4), ctx->P.n_m,
+                                              ctx->P.n_batch, xround_args(ctx).inv12h, ctx->stream));
         } else if (x_fused(ctx, adj)) {  // z and y forward, fused x round trip, y and z inverse
             PM_LAUNCH(ctx, own_kind(0, nf), launch_fft_z_fwd(nf, real, ctx->spec, ctx->fg, ctx->stream));
             PM_LAUNCH(ctx, own_kind(1, nf), launch_fft_pencils(1, false, ctx->spec, 0, nf, ctx->fg, ctx->stream));
@@ -793,7 +814,7 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
             return launch_paint(PAINT_ADJ, pa, ctx->stream);
         }
         if (kind == 1) {
-            ReadArgs ra = read_args(ctx, const_cast<float *>(s));
+            ReadArgs ra = force_read_args(ctx, const_cast<float *>(s));
             ra.f = f;
             return launch_read(READ_FORCE, ra, ctx->stream);
         }
@@ -825,8 +846,13 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
             if ((e = launch_fft_z_inv(3, ctx->spec, ctx->r4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
             return launch_fft_z_inv(4, ctx->spec, ctx->r4, ctx->fg, ctx->stream);
         }
-        if (kind == 8) {  // a whole force and adjoint evaluation: the pipelines differ from the x pass on
-            if (force_meshes(ctx, s, nullptr) != PM_OK || force_meshes(ctx, s, s) != PM_OK) return cudaErrorUnknown;
+        if (kind == 8) {  // a whole force evaluation with its read, and an adjoint one (the pipelines differ
+                          // from the x pass on; the potential read moves the difference into the read)
+            if (force_meshes(ctx, s, nullptr) != PM_OK) return cudaErrorUnknown;
+            ReadArgs ra = force_read_args(ctx, const_cast<float *>(s));
+            ra.f = f;
+            if ((e = launch_read(READ_FORCE, ra, ctx->stream)) != cudaSuccess) return e;
+            if (force_meshes(ctx, s, s) != PM_OK) return cudaErrorUnknown;
             return cudaGetLastError();
         }
         if ((e = launch_fft_z_fwd(1, ctx->r1, ctx->spec, ctx->fg, ctx->stream)) != cudaSuccess) return e;
@@ -1206,7 +1232,7 @@ int pm_force(pm_ctx *ctx, const float *s, float *f) {
     PM_TRY(check_ptr(ctx, f, "f"));
     DeviceGuard guard(ctx->device);
     PM_TRY(force_meshes(ctx, s, nullptr));
-    ReadArgs ra = read_args(ctx, const_cast<float *>(s));
+    ReadArgs ra = force_read_args(ctx, const_cast<float *>(s));
     ra.f = f;
     return read_forces(ctx, READ_FORCE, ra);
 }
@@ -1223,7 +1249,7 @@ int pm_kdk_step(pm_ctx *ctx, int32_t step, float *s, float *p, float *f) {
     pr.step = step;
     PM_LAUNCH(ctx, "pre_kick_drift", launch_pre(PRE_KICK_DRIFT, pr, ctx->stream));
     PM_TRY(force_meshes(ctx, s, nullptr, a_of(ctx, step + 1)));
-    ReadArgs ra = read_args(ctx, s);
+    ReadArgs ra = force_read_args(ctx, s);
     ra.p = p;
     ra.f = f;
     ra.kick_step = step;
@@ -1240,7 +1266,7 @@ int pm_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, fl
         return fail(ctx, PM_EINVAL, "need 0 <= step_begin < step_end <= n_steps");
     DeviceGuard guard(ctx->device);
     return run_graphed(ctx, 1, step_begin, step_end, s, p, f, nullptr, nullptr, 0, [&]() -> int {
-        ReadArgs ra = read_args(ctx, s);
+        ReadArgs ra = force_read_args(ctx, s);
         ra.p = p;
         ra.f = f;
         for (int n = step_begin; n < step_end; ++n) {
@@ -1294,7 +1320,7 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
         } else {
             // VJP of the last half kick at s_N, fused with the reverse drift of step `last`
             PM_TRY(force_meshes(ctx, s, mu, a_of(ctx, last + 1), last, KICK_B));
-            ReadArgs ra = read_args(ctx, s);
+            ReadArgs ra = force_read_args(ctx, s);
             ra.p = p;
             ra.lam = lam;
             ra.mu = mu;
@@ -1312,7 +1338,7 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
                 PM_TRY(ck_copy(ctx, p, ck_ptr(ctx, ck, 1)));
             }
             PM_TRY(force_meshes(ctx, s, mu, a_of(ctx, n), n, n == step_begin ? KICK_A : KICK_MERGED));
-            ReadArgs ra = read_args(ctx, s);
+            ReadArgs ra = force_read_args(ctx, s);
             ra.p = p;
             ra.lam = lam;
             ra.mu = mu;

@@ -81,12 +81,81 @@ __global__ void __launch_bounds__(T) k_paint(PaintArgs a) {
         }
 }
 
-template <int MODE, bool IL, int T, int K>
+// The force at the 8 CIC corners (c0 + i, c1 + j, c2 + l), i, j, l in {0, 1},
+// from the potential mesh phi by the 4-point difference along each axis,
+//   F_a(c) = [8 (phi(c + e_a) - phi(c - e_a)) - (phi(c + 2 e_a) - phi(c - 2 e_a))] / (12 h).
+// The 56 distinct nodes: along x the 6 nodes c0 - 2 .. c0 + 3 of each of the
+// 4 (y, z) corner lines, along y and z the 4 outer nodes of each line (the
+// inner two are corners, already loaded).
+__device__ __forceinline__ void pot_corner_forces(const float *__restrict__ phi, int lgn, float inv12h, const int c[3],
+                                                  float Fc[2][2][2][3]) {
+    const int m = (1 << lgn) - 1;
+    auto at = [&](int x, int y, int z) {
+        return __ldg(phi + ((((int64_t)(x & m) << lgn) | (y & m)) << lgn | (z & m)));
+    };
+    float xl[2][2][6];  // phi(c0 - 2 + k, c1 + j, c2 + l)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) xl[j][l][k] = at(c[0] - 2 + k, c[1] + j, c[2] + l);
+    float yo[2][2][4], zo[2][2][4];  // outer nodes k = 0, 1, 4, 5 of the y and z lines
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = q < 2 ? q : q + 2;
+                yo[i][l][q] = at(c[0] + i, c[1] - 2 + k, c[2] + l);
+                zo[i][l][q] = at(c[0] + i, c[1] + l, c[2] - 2 + k);
+            }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                // line values at offsets -2 .. +2 around the corner, per axis
+                const float *x5 = &xl[j][l][i];
+                const float ym2 = j == 0 ? yo[i][l][0] : yo[i][l][1], ym1 = j == 0 ? yo[i][l][1] : xl[0][l][2 + i];
+                const float yp1 = j == 0 ? xl[1][l][2 + i] : yo[i][l][2], yp2 = j == 0 ? yo[i][l][2] : yo[i][l][3];
+                const float zm2 = l == 0 ? zo[i][j][0] : zo[i][j][1], zm1 = l == 0 ? zo[i][j][1] : xl[j][0][2 + i];
+                const float zp1 = l == 0 ? xl[j][1][2 + i] : zo[i][j][2], zp2 = l == 0 ? zo[i][j][2] : zo[i][j][3];
+                Fc[i][j][l][0] = inv12h * (8.f * (x5[3] - x5[1]) - (x5[4] - x5[0]));
+                Fc[i][j][l][1] = inv12h * (8.f * (yp1 - ym1) - (yp2 - ym2));
+                Fc[i][j][l][2] = inv12h * (8.f * (zp1 - zm1) - (zp2 - zm2));
+            }
+}
+
+// Lattice tile of one block of the potential read: TX x TY x 8 particles
+// (x, y, z; z fastest; 4 x 4 x 8, 4 x 8 x 8 or 8 x 8 x 8), so that the mesh
+// nodes the block's stencils touch form a compact region that L1 holds,
+// instead of 36 full mesh rows per lattice row of particles.
+template <int T>
+struct ReadTile {
+    static constexpr int TZ = 8, TX = T >= 512 ? 8 : 4, TY = T / (TX * TZ);
+};
+
+template <int MODE, bool IL, int T, int K, bool POT = false>
 __global__ void __launch_bounds__(T) k_read(ReadArgs a) {
     const int b = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * T + threadIdx.x;
+    int64_t i = (int64_t)blockIdx.x * T + threadIdx.x;
+    bool valid = i < a.g.npart;
+    if (POT) {
+        using RT = ReadTile<T>;
+        const int np = a.g.np;
+        const int ntz = (np + RT::TZ - 1) / RT::TZ, nty = (np + RT::TY - 1) / RT::TY;
+        const int tb = blockIdx.x;
+        const int iz = (tb % ntz) * RT::TZ + threadIdx.x % RT::TZ;
+        const int iy = ((tb / ntz) % nty) * RT::TY + (threadIdx.x / RT::TZ) % RT::TY;
+        const int ix = (tb / (ntz * nty)) * RT::TX + threadIdx.x / (RT::TZ * RT::TY);
+        valid = ix < np && iy < np && iz < np;
+        i = ((int64_t)ix * np + iy) * np + iz;
+    }
     float red[2] = {0.f, 0.f};
-    if (i < a.g.npart) {
+    if (valid) {
         const int64_t gi = ((int64_t)b * a.g.npart + i) * 3;
         const float sx = a.s[gi], sy = a.s[gi + 1], sz = a.s[gi + 2];
         cic::Stencil<K> st;
@@ -105,6 +174,14 @@ __global__ void __launch_bounds__(T) k_read(ReadArgs a) {
             mu[2] = a.mu[gi + 2];
         }
         float F[3] = {0.f, 0.f, 0.f}, G[3] = {0.f, 0.f, 0.f};
+        float Fc[2][2][2][3];
+        const float *psi = nullptr;
+        if (POT) {
+            const int64_t n3 = (int64_t)1 << (3 * a.lgn);
+            const int c3[3] = {st.n[0][0], st.n[1][0], st.n[2][0]};
+            pot_corner_forces(a.pot + (int64_t)b * n3, a.lgn, a.inv12h, c3, Fc);
+            psi = a.pot + ((int64_t)a.g.nb + b) * n3;
+        }
 #pragma unroll
         for (int ox = 0; ox < K; ++ox)
 #pragma unroll
@@ -121,7 +198,13 @@ __global__ void __launch_bounds__(T) k_read(ReadArgs a) {
                     } else {
                         const float w = wx[ox] * wy[oy] * wz[oz];
                         float fx, fy, fz, fp = 0.f;
-                        if (IL) {
+                        if (POT) {
+                            fx = Fc[ox & 1][oy & 1][oz & 1][0];
+                            fy = Fc[ox & 1][oy & 1][oz & 1][1];
+                            fz = Fc[ox & 1][oy & 1][oz & 1][2];
+                            if (MODE == READ_ADJ)
+                                fp = __ldg(psi + ((int64_t)st.n[0][ox] * nm + st.n[1][oy]) * nm + st.n[2][oz]);
+                        } else if (IL) {
                             const float4 q = __ldg(reinterpret_cast<const float4 *>(m0) + idx);
                             fx = q.x;
                             fy = q.y;
@@ -256,9 +339,26 @@ void read_il(int mode, const ReadArgs &a, cudaStream_t st) {
     }
 }
 
+template <int T>
+void read_pot(int mode, const ReadArgs &a, cudaStream_t st) {
+    using RT = ReadTile<T>;
+    const int64_t np = a.g.np;
+    const dim3 grid((unsigned)(((np + RT::TX - 1) / RT::TX) * ((np + RT::TY - 1) / RT::TY) * ((np + RT::TZ - 1) / RT::TZ)),
+                    a.g.nb);
+    switch (mode) {
+        case READ_FORCE: k_read<READ_FORCE, false, T, 2, true><<<grid, T, 0, st>>>(a); break;
+        case READ_KICK_DRIFT: k_read<READ_KICK_DRIFT, false, T, 2, true><<<grid, T, 0, st>>>(a); break;
+        case READ_HALF_KICK: k_read<READ_HALF_KICK, false, T, 2, true><<<grid, T, 0, st>>>(a); break;
+        case READ_ADJ: k_read<READ_ADJ, false, T, 2, true><<<grid, T, 0, st>>>(a); break;
+        default: break;
+    }
+}
+
 template <int T, int K = 2>
 void read_t(int mode, const ReadArgs &a, cudaStream_t st) {
-    if (a.mesh.il == 4)
+    if (K == 2 && a.pot)
+        read_pot<T>(mode, a, st);
+    else if (a.mesh.il == 4)
         read_il<true, T, K>(mode, a, st);
     else
         read_il<false, T, K>(mode, a, st);
@@ -287,6 +387,7 @@ cudaError_t launch_read(int mode, const ReadArgs &a, cudaStream_t st) {
         else
             k_read<READ_GRAD, false, kThreads, 2><<<particle_grid(a.g), kThreads, 0, st>>>(a);
     } else if (mode >= READ_FORCE && mode <= READ_ADJ && a.g.order == 3) {
+        if (a.pot) return cudaErrorInvalidValue;  // the potential read is CIC only
         read_t<kThreads, 3>(mode, a, st);
     } else if (mode >= READ_FORCE && mode <= READ_ADJ) {
         switch (a.threads) {

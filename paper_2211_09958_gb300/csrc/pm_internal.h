@@ -123,6 +123,13 @@ struct ReadArgs {
     int red_bstride;
     int red2_offset;      // drift reduction at red + red2_offset (0 when no drift)
     int threads;          // block size: 128, 256 (also for 0) or 512 (autotuned)
+    // potential read (CIC, own-FFT meshes): when pot != NULL the force at each
+    // corner is formed from the potential mesh by the 4-point difference
+    // (pot [run][n^3] plain; the adjoint's psi one field later, at
+    // pot + nb n^3) instead of being loaded from the float4 force mesh
+    const float *pot;
+    int lgn;              // log2 n_m
+    float inv12h;         // 1 / (12 h)
 };
 
 cudaError_t launch_paint(int mode, const PaintArgs &a, cudaStream_t st);
