@@ -133,6 +133,7 @@ def algorithmic_bytes(kind, npart, ncell, nmodes):
         "spectral_adj": (32 + 32) * nmodes,
         "grad_stencil_1": (4 + 16) * ncell,                  # phi in; (F, 0) float4 out
         "grad_stencil_2": (8 + 16) * ncell,                  # (phi, psi) in; (F, psi) out
+        "vjp_source": (16 + 8) * ncell,                      # (rho, u) float4 in; (rho, v) out
     }
     # own FFT passes: kind "fft_<axis>_<dir>_<fields>"
     if kind.startswith("fft_"):
@@ -144,8 +145,8 @@ def algorithmic_bytes(kind, npart, ncell, nmodes):
             return nf * 8 * nmodes + (16 if nf >= 3 else 4 * nf) * ncell   # spectra in, real mesh out
         if direction == "round":                          # fused x pass: density in, 3 fields out; 4 in, 4 out
             return (8 + 24) * nmodes if nf == 1 else 64 * nmodes
-        if direction == "pot":                            # potential x pass: 1 in, 1 out; 4 in, 2 out
-            return 16 * nmodes if nf == 1 else 48 * nmodes
+        if direction == "pot":                            # potential x pass: 1 in, 1 out; 2 in, 2 out; 4 in, 2 out
+            return {1: 16, 2: 32, 4: 48}[nf] * nmodes
         return nf * 16 * nmodes                             # pencil pass: read + write
     return per.get(kind)
 

@@ -403,7 +403,7 @@ PreArgs pre_args(pm_ctx *ctx, float *s, float *p) {
 
 const char *own_kind(int pass, int nf) {
     static const char *names[6][5] = {
-        {"", "fft_z_fwd_1", "", "", "fft_z_fwd_4"}, {"", "fft_y_fwd_1", "", "", "fft_y_fwd_4"},
+        {"", "fft_z_fwd_1", "fft_z_fwd_2", "", "fft_z_fwd_4"}, {"", "fft_y_fwd_1", "fft_y_fwd_2", "", "fft_y_fwd_4"},
         {"", "fft_x_fwd_1", "", "", "fft_x_fwd_4"}, {"", "fft_x_inv_1", "", "fft_x_inv_3", "fft_x_inv_4"},
         {"", "fft_y_inv_1", "fft_y_inv_2", "fft_y_inv_3", "fft_y_inv_4"},
         {"", "fft_z_inv_1", "fft_z_inv_2", "fft_z_inv_3", "fft_z_inv_4"}};
@@ -449,12 +449,24 @@ int force_meshes(pm_ctx *ctx, const float *s, const float *mu, double a = -1.0, 
         const int go = adj ? 4 : 3;
         if (pot_pipeline(ctx)) {
             // z and y forward; x round trip to phi (and psi); y and z inverse of
-            // those one or two fields; F = S phi on the real mesh into r4
+            // those one or two fields; F = S phi on the real mesh into r4.  The
+            // adjoint first forms its source v = sum_j S_j u_j on the real mesh
+            // (rho, v into rpot) and transforms two fields instead of four,
+            // except with the learned correction, whose adjoint reads the
+            // painted fields between the transforms
             const int np = adj ? 2 : 1;
-            PM_LAUNCH(ctx, own_kind(0, nf), launch_fft_z_fwd(nf, real, ctx->spec, ctx->fg, ctx->stream));
-            PM_LAUNCH(ctx, own_kind(1, nf), launch_fft_pencils(1, false, ctx->spec, 0, nf, ctx->fg, ctx->stream));
-            PM_LAUNCH(ctx, (adj ? "fft_x_pot_4" : "fft_x_pot_1"),
-                      launch_fft_xpot(adj, ctx->spec, ctx->fg, xround_args(ctx), ctx->stream));
+            const int nt = adj && !ctx->nn_on ? 2 : nf;
+            const float *zin = real;
+            if (nt == 2) {
+                PM_LAUNCH(ctx, "vjp_source",
+                          launch_vjp_source(reinterpret_cast<const float4 *>(ctx->r4), reinterpret_cast<float2 *>(ctx->rpot),
+                                            ctx->P.n_m, ctx->P.n_batch, xround_args(ctx).inv12h, ctx->stream));
+                zin = ctx->rpot;
+            }
+            PM_LAUNCH(ctx, own_kind(0, nt), launch_fft_z_fwd(nt, zin, ctx->spec, ctx->fg, ctx->stream));
+            PM_LAUNCH(ctx, own_kind(1, nt), launch_fft_pencils(1, false, ctx->spec, 0, nt, ctx->fg, ctx->stream));
+            PM_LAUNCH(ctx, (nt == 4 ? "fft_x_pot_4" : (nt == 2 ? "fft_x_pot_2" : "fft_x_pot_1")),
+                      launch_fft_xpot(nt, ctx->spec, ctx->fg, xround_args(ctx), ctx->stream));
             // the correction's adjoint reads the painted (rho, mu) still in r4
             if (adj && ctx->nn_on && a > 0.0) PM_TRY(correction_adjoint(ctx, a, kick_step, kick_sel));
             PM_LAUNCH(ctx, own_kind(4, np), launch_fft_pencils(1, true, ctx->spec, 0, np, ctx->fg, ctx->stream));

@@ -746,8 +746,10 @@ __global__ void __launch_bounds__(lsplit(L) * kPencil, XRoundShape<L, ADJ, FD>::
 //            the stencil form of the fused adjoint above)
 // One forward and one inverse transform in flight at a time: half the
 // registers of the gradient form.
-template <int L, bool ADJ>
-__global__ void __launch_bounds__(lsplit(L) * kPencil, 2) k_fft_xpot(float2 *spec, FftGeom fg, XRoundArgs xa) {
+template <int L, int NF>
+__global__ void __launch_bounds__(lsplit(L) * kPencil, 2)
+    k_fft_xpot(float2 *spec, FftGeom fg, XRoundArgs xa, float gsign) {
+    constexpr bool ADJ = NF == 4;
     constexpr int M1 = lsplit(L), M2 = msplit(L), W = kPencil, J = M2 / M1;
     extern __shared__ float4 smraw[];
     float2 *ys = reinterpret_cast<float2 *>(smraw);
@@ -808,34 +810,40 @@ __global__ void __launch_bounds__(lsplit(L) * kPencil, 2) k_fft_xpot(float2 *spe
     for (int j = 0; j < J; ++j)
 #pragma unroll
         for (int k1 = 0; k1 < M1; ++k1) {
-            const float g = gmode(j, k1);
+            const float g = gsign * gmode(j, k1);
             const float2 d = X[j][bitrev(k1, ilog2(M1))];
             Y[j][k1] = make_float2(g * d.x, g * d.y);
         }
     xr_inverse<L, false>(Y, base, nullptr, 0.f, 0.f, false, ls, ys, r, w, fg.tw);  // phi -> field 0
 }
 
-template <int L, bool ADJ>
+template <int L, int NF>
 cudaError_t xpot_l(float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
     constexpr int M1 = lsplit(L), M2 = msplit(L);
     const size_t smem = sizeof(float2) * M1 * (M2 * kPencil + kPencil);  // >= L * 8 for the stencil stage
-    cudaError_t e = cudaFuncSetAttribute(k_fft_xpot<L, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_xpot<L, NF == 2 ? 1 : NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)fg.nb * (fg.zc / kPencil) * L;
-    k_fft_xpot<L, ADJ><<<(unsigned)blocks, M1 * kPencil, smem, st>>>(spec, fg, xa);
+    if (NF == 2) {  // psi = -IFFT(g v) (field 1), then phi (field 0): two independent round trips
+        k_fft_xpot<L, 1><<<(unsigned)blocks, M1 * kPencil, smem, st>>>(spec + fg.fstride, fg, xa, -1.f);
+        k_fft_xpot<L, 1><<<(unsigned)blocks, M1 * kPencil, smem, st>>>(spec, fg, xa, 1.f);
+    } else {
+        k_fft_xpot<L, NF><<<(unsigned)blocks, M1 * kPencil, smem, st>>>(spec, fg, xa, 1.f);
+    }
     return cudaGetLastError();
 }
 
-template <bool ADJ>
+template <int NF>
 cudaError_t xpot_n(float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
     switch (fg.n) {
-        case 16: return xpot_l<16, ADJ>(spec, fg, xa, st);
-        case 32: return xpot_l<32, ADJ>(spec, fg, xa, st);
-        case 64: return xpot_l<64, ADJ>(spec, fg, xa, st);
-        case 128: return xpot_l<128, ADJ>(spec, fg, xa, st);
-        case 256: return xpot_l<256, ADJ>(spec, fg, xa, st);
-        case 512: return xpot_l<512, ADJ>(spec, fg, xa, st);
-        case 1024: return xpot_l<1024, ADJ>(spec, fg, xa, st);
+        case 16: return xpot_l<16, NF>(spec, fg, xa, st);
+        case 32: return xpot_l<32, NF>(spec, fg, xa, st);
+        case 64: return xpot_l<64, NF>(spec, fg, xa, st);
+        case 128: return xpot_l<128, NF>(spec, fg, xa, st);
+        case 256: return xpot_l<256, NF>(spec, fg, xa, st);
+        case 512: return xpot_l<512, NF>(spec, fg, xa, st);
+        case 1024: return xpot_l<1024, NF>(spec, fg, xa, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -951,7 +959,12 @@ bool encode_z_inv_maps(float2 *spec, const FftGeom &fg, ZInvMap maps[3]) {
 }
 
 cudaError_t launch_fft_z_fwd(int g, const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {
-    return g == 4 ? z_fwd_g<4>(in, spec, fg, st) : z_fwd_g<1>(in, spec, fg, st);
+    switch (g) {
+        case 4: return z_fwd_g<4>(in, spec, fg, st);
+        case 2: return z_fwd_g<2>(in, spec, fg, st);
+        case 1: return z_fwd_g<1>(in, spec, fg, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_fft_z_inv(int gs, const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st) {
@@ -998,11 +1011,17 @@ cudaError_t launch_fft_xround(bool adj, float2 *spec, const FftGeom &fg, const X
 }
 
 // Potential form of the x round trip (k_fft_xpot): force field 0 -> 0;
-// adjoint fields 0..3 -> 0 (phi), 1 (psi).  Needs the 4-point difference
+// adjoint fields 0..3 -> 0 (phi), 1 (psi); adjoint with the source on the
+// real mesh, fields 0, 1 -> 0 (phi), 1 (psi).  Needs the 4-point difference
 // gradient (xa.fd).
-cudaError_t launch_fft_xpot(bool adj, float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
+cudaError_t launch_fft_xpot(int nf, float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st) {
     if (!xa.grad || !xa.dec || !xa.pref || !xa.fd || !own_fft_supported(fg.n)) return cudaErrorInvalidValue;
-    return adj ? xpot_n<true>(spec, fg, xa, st) : xpot_n<false>(spec, fg, xa, st);
+    switch (nf) {
+        case 1: return xpot_n<1>(spec, fg, xa, st);
+        case 2: return xpot_n<2>(spec, fg, xa, st);
+        case 4: return xpot_n<4>(spec, fg, xa, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace pmgb

@@ -199,13 +199,18 @@ struct XRoundArgs {
 };
 cudaError_t launch_fft_xround(bool adj, float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st);
 // Potential form of the x round trip (4-point difference gradient only):
-// force field 0 (delta) -> field 0 (phi, with F_j = S_j phi); adjoint fields
-// 0..3 (delta, u) -> 0 (phi), 1 (psi).
-cudaError_t launch_fft_xpot(bool adj, float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st);
+// nf = 1: field 0 (delta) -> field 0 (phi = IFFT(g delta), F_j = S_j phi);
+// nf = 4: fields 0..3 (delta, u) -> 0 (phi), 1 (psi); nf = 2: fields 0
+// (delta), 1 (v = sum_j S_j u_j) -> 0 (phi), 1 (psi = -IFFT(g v)).
+cudaError_t launch_fft_xpot(int nf, float2 *spec, const FftGeom &fg, const XRoundArgs &xa, cudaStream_t st);
 // F_j = S_j phi on the real mesh (the 4-point difference; symbol i D_j):
 // in [gi][run][n^3] planar (phi, and psi for gi = 2) -> out [run][n^3]
 // float4 (F_x, F_y, F_z, psi or 0).  n a power of two, >= 16.
 cudaError_t launch_grad_stencil(const float *in, int gi, float4 *out, int n, int nb, float inv12h, cudaStream_t st);
+// The adjoint source v = sum_j S_j u_j from the 4-field paint: in [run][n^3]
+// float4 (rho, u_x, u_y, u_z) -> out [run][n^3] float2 (rho, v).  n a power
+// of two, >= 16.
+cudaError_t launch_vjp_source(const float4 *in, float2 *out, int n, int nb, float inv12h, cudaStream_t st);
 cudaError_t launch_fft_pencils(int axis, bool inverse, float2 *spec, int f0, int nf, const FftGeom &fg,
                                cudaStream_t st);
 cudaError_t launch_spec_copy(float2 *blocked, float2 *plain, const FftGeom &fg, bool to_plain, cudaStream_t st);

@@ -485,7 +485,80 @@ __global__ void __launch_bounds__(kThreads) k_grad_stencil(const float *__restri
     }
 }
 
+// The adjoint's source on the real mesh: from the 4-field paint (alpha sum W,
+// sum mu_x W, sum mu_y W, sum mu_z W) per cell, v = sum_j S_j u_j, S_j the
+// periodic 4-point difference along axis j.  Its transform is
+// sum_j i D_j u_j(k), so psi(k) = -g v(k) needs one forward transform
+// instead of three.  out: [run][n^3] float2 (rho, v).  A block takes a
+// 4 x 8 x TZ tile; each component is staged in shared memory with the halo
+// of its own axis only (u_x two planes each side in x, u_y two rows in y,
+// u_z two nodes in z).
+template <int TZ>
+__global__ void __launch_bounds__(kThreads) k_vjp_source(const float4 *__restrict__ in, float2 *__restrict__ out,
+                                                         int lgn, float inv12h) {
+    constexpr int TX = 4, TY = 8, PER = TX * TY * TZ / kThreads;
+    __shared__ float ux[TX + 4][TY][TZ], uy[TX][TY + 4][TZ], uz[TX][TY][TZ + 4], rho[TX][TY][TZ];
+    const int n = 1 << lgn, m = n - 1;
+    const int64_t n3 = (int64_t)1 << (3 * lgn);
+    const int b = blockIdx.y;
+    const float4 *src = in + (int64_t)b * n3;
+    const float *srcf = reinterpret_cast<const float *>(src);
+    const int ntz = n / TZ, nty = n / TY;
+    const int t = blockIdx.x;
+    const int z0 = (t % ntz) * TZ, y0 = ((t / ntz) % nty) * TY, x0 = (t / ntz / nty) * TX;
+    auto cell = [&](int x, int y, int z) -> int64_t {
+        return (((int64_t)(x & m) << lgn) | (y & m)) << lgn | (z & m);
+    };
+    // the x-extended block: whole cells inside, u_x alone in the x halo
+    for (int e = threadIdx.x; e < (TX + 4) * TY * TZ; e += kThreads) {
+        const int iz = e % TZ, iy = (e / TZ) % TY, ix = e / (TZ * TY) - 2;
+        if (ix >= 0 && ix < TX) {
+            const float4 c = __ldg(src + cell(x0 + ix, y0 + iy, z0 + iz));
+            rho[ix][iy][iz] = c.x;
+            ux[ix + 2][iy][iz] = c.y;
+            uy[ix][iy + 2][iz] = c.z;
+            uz[ix][iy][iz + 2] = c.w;
+        } else {
+            ux[ix + 2][iy][iz] = __ldg(srcf + 4 * cell(x0 + ix, y0 + iy, z0 + iz) + 1);
+        }
+    }
+    for (int e = threadIdx.x; e < TX * 4 * TZ; e += kThreads) {  // y halo: u_y
+        const int iz = e % TZ, q = (e / TZ) % 4, ix = e / (TZ * 4);
+        const int iy = q < 2 ? q - 2 : TY + q - 2;
+        uy[ix][iy + 2][iz] = __ldg(srcf + 4 * cell(x0 + ix, y0 + iy, z0 + iz) + 2);
+    }
+    for (int e = threadIdx.x; e < TX * TY * 4; e += kThreads) {  // z halo: u_z
+        const int q = e % 4, iy = (e / 4) % TY, ix = e / (4 * TY);
+        const int iz = q < 2 ? q - 2 : TZ + q - 2;
+        uz[ix][iy][iz + 2] = __ldg(srcf + 4 * cell(x0 + ix, y0 + iy, z0 + iz) + 3);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int c = threadIdx.x + q * kThreads;
+        const int lz = c % TZ, ly = (c / TZ) % TY, lx = c / (TZ * TY);
+        const float sx = 8.f * (ux[lx + 3][ly][lz] - ux[lx + 1][ly][lz]) - (ux[lx + 4][ly][lz] - ux[lx][ly][lz]);
+        const float sy = 8.f * (uy[lx][ly + 3][lz] - uy[lx][ly + 1][lz]) - (uy[lx][ly + 4][lz] - uy[lx][ly][lz]);
+        const float sz = 8.f * (uz[lx][ly][lz + 3] - uz[lx][ly][lz + 1]) - (uz[lx][ly][lz + 4] - uz[lx][ly][lz]);
+        const int64_t g = (((int64_t)(x0 + lx) << lgn | (y0 + ly)) << lgn) | (z0 + lz);
+        out[(int64_t)b * n3 + g] = make_float2(rho[lx][ly][lz], inv12h * (sx + sy + sz));
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_vjp_source(const float4 *in, float2 *out, int n, int nb, float inv12h, cudaStream_t st) {
+    int lgn = 0;
+    while ((1 << lgn) < n) ++lgn;
+    if ((1 << lgn) != n || n < 16) return cudaErrorInvalidValue;
+    const int tz = n < 32 ? n : 32;
+    const dim3 grid((unsigned)((n / 4) * (n / 8) * (n / tz)), nb);
+    if (tz == 16)
+        k_vjp_source<16><<<grid, kThreads, 0, st>>>(in, out, lgn, inv12h);
+    else
+        k_vjp_source<32><<<grid, kThreads, 0, st>>>(in, out, lgn, inv12h);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_grad_stencil(const float *in, int gi, float4 *out, int n, int nb, float inv12h, cudaStream_t st) {
     int lgn = 0;
