@@ -118,14 +118,18 @@ class ClockSampler:
 # Algorithmic HBM bytes per launch of each library kernel (FP32 state,
 # (N, 3) particle arrays; mesh bytes counted on the unpadded n_m^3 grid,
 # complex modes on the n_m^2 (n_m/2+1) rfft grid).
-def algorithmic_bytes(kind, npart, ncell, nmodes):
+def algorithmic_bytes(kind, npart, ncell, nmodes, pot_read=False):
+    """pot_read: the CIC reads take the potential (and psi) meshes, one (two)
+    float per cell, instead of the float4 force mesh (the library does with
+    its default force pipeline, CIC and no learned correction)."""
+    fmesh = 4 if pot_read else 12                         # mesh bytes per cell of a force read
     per = {
         "paint_density": 12 * npart + 4 * ncell,
         "paint_adj": 24 * npart + 16 * ncell,                # s, mu in; 4 fields out
-        "read_force": 24 * npart + 12 * ncell,
-        "read_kick_drift": 48 * npart + 12 * ncell,          # s, p in and out; 3 force fields in
-        "read_half_kick": 48 * npart + 12 * ncell,           # s, p in; p, F out
-        "read_adj": (48 + 48) * npart + 16 * ncell,          # s, p, lam, mu in and out (fused drift)
+        "read_force": 24 * npart + fmesh * ncell,
+        "read_kick_drift": 48 * npart + fmesh * ncell,       # s, p in and out; phi or 3 force fields in
+        "read_half_kick": 48 * npart + fmesh * ncell,        # s, p in; p, F out
+        "read_adj": (48 + 48) * npart + (8 if pot_read else 16) * ncell,   # s, p, lam, mu in and out (fused drift)
         "read_grad": 24 * npart + 4 * ncell,
         "pre_rev_drift": 72 * npart,
         "pre_kick_drift": 60 * npart,
@@ -429,9 +433,10 @@ def run_ours(args):
     if rank == 0:
         hbm, peak_src = _peaks()
         npart, ncell, nmodes = pm.n_batch * w.n_p ** 3, pm.n_batch * w.n_m ** 3, pm.n_batch * w.n_m ** 2 * (w.n_m // 2 + 1)
+        pot_read = tuning.get("pipeline") == 2 and (w.n_m & (w.n_m - 1)) == 0
         table = {}
         for kind, (cnt, ms) in kernels.items():
-            ab = algorithmic_bytes(kind, npart, ncell, nmodes)
+            ab = algorithmic_bytes(kind, npart, ncell, nmodes, pot_read)
             ent = {"launches": cnt, "total_ms": round(ms, 3), "share": round(ms / prof_total, 4)}
             if ab is not None and cnt:
                 ent["gbs"] = round(ab / (ms / cnt / 1e3) / 1e9, 1)
@@ -456,7 +461,7 @@ def run_ours(args):
                         "ms_per_step": float(np.mean(step_ms) - np.mean(fwd_ms))},
             "roofline": {"bound": "hbm", "kernel": dom_kind, "achieved": dk["gbs"], "peak": hbm, "unit": "GB/s",
                          "frac": dk["frac"], "peak_source": peak_src,
-                         "algorithmic_bytes_per_launch": algorithmic_bytes(dom_kind, npart, ncell, nmodes),
+                         "algorithmic_bytes_per_launch": algorithmic_bytes(dom_kind, npart, ncell, nmodes, pot_read),
                          "traffic": traffic},
             "kernels": table,
             "profiled": {"ms_per_step": prof_total / args.steps, "pass": PROFILED_NOTE},

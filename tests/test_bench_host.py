@@ -46,6 +46,15 @@ def test_algorithmic_bytes_per_launch():
     # the fused x round trip saves two spectrum round trips per evaluation
     assert ab("fft_x_fwd_1") + ab("spectral_force") + ab("fft_x_inv_3") - ab("fft_x_round_1") == 64 * K
     assert ab("fft_x_fwd_4") + ab("spectral_adj") + ab("fft_x_inv_4") - ab("fft_x_round_4") == 128 * K
+    # the potential pipeline: one field each way per force x pass, two per
+    # adjoint x pass, the adjoint source stencil, the planar 2-field z inverse
+    assert ab("fft_x_pot_1") == 16 * K and ab("fft_x_pot_2") == 32 * K and ab("fft_x_pot_4") == 48 * K
+    assert ab("vjp_source") == 24 * M and ab("grad_stencil_1") == 20 * M
+    assert ab("fft_z_inv_2") == 2 * 8 * K + 8 * M and ab("fft_z_fwd_2") == 2 * (4 * M + 8 * K)
+    # reads from the potential mesh count one float per cell (two for the adjoint's phi, psi)
+    pr = lambda kind: bench.algorithmic_bytes(kind, N, M, K, pot_read=True)  # noqa: E731
+    assert pr("read_kick_drift") == 48 * N + 4 * M and ab("read_kick_drift") == 48 * N + 12 * M
+    assert pr("read_adj") == 96 * N + 8 * M and ab("read_adj") == 96 * N + 16 * M
 
 
 def test_tuning_argument():
