@@ -27,6 +27,38 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
                  : "memory");
 }
 
+// Lattice tile of one block of the potential read (TX x TY x 8 particles, z
+// fastest; 4 x 4 x 8, 4 x 8 x 8 or 8 x 8 x 8): the mesh nodes a block's
+// stencils touch form a compact region that L1 holds (one thread per
+// particle in lattice order touches 36 full mesh rows per lattice row
+// instead).  The paints keep lattice order: tiled, they ran no faster over
+// the 100-step run and the density paint ran 2x slower on a clustered state,
+// where a tile's particles meet in the same cells at once.
+template <int T>
+struct LatticeTile {
+    static constexpr int TZ = 8, TX = T >= 512 ? 8 : 4, TY = T / (TX * TZ);
+};
+
+template <int T>
+__device__ __forceinline__ bool tile_particle(int np, int64_t &i) {
+    using LT = LatticeTile<T>;
+    const int ntz = (np + LT::TZ - 1) / LT::TZ, nty = (np + LT::TY - 1) / LT::TY;
+    const int tb = blockIdx.x;
+    const int iz = (tb % ntz) * LT::TZ + threadIdx.x % LT::TZ;
+    const int iy = ((tb / ntz) % nty) * LT::TY + (threadIdx.x / LT::TZ) % LT::TY;
+    const int ix = (tb / (ntz * nty)) * LT::TX + threadIdx.x / (LT::TZ * LT::TY);
+    i = ((int64_t)ix * np + iy) * np + iz;
+    return ix < np && iy < np && iz < np;
+}
+
+template <int T>
+dim3 tile_grid(const Geom &g) {
+    using LT = LatticeTile<T>;
+    const int64_t np = g.np;
+    return dim3((unsigned)(((np + LT::TX - 1) / LT::TX) * ((np + LT::TY - 1) / LT::TY) * ((np + LT::TZ - 1) / LT::TZ)),
+                g.nb);
+}
+
 template <int MODE, int T, int K>
 __global__ void __launch_bounds__(T) k_paint(PaintArgs a) {
     const int b = blockIdx.y;
@@ -129,31 +161,12 @@ __device__ __forceinline__ void pot_corner_forces(const float *__restrict__ phi,
             }
 }
 
-// Lattice tile of one block of the potential read: TX x TY x 8 particles
-// (x, y, z; z fastest; 4 x 4 x 8, 4 x 8 x 8 or 8 x 8 x 8), so that the mesh
-// nodes the block's stencils touch form a compact region that L1 holds,
-// instead of 36 full mesh rows per lattice row of particles.
-template <int T>
-struct ReadTile {
-    static constexpr int TZ = 8, TX = T >= 512 ? 8 : 4, TY = T / (TX * TZ);
-};
-
 template <int MODE, bool IL, int T, int K, bool POT = false>
 __global__ void __launch_bounds__(T) k_read(ReadArgs a) {
     const int b = blockIdx.y;
     int64_t i = (int64_t)blockIdx.x * T + threadIdx.x;
     bool valid = i < a.g.npart;
-    if (POT) {
-        using RT = ReadTile<T>;
-        const int np = a.g.np;
-        const int ntz = (np + RT::TZ - 1) / RT::TZ, nty = (np + RT::TY - 1) / RT::TY;
-        const int tb = blockIdx.x;
-        const int iz = (tb % ntz) * RT::TZ + threadIdx.x % RT::TZ;
-        const int iy = ((tb / ntz) % nty) * RT::TY + (threadIdx.x / RT::TZ) % RT::TY;
-        const int ix = (tb / (ntz * nty)) * RT::TX + threadIdx.x / (RT::TZ * RT::TY);
-        valid = ix < np && iy < np && iz < np;
-        i = ((int64_t)ix * np + iy) * np + iz;
-    }
+    if (POT) valid = tile_particle<T>(a.g.np, i);  // lattice tiles: the nodes a block's stencils touch stay in L1
     float red[2] = {0.f, 0.f};
     if (valid) {
         const int64_t gi = ((int64_t)b * a.g.npart + i) * 3;
@@ -341,10 +354,7 @@ void read_il(int mode, const ReadArgs &a, cudaStream_t st) {
 
 template <int T>
 void read_pot(int mode, const ReadArgs &a, cudaStream_t st) {
-    using RT = ReadTile<T>;
-    const int64_t np = a.g.np;
-    const dim3 grid((unsigned)(((np + RT::TX - 1) / RT::TX) * ((np + RT::TY - 1) / RT::TY) * ((np + RT::TZ - 1) / RT::TZ)),
-                    a.g.nb);
+    const dim3 grid = tile_grid<T>(a.g);
     switch (mode) {
         case READ_FORCE: k_read<READ_FORCE, false, T, 2, true><<<grid, T, 0, st>>>(a); break;
         case READ_KICK_DRIFT: k_read<READ_KICK_DRIFT, false, T, 2, true><<<grid, T, 0, st>>>(a); break;
