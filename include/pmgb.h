@@ -99,11 +99,18 @@ typedef struct pm_config {
  *                                nodes j - 1, j, j + 1 of the nearest node j)
  *                                instead of cloud-in-cell; with
  *                                PM_SOLVER_DECONVOLVE the window is
- *                                prod_j sinc^6(k_j h / 2) */
+ *                                prod_j sinc^6(k_j h / 2)
+ *   PM_SOLVER_GROWTH_EMULATOR    the growth quantities behind the KDK, 2LPT
+ *                                and d/dOm tables come from the growth
+ *                                emulator (pm_growth_emulate) instead of one
+ *                                ODE solve per cosmology; needs Omega_m in
+ *                                [0.1, 0.6] and a_init, a_final in [1e-3, 1]
+ *                                (PM_ERANGE otherwise) */
 #define PM_SOLVER_SPECTRAL_GRADIENT 1
 #define PM_SOLVER_DECONVOLVE 2
 #define PM_SOLVER_LOG_A 4
 #define PM_SOLVER_TSC 8
+#define PM_SOLVER_GROWTH_EMULATOR 16
 
 /* Create a context: validates cfg, computes the FP64 growth and coefficient
  * tables on the host, allocates the scratch meshes and creates the cuFFT
@@ -281,6 +288,21 @@ int pm_mesh_irfft(pm_ctx *ctx, const float *spec, float *real);
  *   k_mean, power, n_modes  host [n_batch][n_m/2] outputs. */
 int pm_power_spectrum(pm_ctx *ctx, const float *s, double *k_mean,
                       double *power, double *n_modes);
+
+/* Host-only growth-function emulator (needs no GPU).  The paper names a
+ * growth-function emulator as separate work adjacent to pmwd (Statement of
+ * Need) and does not describe it; this one is a two-dimensional Chebyshev
+ * series in (ln a, Omega_m), 48 x 16 terms of each of D1/a, dD1/da, D2/a^2
+ * and (dD2/da)/a, fitted once per process to the library's own growth ODE
+ * solve (the one pm_create uses; D1(1) = 1, D2 with the same factor
+ * squared).  It reproduces that solve to ~1e-10 over the domain.
+ *   omega_m  in [0.1, 0.6]
+ *   a        host [n] scale factors, each in [1e-3, 1]
+ *   out      host [n][8]: D1, D2, dD1/da, dD2/da, dD1/dOm, dD2/dOm,
+ *            d(dD1/da)/dOm, d(dD2/da)/dOm
+ * Returns PM_OK, PM_EINVAL (n < 0, NULL arrays with n > 0) or PM_ERANGE
+ * (a value outside the domain; nothing is written). */
+int pm_growth_emulate(double omega_m, int32_t n, const double *a, double *out);
 
 /* Host-only (needs no GPU): the FP64 tables pm_create would compute.
  *   kdk   [n_batch][n_steps][3]  K_a, Dr, K_b per step       (may be NULL)

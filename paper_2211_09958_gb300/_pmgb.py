@@ -38,7 +38,7 @@ class PmConfig(ctypes.Structure):
     ]
 
 
-SOLVER_SPECTRAL_GRADIENT, SOLVER_DECONVOLVE, SOLVER_LOG_A, SOLVER_TSC = 1, 2, 4, 8
+SOLVER_SPECTRAL_GRADIENT, SOLVER_DECONVOLVE, SOLVER_LOG_A, SOLVER_TSC, SOLVER_GROWTH_EMULATOR = 1, 2, 4, 8, 16
 
 
 _P = ctypes.c_void_p
@@ -61,6 +61,7 @@ _SIGNATURES = {
     "pm_density": (ctypes.c_int, [_P, _P, _P]),
     "pm_density_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
     "pm_mse_loss": (ctypes.c_int, [_P, _P, _P, _c_double_p, _P]),
+    "pm_growth_emulate": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, _c_double_p, _c_double_p]),
     "pm_mse_loss_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _P, _P,
                                            _P, _P, _P]),
     "pm_mesh_rfft": (ctypes.c_int, [_P, _P, _P]),

@@ -250,12 +250,22 @@ int upload_tables(pm_ctx *ctx) {
     return PM_OK;
 }
 
-int check_cosmology(pm_ctx *ctx, const double *om, const double *s8, int B) {
+int check_cosmology(pm_ctx *ctx, const double *om, const double *s8, int B, int solver = 0) {
     if (!om || !s8) return fail(ctx, PM_EINVAL, "omega_m and sigma8 must be host arrays of n_batch values");
     for (int b = 0; b < B; ++b) {
         if (!(om[b] > 0.0 && om[b] <= 1.0)) return fail(ctx, PM_EINVAL, "omega_m must be in (0, 1]");
         if (!(s8[b] > 0.0)) return fail(ctx, PM_EINVAL, "sigma8 must be > 0");
+        if ((solver & PM_SOLVER_GROWTH_EMULATOR) && !growth_emulator_covers(om[b], 0.5))
+            return fail(ctx, PM_ERANGE, "the growth emulator covers omega_m in [0.1, 0.6]");
     }
+    return PM_OK;
+}
+
+// The time range the growth emulator covers (solver flag 16).
+int check_emulator_range(double a_init, double a_final, int solver) {
+    if ((solver & PM_SOLVER_GROWTH_EMULATOR) &&
+        !(growth_emulator_covers(0.3, a_init) && growth_emulator_covers(0.3, a_final)))
+        return fail(nullptr, PM_ERANGE, "the growth emulator covers a in [1e-3, 1]");
     return PM_OK;
 }
 
@@ -999,9 +1009,10 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
     if (!(c.box > 0)) return fail(nullptr, PM_EINVAL, "box must be > 0");
     if (!(c.a_init > 0 && c.a_final > c.a_init)) return fail(nullptr, PM_EINVAL, "need 0 < a_init < a_final");
     if (!(c.h > 0)) return fail(nullptr, PM_EINVAL, "h must be > 0");
-    if (c.solver & ~15) return fail(nullptr, PM_EINVAL, "unknown solver flag");
+    if (c.solver & ~31) return fail(nullptr, PM_EINVAL, "unknown solver flag");
     {
-        int rc = check_cosmology(nullptr, c.omega_m, c.sigma8, c.n_batch);
+        int rc = check_cosmology(nullptr, c.omega_m, c.sigma8, c.n_batch, c.solver);
+        if (!rc) rc = check_emulator_range(c.a_init, c.a_final, c.solver);
         if (rc) return rc;
     }
     const int64_t npart = (int64_t)c.n_p * c.n_p * c.n_p;
@@ -1173,7 +1184,7 @@ int pm_set_stream(pm_ctx *ctx, void *stream) {
 int pm_set_cosmology(pm_ctx *ctx, const double *omega_m, const double *sigma8) {
     if (!ctx) return fail(nullptr, PM_EINVAL, "ctx must not be NULL");
     DeviceGuard guard(ctx->device);
-    PM_TRY(check_cosmology(ctx, omega_m, sigma8, ctx->P.n_batch));
+    PM_TRY(check_cosmology(ctx, omega_m, sigma8, ctx->P.n_batch, ctx->P.solver));
     PM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->om.assign(omega_m, omega_m + ctx->P.n_batch);
     ctx->s8.assign(sigma8, sigma8 + ctx->P.n_batch);
@@ -1204,11 +1215,12 @@ int pm_host_coefficients(const pm_config *cfg, double *kdk, double *dkdk, double
     if (!cfg) return fail(nullptr, PM_EINVAL, "cfg must not be NULL");
     if (cfg->n_batch < 1 || cfg->n_steps < 1 || !(cfg->a_init > 0 && cfg->a_final > cfg->a_init))
         return fail(nullptr, PM_EINVAL, "bad n_batch, n_steps or a range");
+    if (cfg->solver & ~31) return fail(nullptr, PM_EINVAL, "unknown solver flag");
     {
-        int rc = check_cosmology(nullptr, cfg->omega_m, cfg->sigma8, cfg->n_batch);
+        int rc = check_cosmology(nullptr, cfg->omega_m, cfg->sigma8, cfg->n_batch, cfg->solver);
+        if (!rc) rc = check_emulator_range(cfg->a_init, cfg->a_final, cfg->solver);
         if (rc) return rc;
     }
-    if (cfg->solver & ~15) return fail(nullptr, PM_EINVAL, "unknown solver flag");
     Params P{cfg->n_p, cfg->n_m, cfg->n_batch, cfg->n_steps, cfg->box, cfg->a_init, cfg->a_final, cfg->h, cfg->n_s,
              cfg->solver};
     const int N = cfg->n_steps;

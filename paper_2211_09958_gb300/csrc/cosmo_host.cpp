@@ -18,7 +18,9 @@
 //   P(k) = A k^ns T_BBKS(k / (Om h))^2, A from the top-hat sigma8 integral.
 // Integration: classical RK4 in ln a with steps <= 1e-3; sigma8 integral:
 // composite Simpson in ln k over [1e-5, 1e3] h/Mpc, 10^4 intervals.
-// Om derivatives: central differences with dOm = 1e-5.
+// Om derivatives: central differences with dOm = 1e-5.  With solver flag 16
+// the growth quantities come from the growth-function emulator
+// (growth_emulator.cpp) instead of the ODE solve.
 
 #include <algorithm>
 #include <cmath>
@@ -122,6 +124,15 @@ double half_step_a(const Params &p, int n) {
 }
 
 namespace {
+// Growth quantities at a: the ODE solve, or with the emulator solver flag
+// (16) the growth-function emulator.
+void growth_values(const Params &p, double om, const std::vector<double> &a, std::vector<Growth> *out) {
+    if (p.solver & 16)
+        growth_emulated(om, a, out);
+    else
+        growth_at(om, a, out);
+}
+
 void kdk_factors(double om, const Params &p, std::vector<double> *ka, std::vector<double> *dr,
                  std::vector<double> *kb) {
     const int n_steps = p.n_steps;
@@ -131,7 +142,7 @@ void kdk_factors(double om, const Params &p, std::vector<double> *ka, std::vecto
     std::vector<double> all(a);
     all.insert(all.end(), ah.begin(), ah.end());
     std::vector<Growth> g;
-    growth_at(om, all, &g);
+    growth_values(p, om, all, &g);
     ka->resize(n_steps);
     dr->resize(n_steps);
     kb->resize(n_steps);
@@ -144,9 +155,12 @@ void kdk_factors(double om, const Params &p, std::vector<double> *ka, std::vecto
 }
 }  // namespace
 
-void lpt_factors(double om, double a_init, double out[4]) {
+void lpt_factors(double om, double a_init, double out[4], const Params *p) {
     std::vector<Growth> g;
-    growth_at(om, {a_init}, &g);
+    if (p)
+        growth_values(*p, om, {a_init}, &g);
+    else
+        growth_at(om, {a_init}, &g);
     out[0] = g[0].D1;
     out[1] = g[0].D2;
     out[2] = g[0].gp;
@@ -203,10 +217,10 @@ void host_tables(const Params &p, double om, double s8, HostTables *t) {
         t->ddr[n] = (dr_u[n] - dr_d[n]) / (2 * kFdOmega);
         t->dkb[n] = (kb_u[n] - kb_d[n]) / (2 * kFdOmega);
     }
-    lpt_factors(om, p.a_init, t->lpt);
+    lpt_factors(om, p.a_init, t->lpt, &p);
     double up[4], dn[4];
-    lpt_factors(om + kFdOmega, p.a_init, up);
-    lpt_factors(om - kFdOmega, p.a_init, dn);
+    lpt_factors(om + kFdOmega, p.a_init, up, &p);
+    lpt_factors(om - kFdOmega, p.a_init, dn, &p);
     for (int i = 0; i < 4; ++i) t->dlpt[i] = (up[i] - dn[i]) / (2 * kFdOmega);
     t->amp = power_amplitude(om, s8, p.h, p.n_s);
     t->dlnamp = (std::log(power_amplitude(om + kFdOmega, s8, p.h, p.n_s)) -

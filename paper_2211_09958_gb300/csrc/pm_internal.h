@@ -39,9 +39,14 @@ struct HostTables {
 
 double hubble_e(double a, double om);
 void growth_at(double om, const std::vector<double> &a, std::vector<Growth> *out);
+// Growth-function emulator (growth_emulator.cpp): Omega_m in [0.1, 0.6],
+// a in [1e-3, 1]; growth_emulated fills the same quantities as growth_at.
+bool growth_emulator_covers(double om, double a);
+void growth_emulate(double om, double a, double out[8]);
+void growth_emulated(double om, const std::vector<double> &a, std::vector<Growth> *out);
 void kdk_factors(double om, double a_init, double a_final, int n_steps, std::vector<double> *ka,
                  std::vector<double> *dr, std::vector<double> *kb);
-void lpt_factors(double om, double a_init, double out[4]);
+void lpt_factors(double om, double a_init, double out[4], const Params *p = nullptr);
 double bbks_transfer(double k, double om, double h);
 double power_amplitude(double om, double s8, double h, double ns);
 void host_tables(const Params &p, double om, double s8, HostTables *t);

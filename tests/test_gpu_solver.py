@@ -77,3 +77,31 @@ def test_loss_gradient_parity_with_all_flags(solver):
     assert abs(loss.item() - rl) <= 1e-4 * abs(rl)
     g = _host(nz.grad)[0]
     assert np.linalg.norm(g - rg) <= 1e-3 * np.linalg.norm(rg)
+
+
+def test_growth_emulator_run_against_oracle():
+    # the KDK and 2LPT tables from the growth emulator (solver flag 16) instead
+    # of the ODE solve: the run and its gradients still meet the default
+    # solver's parity bounds against the oracle (which solves the ODE), for
+    # a batch of cosmologies across the emulator's Omega_m range
+    from paper_2211_09958_gb300.pm import ParticleMesh, density, simulate
+    n_p, n_m, box, steps = 16, 32, 64.0, 6
+    om, s8 = [0.15, 0.3, 0.55], [0.7, 0.8, 0.9]
+    pm = ParticleMesh(n_p, n_m, box, om, s8, steps, solver=16)
+    noise = np.stack([inputs.white_noise(n_p, 700 + b) for b in range(3)])
+    target = np.stack([inputs.target_field(n_m, 800 + b) for b in range(3)])
+    nz = _cuda(noise).requires_grad_(True)
+    omt = torch.tensor(om, dtype=torch.float64, requires_grad=True)
+    s8t = torch.tensor(s8, dtype=torch.float64, requires_grad=True)
+    s, _ = simulate(pm, nz, omt, s8t)
+    losses = torch.mean((density(pm, s) - _cuda(target)) ** 2, dim=(1, 2, 3))
+    losses.sum().backward()
+    for b in range(3):
+        st = opm.Setup(n_p, n_m, box, Cosmology(om[b], s8[b]), n_steps=steps)
+        rs, _, _ = opm.simulate(noise[b].astype(np.float64), st)
+        assert np.max(np.abs(s[b].detach().cpu().numpy() - rs)) < 1e-4 * box / n_p, b
+        o_loss, o_gn, o_om, o_s8 = opm.loss_and_grad(noise[b].astype(np.float64), target[b].astype(np.float64), st)
+        g = nz.grad[b].cpu().numpy().astype(np.float64).ravel()
+        assert abs(losses[b].item() - o_loss) < 1e-4 * o_loss, b
+        assert np.linalg.norm(g - o_gn.ravel()) / np.linalg.norm(o_gn) < 1e-3, b
+        assert abs(s8t.grad[b].item() - o_s8) < 1e-3 * abs(o_s8), b

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 @pytest.mark.parametrize("field,value", [("n_p", 3), ("n_p", 15), ("n_p", 8192), ("n_m", 2), ("n_m", 8194),
                                          ("n_batch", 0), ("n_steps", 0), ("box", -1.0), ("box", float("nan")),
-                                         ("a_init", 2.0), ("a_final", 0.01), ("h", 0.0), ("solver", 16)])
+                                         ("a_init", 2.0), ("a_final", 0.01), ("h", 0.0), ("solver", 32)])
 def test_create_rejects_bad_config(lib, field, value):
     cfg = _pmgb.make_config(8, 16, 32.0, 0.3, 0.8, 4)
     setattr(cfg, field, value)
@@ -107,7 +107,7 @@ def test_log_a_tables_match_oracle(lib, steps):
 
 
 def test_unknown_solver_flag_is_rejected(lib):
-    cfg = _pmgb.make_config(32, 64, 128.0, [0.3], [0.8], 4, solver=16)
+    cfg = _pmgb.make_config(32, 64, 128.0, [0.3], [0.8], 4, solver=32)
     out = ctypes.c_void_p()
     assert lib.pm_create(ctypes.byref(cfg), ctypes.byref(out)) == -1
     assert b"solver" in lib.pm_last_error(None)
