@@ -666,15 +666,14 @@ int ensure_nn(pm_ctx *ctx) {
         return fail(ctx, PM_ENOMEM, "cannot allocate the learned-correction buffers");
     }
     ctx->nnw = nn_carve(ctx->nn_packed);
-    PM_CUDA(ctx, nn_prepare());
     PM_CUDA(ctx, nn_tc_prepare());
     return PM_OK;
 }
 
 NNArgs nn_args(pm_ctx *ctx, double a) {
     NNArgs na{};
-    na.w = NNWeights{ctx->nnw.w1t, ctx->nnw.w2t, ctx->nnw.w2n, ctx->nnw.w3t, ctx->nnw.w3n, ctx->nnw.b1,
-                     ctx->nnw.b2,  ctx->nnw.b3,  ctx->nnw.w1c, ctx->nnw.w2c, ctx->nnw.w3c, ctx->nnw.w1n};
+    na.w = NNWeights{ctx->nnw.w1c, ctx->nnw.w2c, ctx->nnw.w3c, ctx->nnw.w1b,
+                     ctx->nnw.w2b, ctx->nnw.w3b, ctx->nnw.b1,  ctx->nnw.b2, ctx->nnw.b3};
     na.err = ctx->nn_err;
     na.feat = ctx->nn_feat;
     na.n = ctx->P.n_m;
@@ -730,13 +729,14 @@ int apply_correction(pm_ctx *ctx, double a) {
 int correction_adjoint(pm_ctx *ctx, double a, int kick_step, int kick_sel) {
     const int64_t cells = nn_cells(ctx);
     NNArgs na = nn_args(ctx, a);
-    if (!na.w.w1n || !ctx->nn_mesh4 || !ctx->nn_gx || kick_step < 0 || kick_step >= ctx->P.n_steps)
+    if (!na.w.w1b || !ctx->nn_mesh4 || !ctx->nn_gx || kick_step < 0 || kick_step >= ctx->P.n_steps)
         return fail(ctx, PM_ESTATE, "learned-correction adjoint buffers are not set up");
     na.rho = ctx->r4;
     na.rho_stride = 4;
     na.out = ctx->nn_mesh4;
     na.accumulate = 0;
-    PM_LAUNCH(ctx, "nn_fwd_train", launch_nn_fwd(na, cells, true, ctx->stream));
+    PM_LAUNCH(ctx, "nn_feat", launch_nn_feat(ctx->r4, ctx->nn_feat, cells, ctx->stream, 4));
+    PM_LAUNCH(ctx, "nn_fwd_train", launch_nn_fwd_tc(na, cells, ctx->stream, true));
     na.gmesh = ctx->r4;
     na.table = ctx->d_table;
     na.kick_step = kick_step;
@@ -757,12 +757,8 @@ int nn_forward_at(pm_ctx *ctx, const float *s, double a, bool train) {
     pa.mesh = dref;
     PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
     NNArgs na = nn_args(ctx, a);
-    if (train)
-        PM_LAUNCH(ctx, "nn_fwd_train", launch_nn_fwd(na, nn_cells(ctx), true, ctx->stream));
-    else {
-        PM_LAUNCH(ctx, "nn_feat", launch_nn_feat(ctx->r1, ctx->nn_feat, nn_cells(ctx), ctx->stream));
-        PM_LAUNCH(ctx, "nn_fwd_tc", launch_nn_fwd_tc(na, nn_cells(ctx), ctx->stream));
-    }
+    PM_LAUNCH(ctx, "nn_feat", launch_nn_feat(ctx->r1, ctx->nn_feat, nn_cells(ctx), ctx->stream));
+    PM_LAUNCH(ctx, (train ? "nn_fwd_train" : "nn_fwd_tc"), launch_nn_fwd_tc(na, nn_cells(ctx), ctx->stream, train));
     return PM_OK;
 }
 

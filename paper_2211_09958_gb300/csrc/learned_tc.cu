@@ -16,6 +16,8 @@
 // (A1 is the first 8 KB of A2: the L1 MMAs have finished reading it before
 // the h1 epilogue writes there.)
 //   out[cell][j] (+)= s_out (D3[j] + b3[j]), j < 3
+// Training (TRAIN) also stores the features x and the activations h1, h2 as
+// row-major bf16 rows [cells][32 | 128] for the backward pass.
 // Operands sit in shared memory in the no-swizzle K-major core-matrix layout
 // (nn_cm_index).  A persistent block stages the weights once and runs PIPES
 // independent tile pipelines of 8 warps (own A buffer, TMEM columns,
@@ -178,7 +180,7 @@ __device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
 // as two 16-byte core-matrix rows at dst and dst + M * 16.
 template <int HALF>
 __device__ __forceinline__ void feature_rows(const unsigned short *f, int64_t c, int n, unsigned short afeat,
-                                             char *dst) {
+                                             char *dst, bf16 *xg_row) {
     const int x = (int)(c / ((int64_t)n * n)), y = (int)((c / n) % n), z = (int)(c % n);
     const int xs[3] = {x == 0 ? n - 1 : x - 1, x, x == n - 1 ? 0 : x + 1};
     const int ys[3] = {y == 0 ? n - 1 : y - 1, y, y == n - 1 ? 0 : y + 1};
@@ -201,6 +203,8 @@ __device__ __forceinline__ void feature_rows(const unsigned short *f, int64_t c,
         }
         // the next 8 columns are the next K-direction core matrix, M * 16 bytes on
         *reinterpret_cast<uint4 *>(dst + chunk * M * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+        if (xg_row)  // training: the features, row-major, for the first layer's weight gradient
+            *reinterpret_cast<uint4 *>(xg_row + 16 * HALF + 8 * chunk) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
@@ -213,8 +217,10 @@ __device__ __forceinline__ void mma_chain(uint32_t d_tmem, uint32_t a_base, uint
 }
 
 // 64 columns [c0, c0 + 64) of a 128-wide accumulator for this thread's row:
-// + bias, ReLU, bf16, into the A2 operand (row `row`, columns c0 ..).
-__device__ __forceinline__ void relu_to_a2(uint32_t taddr, const float *bias, int c0, int row, char *a2) {
+// + bias, ReLU, bf16, into the A2 operand (row `row`, columns c0 ..); in
+// training also into the row-major activation row h_row (global).
+__device__ __forceinline__ void relu_to_a2(uint32_t taddr, const float *bias, int c0, int row, char *a2,
+                                           bf16 *h_row) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         float v[32];
@@ -228,10 +234,12 @@ __device__ __forceinline__ void relu_to_a2(uint32_t taddr, const float *bias, in
             u.z = pack2_relu(v[8 * q + 4] + bias[c + 4], v[8 * q + 5] + bias[c + 5]);
             u.w = pack2_relu(v[8 * q + 6] + bias[c + 6], v[8 * q + 7] + bias[c + 7]);
             *reinterpret_cast<uint4 *>(a2 + 2 * nn_cm_index(row, c, M)) = u;
+            if (h_row) *reinterpret_cast<uint4 *>(h_row + c) = u;
         }
     }
 }
 
+template <bool TRAIN>
 __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t tiles) {
     extern __shared__ __align__(1024) char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -287,10 +295,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t til
             const int64_t c = cell0 - run * n3 + cl;
             const unsigned short *f = reinterpret_cast<const unsigned short *>(a.feat) + run * n3;
             const unsigned short afeat = __bfloat16_as_ushort(__float2bfloat16_rn(a.afeat));
+            bf16 *xrow = TRAIN ? a.xg + (cell0 + cl) * NI : nullptr;
             if (tp < M)
-                feature_rows<0>(f, c, n, afeat, abuf + 2 * nn_cm_index(cl, 0, M));
+                feature_rows<0>(f, c, n, afeat, abuf + 2 * nn_cm_index(cl, 0, M), xrow);
             else
-                feature_rows<1>(f, c, n, afeat, abuf + 2 * nn_cm_index(cl, 16, M));
+                feature_rows<1>(f, c, n, afeat, abuf + 2 * nn_cm_index(cl, 16, M), xrow);
         }
         fence_async_smem();
         fence_before();
@@ -303,7 +312,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t til
         }
         ok = wait_all(bar, phase, tp, pipe);
         if (!ok) break;
-        relu_to_a2(lane_base, bias, 64 * colhalf, row, abuf);
+        relu_to_a2(lane_base, bias, 64 * colhalf, row, abuf, TRAIN ? a.h1g + (cell0 + row) * NH : nullptr);
         fence_async_smem();
         fence_before();
         pipe_sync(pipe);
@@ -315,7 +324,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t til
         }
         ok = wait_all(bar, phase, tp, pipe);
         if (!ok) break;
-        relu_to_a2(lane_base, bias + NH, 64 * colhalf, row, abuf);
+        relu_to_a2(lane_base, bias + NH, 64 * colhalf, row, abuf, TRAIN ? a.h2g + (cell0 + row) * NH : nullptr);
         fence_async_smem();
         fence_before();
         pipe_sync(pipe);
@@ -355,10 +364,382 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t til
     }
 }
 
-// Feature mesh: bf16(asinh(rho - 1)) per cell, four cells a thread.
-__global__ void k_nn_feat(const float4 *__restrict__ rho, uint2 *__restrict__ feat, int64_t n4) {
+// ------------------------------------------------------ backward pass ---
+//
+// From the output cotangent to the activation cotangents, per 128-cell tile,
+// with the same pipelines, TMEM columns and bounded waits as the forward:
+//   gy = bf16(c s_out u)  -> smem A (128 x 16; columns 3.. zero), g3 row
+//   D = gy W3             (N = 128: B[i][o] = W3[i][o], o < 3)
+//   g2 = D [h2 > 0]       -> smem A (128 x 128), g2 row
+//   D = g2 W2^T           (N = 128: B[i][o] = W2[i][o])
+//   g1 = D [h1 > 0]       -> smem A, g1 row
+//   D = g1 W1^T           (N = 32: B[f][o] = W1[f][o]) -> g_x row (FP32), when wanted
+// u is slots 1..3 of the interleaved gradient mesh and c the run's kick
+// factor.  The bias gradients are column sums of g3, g2 and g1 over the
+// cells: each warp sums its 32 rows of a 32-column block by a transposing
+// butterfly (lane l ends with column l), kept in registers across the tiles
+// and added to the global FP32 gradient once per thread at the end.
+constexpr int OFF_V2 = 0;                          // W2 as [in][out], 128 x 128
+constexpr int OFF_V3 = OFF_V2 + NH * NH * 2;       // W3 as [hidden][out], 128 x 16
+constexpr int OFF_V1 = OFF_V3 + NH * N3 * 2;       // W1 as [feature][hidden], 32 x 128
+constexpr int OFF_BA = OFF_V1 + NI * NH * 2;       // PIPES x A (128 x 128), gy aliased at its start
+constexpr int OFF_BBAR = OFF_BA + PIPES * A_BYTES;
+constexpr int OFF_BTMEM = OFF_BBAR + 8 * PIPES;
+constexpr int BWD_SMEM = OFF_BTMEM + 8;
+static_assert(OFF_V3 % 128 == 0 && OFF_V1 % 128 == 0 && OFF_BA % 128 == 0, "alignment");
+static_assert(2 * (BWD_SMEM + 1024) <= 228 * 1024, "two blocks per SM");
+
+// Column sums of a warp's 32 rows x 32 columns (v: this lane's row): lane l
+// returns the sum of column l.  31 shuffles.
+__device__ __forceinline__ float column_sums32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool upper = (lane & s) != 0;  // keep columns [s, 2s) of the current block, send [0, s)
+#pragma unroll
+        for (int j = 0; j < s; ++j) {
+            const float send = upper ? v[j] : v[j + s];
+            const float keep = upper ? v[j + s] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0];
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ uint32_t pack2_rn(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// 64 columns [c0, c0 + 64) of this thread's accumulator row, masked by the
+// stored activation row (h > 0): bf16 into the A operand (when a_op) and the
+// global cotangent row g_row; the warp's column sums of the FP32 masked
+// values added to gsum[0..1] (lane l: columns c0 + l and c0 + 32 + l).
+__device__ __forceinline__ void masked_to_a(uint32_t taddr, int c0, int row, char *a_op, const bf16 *h_row,
+                                            bf16 *g_row, float (&gsum)[2], int lane) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float v[32];
+        tmem_ld32(taddr + c0 + 32 * h, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = c0 + 32 * h + 8 * q;
+            const uint4 hv = *reinterpret_cast<const uint4 *>(h_row + c);
+            const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {  // bf16 h > 0: sign bit clear and not +0
+                if ((hw[e] & 0x8000u) || !(hw[e] & 0x7fffu)) v[8 * q + 2 * e] = 0.f;
+                if ((hw[e] & 0x80000000u) || !(hw[e] & 0x7fff0000u)) v[8 * q + 2 * e + 1] = 0.f;
+            }
+            uint4 u;
+            u.x = pack2_rn(v[8 * q + 0], v[8 * q + 1]);
+            u.y = pack2_rn(v[8 * q + 2], v[8 * q + 3]);
+            u.z = pack2_rn(v[8 * q + 4], v[8 * q + 5]);
+            u.w = pack2_rn(v[8 * q + 6], v[8 * q + 7]);
+            if (a_op) *reinterpret_cast<uint4 *>(a_op + 2 * nn_cm_index(row, c, M)) = u;
+            *reinterpret_cast<uint4 *>(g_row + c) = u;
+        }
+        gsum[h] += column_sums32(v, lane);
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 2) k_mlp_bwd_tc(NNArgs a, int64_t tiles) {
+    extern __shared__ __align__(1024) char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int pipe = tid / PT, tp = tid % PT;
+    const int quarter = warp & 3, colhalf = (warp >> 2) & 1;
+    const int row = 32 * quarter + lane;
+    const uint32_t bar = smem_u32(sm + OFF_BBAR + 8 * pipe);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_BTMEM);
+    {
+        const int4 *src[3] = {reinterpret_cast<const int4 *>(a.w.w2b), reinterpret_cast<const int4 *>(a.w.w3b),
+                              reinterpret_cast<const int4 *>(a.w.w1b)};
+        const int off[3] = {OFF_V2, OFF_V3, OFF_V1}, n16[3] = {NH * NH / 8, NH * N3 / 8, NI * NH / 8};
+        for (int m = 0; m < 3; ++m)
+            for (int k = tid; k < n16[m]; k += THREADS) reinterpret_cast<int4 *>(sm + off[m])[k] = src[m][k];
+    }
+    if (tp == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tcol = *tslot + 128 * pipe;
+    const uint32_t lane_base = tcol + ((uint32_t)(32 * quarter) << 16);
+    char *abuf = sm + OFF_BA + pipe * A_BYTES;
+    const uint32_t sA = smem_u32(abuf);
+    const uint32_t sV2 = smem_u32(sm + OFF_V2), sV3 = smem_u32(sm + OFF_V3), sV1 = smem_u32(sm + OFF_V1);
+
+    const int64_t n3 = (int64_t)a.n * a.n * a.n;
+    float gs3[NO] = {0.f, 0.f, 0.f}, gs2[2] = {0.f, 0.f}, gs1[2] = {0.f, 0.f};
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int64_t tile = (int64_t)blockIdx.x * PIPES + pipe; tile < tiles && ok; tile += (int64_t)gridDim.x * PIPES) {
+        const int64_t cell0 = tile * M, cell = cell0 + row;
+        const int64_t run = cell0 / n3;
+        if (colhalf == 0) {  // output cotangent of this thread's cell
+            const float s_out = a.pref[run] * a.s_scale * nn_kick_coef(a, run);
+            const float4 u = *reinterpret_cast<const float4 *>(a.gmesh + cell * 4);
+            const uint32_t g01 = pack2_rn(s_out * u.y, s_out * u.z), g2 = pack2_rn(s_out * u.w, 0.f);
+            const uint4 r0 = make_uint4(g01, g2, 0u, 0u);
+            *reinterpret_cast<uint4 *>(abuf + 2 * nn_cm_index(row, 0, M)) = r0;
+            *reinterpret_cast<uint4 *>(abuf + 2 * nn_cm_index(row, 8, M)) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(a.g3g + cell * 8) = r0;
+            float gq[NO] = {__uint_as_float(g01 << 16), __uint_as_float(g01 & 0xffff0000u), __uint_as_float(g2 << 16)};
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+#pragma unroll
+                for (int o = 16; o; o >>= 1) gq[j] += __shfl_xor_sync(0xffffffffu, gq[j], o);
+                gs3[j] += gq[j];
+            }
+        }
+        fence_async_smem();
+        fence_before();
+        pipe_sync(pipe);
+        if (tp == 0) {
+            fence_after();
+            mma_chain(tcol, sA, sV3, N3, NH);
+            mma_commit(bar);
+        }
+        ok = wait_all(bar, phase, tp, pipe);
+        if (!ok) break;
+        masked_to_a(lane_base, 64 * colhalf, row, abuf, a.h2g + cell * NH, a.g2g + cell * NH, gs2, lane);
+        fence_async_smem();
+        fence_before();
+        pipe_sync(pipe);
+        if (tp == 0) {
+            fence_after();
+            mma_chain(tcol, sA, sV2, NH, NH);
+            mma_commit(bar);
+        }
+        ok = wait_all(bar, phase, tp, pipe);
+        if (!ok) break;
+        masked_to_a(lane_base, 64 * colhalf, row, a.gx ? abuf : nullptr, a.h1g + cell * NH, a.g1g + cell * NH,
+                    gs1, lane);
+        if (a.gx) {
+            fence_async_smem();
+            fence_before();
+            pipe_sync(pipe);
+            if (tp == 0) {
+                fence_after();
+                mma_chain(tcol, sA, sV1, NH, NI);
+                mma_commit(bar);
+            }
+            ok = wait_all(bar, phase, tp, pipe);
+            if (!ok) break;
+            float v[16];
+            tmem_ld16(lane_base + 16 * colhalf, v);
+            float4 *dst = reinterpret_cast<float4 *>(a.gx + cell * NI + 16 * colhalf);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        fence_before();
+        pipe_sync(pipe);
+        fence_after();
+    }
+    if (!ok && tp == 0) {
+        atomicExch(a.err, 1);
+        bar_wait(bar, phase ^ 1);
+    }
+    if (ok) {
+        const int c = 64 * colhalf + lane;
+        atomicAdd(a.gb2 + c, gs2[0]);
+        atomicAdd(a.gb2 + c + 32, gs2[1]);
+        atomicAdd(a.gb1 + c, gs1[0]);
+        atomicAdd(a.gb1 + c + 32, gs1[1]);
+        if (colhalf == 0 && lane == 0)
+            for (int j = 0; j < NO; ++j) atomicAdd(a.gb3 + j, gs3[j]);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------ weight gradients ---
+//
+// dW = sum over cells of a_c (x) b_c for one layer, on the tensor cores:
+// D[i][j] += sum_k A[i][k] B[j][k] with i the 128 units of the activation
+// (or cotangent) side, j the N units of the other side and k the cells, one
+// tcgen05.mma chain (K = 128 cells, 8 MMAs of K = 16) per chunk of 128
+// cells, accumulating in TMEM across all the chunks a block takes.
+//   dW2 = h1^T g2:  A = h1 [cells][128], B = g2 [cells][128], N = 128
+//   dW3 = h2^T g3:  A = h2, B = g3 [cells][8] (3 valid; zero to N = 16)
+//   dW1^T = g1^T x: A = g1, B = x [cells][32], N = 32; stored transposed
+// The [cells][units] rows arrive with coalesced 16-byte loads in a natural
+// [cell][unit] buffer, and each thread then gathers 8 cells of one unit into
+// one 16-byte row of the K-major core-matrix layout (element (i, k) at
+// nn_cm_index(i, k, 128)); two operand stages, so that one chunk is staged
+// while the MMAs of the previous one run.  At the
+// end each thread reads its TMEM lane (unit i) and adds its columns to the
+// FP32 gradient in global memory.  Waits are bounded as in k_mlp_fwd_tc.
+constexpr int WG_THREADS = 256;
+constexpr int WG_K = 128;  // cells per chunk
+
+template <int N>
+struct WgShape {
+    static constexpr int A_BYTES = M * WG_K * 2, B_BYTES = N * WG_K * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int OFF_NAT = 2 * STAGE;                 // natural [cell][unit] landing buffer
+    static constexpr int OFF_BAR = OFF_NAT + M * WG_K * 2, OFF_TMEM = OFF_BAR + 16, SMEM = OFF_TMEM + 8;
+    static constexpr uint32_t COLS = N < 32 ? 32 : N;  // TMEM allocation: a power of two >= 32
+};
+
+// rows [c0, c0 + 128) of src ([cells][ld] bf16) -> nat [128][ld], coalesced 16-byte copies
+__device__ __forceinline__ void wg_land(const bf16 *src, int ld, int64_t c0, char *nat, int tid) {
+    const int n16 = WG_K * ld / 8;
+    const uint4 *g = reinterpret_cast<const uint4 *>(src + c0 * ld);
+    for (int e = tid; e < n16; e += WG_THREADS) reinterpret_cast<uint4 *>(nat)[e] = __ldg(g + e);
+}
+
+// nat [128 cells][ld units] -> K-major core matrices of R rows (units; rows
+// >= ld are zero): thread (unit j, cells 8 kb .. 8 kb + 7) writes one 16-byte row.
+template <int R>
+__device__ __forceinline__ void wg_transpose(const char *nat, int ld, char *dst, int tid) {
+    const unsigned short *src = reinterpret_cast<const unsigned short *>(nat);
+    for (int e = tid; e < R * (WG_K / 8); e += WG_THREADS) {
+        const int j = e % R, kb = e / R;
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t lo = j < ld ? src[(8 * kb + 2 * q) * ld + j] : 0u;
+            const uint32_t hi = j < ld ? src[(8 * kb + 2 * q + 1) * ld + j] : 0u;
+            w[q] = lo | (hi << 16);
+        }
+        *reinterpret_cast<uint4 *>(dst + 2 * nn_cm_index(j, 8 * kb, R)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(WG_THREADS, 1)
+    k_wgrad_tc(const bf16 *__restrict__ A, const bf16 *__restrict__ B, int ldb, int64_t chunks, float *out,
+               int ldo, int nvalid, int transposed, int *err) {
+    using S = WgShape<N>;
+    extern __shared__ __align__(1024) char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar0 = smem_u32(sm + S::OFF_BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + S::OFF_TMEM);
+    if (tid == 0) {
+        for (int st = 0; st < 2; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * st) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(S::COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tcol = *tslot;
+    uint32_t phase[2] = {0, 0};
+    int issued[2] = {0, 0};
+    bool ok = true;
+    int64_t it = 0;
+    for (int64_t ch = blockIdx.x; ch < chunks && ok; ch += gridDim.x, ++it) {
+        const int st = (int)(it & 1);
+        const uint32_t bar = bar0 + 8 * st;
+        if (issued[st]) {  // the MMAs that read this stage two chunks ago must be done
+            const int good = tid == 0 ? (int)bar_wait(bar, phase[st]) : 1;
+            ok = __syncthreads_and(good) != 0;
+            phase[st] ^= 1;
+            issued[st] = 0;
+            if (!ok) break;
+        }
+        char *sa = sm + st * S::STAGE, *sb = sa + S::A_BYTES, *nat = sm + S::OFF_NAT;
+        const int64_t c0 = ch * WG_K;
+        wg_land(A, M, c0, nat, tid);
+        __syncthreads();
+        wg_transpose<M>(nat, M, sa, tid);
+        __syncthreads();
+        wg_land(B, ldb, c0, nat, tid);
+        __syncthreads();
+        wg_transpose<N>(nat, ldb, sb, tid);
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            const uint32_t lbo_a = (M / 8) * 128, lbo_b = (uint32_t)(N / 8) * 128;
+            const uint32_t a_base = smem_u32(sa), b_base = smem_u32(sb);
+            for (int kk = 0; kk < WG_K / 16; ++kk)
+                mma_f16(tcol, sdesc(a_base + 2 * kk * lbo_a, lbo_a, 128), sdesc(b_base + 2 * kk * lbo_b, lbo_b, 128),
+                        idesc(N), (it > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(bar);
+        }
+        issued[st] = 1;
+    }
+    // drain both stages
+    for (int st = 0; st < 2; ++st) {
+        if (!issued[st]) continue;
+        const int good = tid == 0 ? (int)bar_wait(bar0 + 8 * st, phase[st]) : 1;
+        ok = (__syncthreads_and(good) != 0) && ok;
+        phase[st] ^= 1;
+    }
+    fence_after();
+    if (ok && it > 0 && warp < 4) {  // warp w reads TMEM lanes 32 w .. 32 w + 31 (units i)
+        const int i = 32 * warp + lane;
+        const uint32_t lane_base = tcol + ((uint32_t)(32 * warp) << 16);
+        for (int c = 0; c < N; c += 32) {
+            float v[32];
+            if (N >= 32) {
+                tmem_ld32(lane_base + c, v);
+            } else {
+                float v4[4];
+#pragma unroll
+                for (int q = 0; q < N / 4; ++q) {
+                    tmem_ld4(lane_base + 4 * q, v4);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) v[4 * q + r] = v4[r];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < (N < 32 ? N : 32); ++j)
+                if (c + j < nvalid) atomicAdd(transposed ? out + (c + j) * ldo + i : out + i * ldo + c + j, v[j]);
+        }
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tcol), "r"(S::COLS) : "memory");
+    }
+}
+
+// Feature mesh: bf16(asinh(rho - 1)) per cell, four cells a thread; rho
+// every `stride`-th float (1: a plain mesh; 4: slot 0 of the adjoint's
+// interleaved paint).
+__global__ void k_nn_feat(const float *__restrict__ rho, int stride, uint2 *__restrict__ feat, int64_t n4) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 r = rho[i];
+        const float4 r = stride == 1 ? reinterpret_cast<const float4 *>(rho)[i]
+                                     : make_float4(rho[16 * i], rho[16 * i + 4], rho[16 * i + 8], rho[16 * i + 12]);
         const __nv_bfloat162 lo = __floats2bfloat162_rn(asinhf(r.x - 1.f), asinhf(r.y - 1.f));
         const __nv_bfloat162 hi = __floats2bfloat162_rn(asinhf(r.z - 1.f), asinhf(r.w - 1.f));
         feat[i] = make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
@@ -367,22 +748,66 @@ __global__ void k_nn_feat(const float4 *__restrict__ rho, uint2 *__restrict__ fe
 
 }  // namespace
 
-cudaError_t launch_nn_feat(const float *rho, __nv_bfloat16 *feat, int64_t cells, cudaStream_t st) {
+cudaError_t launch_nn_feat(const float *rho, __nv_bfloat16 *feat, int64_t cells, cudaStream_t st, int stride) {
+    if (stride != 1 && stride != 4) return cudaErrorInvalidValue;
     const int64_t n4 = cells / 4, blocks = (n4 + 255) / 256;
-    k_nn_feat<<<(unsigned)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(
-        reinterpret_cast<const float4 *>(rho), reinterpret_cast<uint2 *>(feat), n4);
+    k_nn_feat<<<(unsigned)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(rho, stride,
+                                                                              reinterpret_cast<uint2 *>(feat), n4);
     return cudaGetLastError();
 }
 
 cudaError_t nn_tc_prepare() {
-    return cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_mlp_fwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_mlp_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_mlp_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, BWD_SMEM)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_wgrad_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  WgShape<128>::SMEM)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_wgrad_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  WgShape<32>::SMEM)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_wgrad_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  WgShape<16>::SMEM)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
 }
 
-cudaError_t launch_nn_fwd_tc(const NNArgs &a, int64_t cells, cudaStream_t st) {
+// The three weight gradients of one training step on the tensor cores,
+// from the activations the training forward stored (x, h1, h2) and the
+// cotangents the backward stored (g1, g2, g3); added to a.grad.
+cudaError_t launch_nn_wgrad_tc(const NNArgs &a, int64_t cells, cudaStream_t st) {
+    const int64_t chunks = cells / WG_K;
+    const unsigned grid = (unsigned)(chunks < 152 ? chunks : 152);
+    float *dW1 = a.grad, *dW2 = dW1 + NI * NH + NH, *dW3 = dW2 + NH * NH + NH;
+    k_wgrad_tc<128><<<grid, WG_THREADS, WgShape<128>::SMEM, st>>>(a.h1g, a.g2g, NH, chunks, dW2, NH, NH, 0, a.err);
+    k_wgrad_tc<16><<<grid, WG_THREADS, WgShape<16>::SMEM, st>>>(a.h2g, a.g3g, 8, chunks, dW3, NO, NO, 0, a.err);
+    k_wgrad_tc<32><<<grid, WG_THREADS, WgShape<32>::SMEM, st>>>(a.g1g, a.xg, NI, chunks, dW1, NH, NI, 1, a.err);
+    return cudaGetLastError();
+}
+
+// Backward of one training step: activation cotangents, bias gradients and
+// (a.gx) the feature cotangent, then the weight gradients.
+cudaError_t launch_nn_bwd(const NNArgs &a, int64_t cells, cudaStream_t st) {
+    const int64_t tiles = cells / M;
+    const int64_t want = (tiles + PIPES - 1) / PIPES;
+    const int64_t cap = 2 * 152;
+    k_mlp_bwd_tc<<<(unsigned)(want < cap ? want : cap), THREADS, BWD_SMEM, st>>>(a, tiles);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_nn_wgrad_tc(a, cells, st);
+}
+
+cudaError_t launch_nn_fwd_tc(const NNArgs &a, int64_t cells, cudaStream_t st, bool train) {
     const int64_t tiles = cells / M;
     const int64_t want = (tiles + PIPES - 1) / PIPES;
     const int64_t cap = 2 * 152;  // two blocks per SM: 2 x 256 TMEM columns, 2 x ~109 KB shared memory
-    k_mlp_fwd_tc<<<(unsigned)(want < cap ? want : cap), THREADS, SMEM_BYTES, st>>>(a, tiles);
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    if (train)
+        k_mlp_fwd_tc<true><<<grid, THREADS, SMEM_BYTES, st>>>(a, tiles);
+    else
+        k_mlp_fwd_tc<false><<<grid, THREADS, SMEM_BYTES, st>>>(a, tiles);
     return cudaGetLastError();
 }
 

@@ -243,17 +243,17 @@ cudaError_t launch_lpt_adj_final(const Spec &sp, const LinParams *lp, int f_nois
 
 constexpr int NN_IN = 32, NN_HID = 128, NN_OUT = 3;
 
-struct NNWeights {  // packed bf16 operands and FP32 biases (learned.cu)
-    const __nv_bfloat16 *w1t, *w2t, *w2n, *w3t, *w3n;
+// Packed bf16 tensor-core (tcgen05) operands, K-major core-matrix layout
+// (nn_cm_index), and FP32 biases (learned.cu):
+//   forward  (rows = outputs, K = inputs)  w1c [128][32], w2c [128][128], w3c [16][128]
+//   backward (rows = inputs, K = outputs)  w1b [32][128], w2b [128][128], w3b [128][16]
+struct NNWeights {
+    const __nv_bfloat16 *w1c, *w2c, *w3c, *w1b, *w2b, *w3b;
     const float *b1, *b2, *b3;
-    const __nv_bfloat16 *w1c, *w2c, *w3c;  // tensor-core (tcgen05) operand layouts
-    const __nv_bfloat16 *w1n;              // [32][136] W1 as [feature][hidden] (input gradient)
 };
 struct NNWeightsMut {
-    __nv_bfloat16 *w1t, *w2t, *w2n, *w3t, *w3n;
+    __nv_bfloat16 *w1c, *w2c, *w3c, *w1b, *w2b, *w3b;
     float *b1, *b2, *b3;
-    __nv_bfloat16 *w1c, *w2c, *w3c;
-    __nv_bfloat16 *w1n;
 };
 
 // Element index of (row r, column k) of an R x K bf16 operand stored as
@@ -288,16 +288,32 @@ struct NNArgs {
     float *gx;
 };
 
+#ifdef __CUDACC__
+// The kick factor that scales run `run`'s output cotangent (1 without a table).
+__device__ __forceinline__ float nn_kick_coef(const NNArgs &a, int64_t run) {
+    if (!a.table) return 1.f;
+    const float4 t = a.table[(int64_t)a.kick_step * a.nb + run];
+    return a.kick_sel == KICK_A ? t.x : (a.kick_sel == KICK_B ? t.z : t.w);
+}
+#endif
+
 int nn_param_count();
-cudaError_t nn_prepare();  // kernel attributes; call once before any capture
 size_t nn_packed_bytes();
 NNWeightsMut nn_carve(void *base);
 cudaError_t launch_nn_pack(const float *theta, const NNWeightsMut &w, cudaStream_t st);
-cudaError_t launch_nn_fwd(const NNArgs &a, int64_t cells, bool train, cudaStream_t st);
+// Backward of one training step on the tensor cores: activation cotangents
+// g3, g2, g1 (and the feature cotangent a.gx when set), bias gradients, then
+// the weight gradients; needs the activations of the training forward.
 cudaError_t launch_nn_bwd(const NNArgs &a, int64_t cells, cudaStream_t st);
+// The weight gradients of one training step on the tensor cores (tcgen05):
+// dW1 += x^T g1, dW2 += h1^T g2, dW3 += h2^T g3 over all cells.
+cudaError_t launch_nn_wgrad_tc(const NNArgs &a, int64_t cells, cudaStream_t st);
 cudaError_t nn_tc_prepare();
-cudaError_t launch_nn_feat(const float *rho, __nv_bfloat16 *feat, int64_t cells, cudaStream_t st);
-cudaError_t launch_nn_fwd_tc(const NNArgs &a, int64_t cells, cudaStream_t st);
+// bf16(asinh(rho - 1)) per cell; rho every `stride`-th float (1 or 4).
+cudaError_t launch_nn_feat(const float *rho, __nv_bfloat16 *feat, int64_t cells, cudaStream_t st, int stride = 1);
+// The network on the tensor cores (tcgen05) from the feature mesh a.feat;
+// train = also store x, h1, h2 (a.xg, a.h1g, a.h2g) for the backward pass.
+cudaError_t launch_nn_fwd_tc(const NNArgs &a, int64_t cells, cudaStream_t st, bool train = false);
 cudaError_t launch_nn_residual(float *pred, const float *target, int64_t n, float scale, double *loss,
                                cudaStream_t st);
 cudaError_t launch_adam(float *theta, float *grad, float *m, float *v, int np, float lr, float b1, float b2, float eps,
