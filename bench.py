@@ -138,6 +138,18 @@ def algorithmic_bytes(kind, npart, ncell, nmodes, pot_read=False):
         "grad_stencil_1": (4 + 16) * ncell,                  # phi in; (F, 0) float4 out
         "grad_stencil_2": (8 + 16) * ncell,                  # (phi, psi) in; (F, psi) out
         "vjp_source": (16 + 8) * ncell,                      # (rho, u) float4 in; (rho, v) out
+        # binned deposit: binning (s in, tile and rank out; then the CSR
+        # scatter), the tile-owned paint (the paint's own bytes: particles in,
+        # every cell out once) and the halo pass (33 of 256 cells' halo lines
+        # in; the 31 x = 0 / y = 0 lines of 256 read and written)
+        "bin_count": 20 * npart,
+        "bin_scan_sums": 4 * (ncell // 4096),
+        "bin_scan": 12 * (ncell // 4096),
+        "bin_scatter": 12 * npart,
+        "deposit_density": 12 * npart + 4 * ncell,
+        "deposit_adj": 24 * npart + 16 * ncell,
+        "deposit_halo_1": (33 * 4 + 31 * 8) * ncell // 256,
+        "deposit_halo_4": (33 * 16 + 31 * 32) * ncell // 256,
     }
     # own FFT passes: kind "fft_<axis>_<dir>_<fields>"
     if kind.startswith("fft_"):

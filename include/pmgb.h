@@ -383,7 +383,15 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  * [8 (phi(c + e_j) - phi(c - e_j)) - (phi(c + 2 e_j) - phi(c - 2 e_j))] / 12h,
  * whose Fourier symbol is i D_j: the same linear map with two fewer inverse
  * transforms per evaluation; default 2 (1 with the spectral-gradient flag,
- * which has no stencil form).
+ * which has no stencil form).  [9] is the mass assignment into the own
+ * transform's meshes: 1 zero the mesh, then one thread per particle adds
+ * its weights with global float atomics; 2 bin the particles by the
+ * 16^3-cell tile of their base cell (counting sort), then one block per
+ * 16 x 16 column of tiles sums its particles in shared memory and writes
+ * every cell of the column once, with the faces shared between columns
+ * added by a second pass.  2 is the default where it applies (own
+ * transform, CIC, n_m a multiple of 16, n_batch n_p^3 < 2^31), else 1;
+ * where it does not apply, 2 also runs as 1.
  *
  * pm_autotune     times every candidate of each family in turn (the others
  *                 held at their current best) on this context's scratch
@@ -395,9 +403,9 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  *                 above (0 where not timed).  Synchronises the stream.
  * pm_set_tuning   set all of them explicitly (PM_EINVAL for other values)
  * pm_get_tuning   read them (host int[PM_TUNE_KINDS])
- * Results do not depend on the choice beyond the order of FP32 atomics and,
- * for [7] and [8], the FP32 rounding order of the transforms. */
-#define PM_TUNE_KINDS 9
+ * Results do not depend on the choice beyond the order of FP32 sums (atomics,
+ * [9]) and, for [7] and [8], the FP32 rounding order of the transforms. */
+#define PM_TUNE_KINDS 10
 int pm_autotune(pm_ctx *ctx, const float *s, float *ms);
 int pm_set_tuning(pm_ctx *ctx, const int *threads);
 int pm_get_tuning(pm_ctx *ctx, int *threads);

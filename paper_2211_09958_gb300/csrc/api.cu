@@ -84,7 +84,13 @@ struct pm_ctx {
     // launch shapes of the tunable kernel families: block sizes of paint,
     // read, spectral force/adjoint, z-pass FFT (n >= 256); x-pass pencil width
     // shape; z-inverse and z-forward staging; x round trip; force pipeline
-    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8, 2, 1, 2, 2};
+    int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8, 2, 1, 2, 2, 1};
+    // binned tile-owned deposit (own-FFT meshes, CIC, n_m a multiple of 16):
+    // bin keys, ranks and CSR of the particles, counters, scan scratch, halo lines
+    bool dep_ok = false;
+    int *dep_key = nullptr, *dep_rank = nullptr, *dep_idx = nullptr, *dep_count = nullptr, *dep_offset = nullptr,
+        *dep_chunk = nullptr;
+    float *dep_halo = nullptr;
     // learned force correction (own-FFT meshes only)
     bool nn_on = false;
     void *nn_packed = nullptr;
@@ -375,6 +381,56 @@ PaintArgs paint_args(pm_ctx *ctx, const float *s, const float *mu = nullptr) {
     return a;
 }
 
+bool binned_deposit(const pm_ctx *ctx) { return ctx->dep_ok && ctx->tune[9] == 2; }
+
+// Paint into a plain mesh that this call fills completely, every cell
+// starting from `base`: the binned tile-owned deposit (no zeroing), or
+// filling and the atomic scatter.
+int paint_own(pm_ctx *ctx, int mode, const PaintArgs &pa, float base = 0.f) {
+    const bool adj = mode == PAINT_ADJ;
+    const int nf = adj ? 4 : 1;
+    if (binned_deposit(ctx) && pa.mesh.zs == ctx->P.n_m && pa.mesh.il == (adj ? 4 : 0)) {
+        DepositArgs da{};
+        da.g = ctx->g;
+        da.s = pa.s;
+        da.mu = pa.mu;
+        da.key = ctx->dep_key;
+        da.rank = ctx->dep_rank;
+        da.idx = ctx->dep_idx;
+        da.count = ctx->dep_count;
+        da.offset = ctx->dep_offset;
+        da.chunk_sum = ctx->dep_chunk;
+        da.mesh = pa.mesh.ptr;
+        da.halo = ctx->dep_halo;
+        da.tiles = deposit_tiles(ctx->g);
+        da.base = base;
+        PM_LAUNCH(ctx, "bin_count", launch_bin_count(da, ctx->stream));
+        PM_LAUNCH(ctx, "bin_scan_sums", launch_bin_scan_sums(da, ctx->stream));
+        PM_LAUNCH(ctx, "bin_scan", launch_bin_scan(da, ctx->stream));
+        PM_LAUNCH(ctx, "bin_scatter", launch_bin_scatter(da, ctx->stream));
+        PM_LAUNCH(ctx, (adj ? "deposit_adj" : "deposit_density"), launch_deposit(nf, da, ctx->stream));
+        PM_LAUNCH(ctx, (adj ? "deposit_halo_4" : "deposit_halo_1"), launch_deposit_halo(nf, da, ctx->stream));
+        return PM_OK;
+    }
+    const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
+    if (base == 0.f)
+        PM_MEMSET(ctx, cudaMemsetAsync(pa.mesh.ptr, 0, sizeof(float) * n3 * nf * ctx->P.n_batch, ctx->stream));
+    else
+        PM_LAUNCH(ctx, "fill", launch_fill(pa.mesh.ptr, n3 * nf * ctx->P.n_batch, base, ctx->stream));
+    PM_LAUNCH(ctx, paint_kind(mode), launch_paint(mode, pa, ctx->stream));
+    return PM_OK;
+}
+
+// The density of s (alpha sum W) into the real scratch field dref.
+int paint_density(pm_ctx *ctx, const float *s, const MeshRef &dref) {
+    PaintArgs pa = paint_args(ctx, s);
+    pa.mesh = dref;
+    if (ctx->own) return paint_own(ctx, PAINT_DENSITY, pa);
+    PM_MEMSET(ctx, cudaMemsetAsync(dref.ptr, 0, sizeof(float) * density_floats(ctx), ctx->stream));
+    PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
+    return PM_OK;
+}
+
 ReadArgs read_args(pm_ctx *ctx, float *s) {
     ReadArgs a{};
     a.g = ctx->g;
@@ -454,8 +510,7 @@ int force_meshes(pm_ctx *ctx, const float *s, const float *mu, double a = -1.0, 
         const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
         float *real = adj ? ctx->r4 : ctx->r1;
         pa.mesh = adj ? mesh_ref(ctx) : density_ref(ctx);
-        PM_MEMSET(ctx, cudaMemsetAsync(real, 0, sizeof(float) * n3 * nf * ctx->P.n_batch, ctx->stream));
-        PM_LAUNCH(ctx, paint_kind(mode), launch_paint(mode, pa, ctx->stream));
+        PM_TRY(paint_own(ctx, mode, pa));
         const int go = adj ? 4 : 3;
         if (pot_pipeline(ctx)) {
             // z and y forward; x round trip to phi (and psi); y and z inverse of
@@ -752,10 +807,7 @@ int correction_adjoint(pm_ctx *ctx, double a, int kick_step, int kick_sel) {
 // 0..2 overwritten); train = also keep the activations.
 int nn_forward_at(pm_ctx *ctx, const float *s, double a, bool train) {
     const MeshRef dref = density_ref(ctx);
-    PM_MEMSET(ctx, cudaMemsetAsync(dref.ptr, 0, sizeof(float) * density_floats(ctx), ctx->stream));
-    PaintArgs pa = paint_args(ctx, s);
-    pa.mesh = dref;
-    PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
+    PM_TRY(paint_density(ctx, s, dref));
     NNArgs na = nn_args(ctx, a);
     PM_LAUNCH(ctx, "nn_feat", launch_nn_feat(ctx->r1, ctx->nn_feat, nn_cells(ctx), ctx->stream));
     PM_LAUNCH(ctx, (train ? "nn_fwd_train" : "nn_fwd_tc"), launch_nn_fwd_tc(na, nn_cells(ctx), ctx->stream, train));
@@ -772,16 +824,16 @@ const char *pm_last_error(const pm_ctx *ctx) { return ctx ? ctx->err.c_str() : g
 
 int64_t pm_launch_count(const pm_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
-const int kTuneCand[PM_TUNE_KINDS][3] = {{128, 256, 512}, {128, 256, 512}, {128, 256, 512},
-                                         {128, 256, 512}, {8, 16, 0},      {1, 2, 0},
-                                         {1, 2, 0},       {1, 2, 3},       {1, 2, 0}};
+const int kTuneCand[PM_TUNE_KINDS][3] = {{128, 256, 512}, {128, 256, 512}, {128, 256, 512}, {128, 256, 512},
+                                         {8, 16, 0},      {1, 2, 0},       {1, 2, 0},       {1, 2, 3},
+                                         {1, 2, 0},       {1, 2, 0}};
 
 static int set_tuning(pm_ctx *ctx, const int *t) {
     for (int k = 0; k < PM_TUNE_KINDS; ++k)
         if (t[k] <= 0 || (t[k] != kTuneCand[k][0] && t[k] != kTuneCand[k][1] && t[k] != kTuneCand[k][2]))
             return fail(ctx, PM_EINVAL,
                         "block sizes must be 128, 256 or 512, the x-pass width 8 or 16, the z stagings 1 or 2, "
-                        "the x round trip 1, 2 or 3, the force pipeline 1 or 2");
+                        "the x round trip 1, 2 or 3, the force pipeline 1 or 2, the deposit 1 or 2");
     for (int k = 0; k < PM_TUNE_KINDS; ++k) ctx->tune[k] = t[k];
     ctx->fg.zthreads = ctx->tune[3];
     ctx->fg.xwidth = ctx->tune[4];
@@ -864,6 +916,15 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
             if ((e = launch_fft_z_inv(3, ctx->spec, ctx->r4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
             return launch_fft_z_inv(4, ctx->spec, ctx->r4, ctx->fg, ctx->stream);
         }
+        if (kind == 9) {  // a density paint and an adjoint paint, each filling its mesh
+            PaintArgs pa = paint_args(ctx, s);
+            pa.mesh = density_ref(ctx);
+            if (paint_own(ctx, PAINT_DENSITY, pa) != PM_OK) return cudaErrorUnknown;
+            pa = paint_args(ctx, s, s);
+            pa.mesh = mesh_ref(ctx);
+            if (paint_own(ctx, PAINT_ADJ, pa) != PM_OK) return cudaErrorUnknown;
+            return cudaGetLastError();
+        }
         if (kind == 8) {  // a whole force evaluation with its read, and an adjoint one (the pipelines differ
                           // from the x pass on; the potential read moves the difference into the read)
             if (force_meshes(ctx, s, nullptr) != PM_OK) return cudaErrorUnknown;
@@ -885,7 +946,8 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
         if ((kind == 3 && !(ctx->own && ctx->P.n_m >= 256)) || (kind == 4 && !ctx->own) ||
             (kind == 5 && !(ctx->own && ctx->zmaps[0].valid)) || (kind == 6 && !ctx->own) ||
             (kind == 7 && !ctx->own) ||
-            (kind == 8 && !(ctx->own && !(ctx->P.solver & PM_SOLVER_SPECTRAL_GRADIENT)))) {
+            (kind == 8 && !(ctx->own && !(ctx->P.solver & PM_SOLVER_SPECTRAL_GRADIENT))) ||
+            (kind == 9 && !ctx->dep_ok)) {
             if (ms) ms[3 * kind] = ms[3 * kind + 1] = ms[3 * kind + 2] = 0.f;
             continue;
         }
@@ -1073,6 +1135,23 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
         ctx->tune[7] = ctx->P.n_m >= 512 ? 3 : 2;  // the fused adjoint spills on lines of 512+ points
         // the potential pipeline needs the 4-point difference gradient
         ctx->tune[8] = (c.solver & PM_SOLVER_SPECTRAL_GRADIENT) ? 1 : 2;
+        if (deposit_supported(ctx->g, n)) {
+            const size_t parts = (size_t)npart * B, bins = (size_t)deposit_tiles(ctx->g) * B;
+            if (cudaMalloc(&ctx->dep_key, sizeof(int) * parts) != cudaSuccess ||
+                cudaMalloc(&ctx->dep_rank, sizeof(int) * parts) != cudaSuccess ||
+                cudaMalloc(&ctx->dep_idx, sizeof(int) * parts) != cudaSuccess ||
+                cudaMalloc(&ctx->dep_count, sizeof(int) * bins) != cudaSuccess ||
+                cudaMalloc(&ctx->dep_offset, sizeof(int) * (bins + 1)) != cudaSuccess ||
+                cudaMalloc(&ctx->dep_chunk, sizeof(int) * deposit_scan_chunks(ctx->g)) != cudaSuccess ||
+                cudaMalloc(&ctx->dep_halo, sizeof(float) * deposit_halo_floats(ctx->g)) != cudaSuccess ||
+                cudaMemset(ctx->dep_count, 0, sizeof(int) * bins) != cudaSuccess || deposit_prepare() != cudaSuccess) {
+                cudaGetLastError();
+                fail(ctx, PM_ENOMEM, "cannot allocate the binned-deposit buffers");
+                return bail(PM_ENOMEM);
+            }
+            ctx->dep_ok = true;
+            ctx->tune[9] = 2;
+        }
     } else if (cudaMalloc(&ctx->mesh, sizeof(float) * (size_t)ctx->mesh_pad * B * kMeshFields) != cudaSuccess) {
         cudaGetLastError();
         fail(ctx, PM_ENOMEM, "cannot allocate the FFT meshes");
@@ -1160,6 +1239,9 @@ int pm_destroy(pm_ctx *ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (void *p : {(void *)ctx->r1, (void *)ctx->r4, (void *)ctx->rpot, (void *)ctx->spec, (void *)ctx->tw,
                     (void *)ctx->d_err})
+        if (p) cudaFree(p);
+    for (void *p : {(void *)ctx->dep_key, (void *)ctx->dep_rank, (void *)ctx->dep_idx, (void *)ctx->dep_count,
+                    (void *)ctx->dep_offset, (void *)ctx->dep_chunk, (void *)ctx->dep_halo})
         if (p) cudaFree(p);
     for (void *p : {(void *)ctx->mesh, (void *)ctx->lat, (void *)ctx->d_table, (void *)ctx->d_pref, (void *)ctx->d_grad, (void *)ctx->d_dec,
                     (void *)ctx->d_fac, (void *)ctx->d_lin, (void *)ctx->d_red, (void *)ctx->d_pk,
@@ -1461,11 +1543,9 @@ int pm_density(pm_ctx *ctx, const float *s, float *delta) {
     PM_TRY(check_ptr(ctx, delta, "delta"));
     DeviceGuard guard(ctx->device);
     const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
-    PM_LAUNCH(ctx, "fill", launch_fill(delta, n3 * ctx->P.n_batch, -1.f, ctx->stream));
     PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
-    pa.mesh = MeshRef{delta, 0, n3, ctx->P.n_m};
-    PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
-    return PM_OK;
+    pa.mesh = MeshRef{delta, 0, n3, ctx->P.n_m, 0};
+    return paint_own(ctx, PAINT_DENSITY, pa, -1.f);  // delta = rho - 1
 }
 
 int pm_density_adjoint(pm_ctx *ctx, const float *s, const float *ddelta, float *ds) {
@@ -1491,10 +1571,7 @@ int pm_mse_loss(pm_ctx *ctx, const float *s, const float *target, double *loss, 
     DeviceGuard guard(ctx->device);
     const int B = ctx->P.n_batch;
     const MeshRef dref = density_ref(ctx);
-    PM_MEMSET(ctx, cudaMemsetAsync(dref.ptr, 0, sizeof(float) * density_floats(ctx), ctx->stream));
-    PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
-    pa.mesh = dref;
-    PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
+    PM_TRY(paint_density(ctx, s, dref));
     PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_pk, 0, sizeof(double) * B, ctx->stream));
     PM_LAUNCH(ctx, "mse", launch_mse(dref, target, ctx->P.n_m, B, ctx->d_pk, ctx->stream));
     if (dlds) {
@@ -1560,10 +1637,7 @@ int pm_power_spectrum(pm_ctx *ctx, const float *s, double *k_mean, double *power
     DeviceGuard guard(ctx->device);
     const int B = ctx->P.n_batch, nb = ctx->P.n_m / 2;
     const MeshRef dref = density_ref(ctx);
-    PM_MEMSET(ctx, cudaMemsetAsync(dref.ptr, 0, sizeof(float) * density_floats(ctx), ctx->stream));
-    PaintArgs pa = paint_args(ctx, const_cast<float *>(s));
-    pa.mesh = dref;
-    PM_LAUNCH(ctx, paint_kind(PAINT_DENSITY), launch_paint(PAINT_DENSITY, pa, ctx->stream));
+    PM_TRY(paint_density(ctx, s, dref));
     if (ctx->own)
         PM_TRY(own_forward(ctx, ctx->r1, 1));
     else

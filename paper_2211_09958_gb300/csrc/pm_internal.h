@@ -138,6 +138,36 @@ struct ReadArgs {
 };
 
 cudaError_t launch_paint(int mode, const PaintArgs &a, cudaStream_t st);
+
+// Binned, tile-owned CIC deposit (deposit_kernels.cu): particles binned by
+// the DEPOSIT_TILE^3 tile of their base cell, then one block per column of
+// tiles writes each owned mesh cell once; halo lines added by a second pass.
+// Own-FFT plain meshes only (zs == n_m), n_m a multiple of DEPOSIT_TILE, CIC.
+constexpr int DEPOSIT_TILE = 16;
+struct DepositArgs {
+    Geom g;
+    const float *s, *mu;  // [run][npart][3]; mu for the 4-field paint
+    int *key, *rank;      // [run * npart] tile and rank within it (bin_count)
+    int *idx;             // [run * npart] particles in bin order (bin_scatter)
+    int *count;           // [run * tiles] counters, zero between binnings
+    int *offset;          // [run * tiles + 1] CSR offsets into idx
+    int *chunk_sum;       // [deposit_scan_chunks] scan scratch
+    float *mesh;          // plain [run][n^3] (1 field) or interleaved [run][n^3][4]
+    float *halo;          // [run][nt][nt][2 TILE + 1][n_m] x fields halo lines
+    int64_t tiles;        // tiles per run
+    float base;           // value every cell starts from (added once, at the owned store)
+};
+bool deposit_supported(const Geom &g, int zs);
+int64_t deposit_tiles(const Geom &g);
+int64_t deposit_halo_floats(const Geom &g);  // for 4 fields
+int64_t deposit_scan_chunks(const Geom &g);
+cudaError_t deposit_prepare();  // kernel attributes; call once before any capture
+cudaError_t launch_bin_count(const DepositArgs &a, cudaStream_t st);
+cudaError_t launch_bin_scan_sums(const DepositArgs &a, cudaStream_t st);
+cudaError_t launch_bin_scan(const DepositArgs &a, cudaStream_t st);
+cudaError_t launch_bin_scatter(const DepositArgs &a, cudaStream_t st);
+cudaError_t launch_deposit(int nf, const DepositArgs &a, cudaStream_t st);
+cudaError_t launch_deposit_halo(int nf, const DepositArgs &a, cudaStream_t st);
 cudaError_t launch_pre(int mode, const PreArgs &a, cudaStream_t st);
 cudaError_t launch_read(int mode, const ReadArgs &a, cudaStream_t st);
 cudaError_t launch_fill(float *ptr, int64_t n, float v, cudaStream_t st);

@@ -47,6 +47,7 @@ class ParticleMesh:
         tuning = self.get_tuning()
         self._x_round_default = tuning["x_round"]          # 2, or 3 on meshes of 512 and more
         self._pipeline_default = tuning["pipeline"]        # 2, or 1 with the spectral-gradient flag
+        self._deposit_default = tuning["deposit"]          # 2 where the binned deposit applies, else 1
 
     # ------------------------------------------------------------ helpers --
     @property
@@ -238,7 +239,7 @@ class ParticleMesh:
 
     # ------------------------------------------------------- autotuner --
     TUNE_FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x", "z_staging", "z_fwd_staging", "x_round",
-                     "pipeline")
+                     "pipeline", "deposit")
 
     def autotune(self, s):
         """Pick the fastest launch shape per kernel family on particles s;
@@ -249,7 +250,9 @@ class ParticleMesh:
         inverse x pass as three launches), 2 (one fused kernel) and 3 (fused
         for the force, three launches for the adjoint), pipeline 1 (force
         components as inverse transforms) and 2 (one inverse transform of
-        the potential, then the 4-point difference on the real mesh))."""
+        the potential, then the 4-point difference on the real mesh),
+        deposit 1 (zeroing and the atomic scatter) and 2 (particles binned
+        by tile, each cell written once by the block that owns it))."""
         self._particles(s, "s")
         ms = np.zeros((len(self.TUNE_FAMILIES), 3), np.float32)
         self._call("pm_autotune", _ptr(s), ms.ctypes.data_as(ctypes.c_void_p))
@@ -261,17 +264,20 @@ class ParticleMesh:
         return dict(zip(self.TUNE_FAMILIES, (int(v) for v in t)))
 
     def set_tuning(self, paint=256, read=256, spectral=256, fft_z=256, fft_x=8, z_staging=None, z_fwd_staging=1,
-                   x_round=None, pipeline=None):
+                   x_round=None, pipeline=None, deposit=None):
         """Fix the launch shapes; a family not named takes the context's
         default (z_staging keeps its current value, x_round and pipeline the
-        defaults the context was created with)."""
+        defaults the context was created with, and so does deposit)."""
         if z_staging is None:
             z_staging = self.get_tuning()["z_staging"]
         if x_round is None:
             x_round = self._x_round_default
         if pipeline is None:
             pipeline = self._pipeline_default
-        t = np.array([paint, read, spectral, fft_z, fft_x, z_staging, z_fwd_staging, x_round, pipeline], np.int32)
+        if deposit is None:
+            deposit = self._deposit_default
+        t = np.array([paint, read, spectral, fft_z, fft_x, z_staging, z_fwd_staging, x_round, pipeline, deposit],
+                     np.int32)
         self._call("pm_set_tuning", t.ctypes.data_as(ctypes.c_void_p))
 
     def use_graphs(self, enable=True):

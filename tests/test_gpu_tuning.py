@@ -10,12 +10,13 @@ from paper_2211_09958_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x", "z_staging", "z_fwd_staging", "x_round", "pipeline")
+FAMILIES = ("paint", "read", "spectral", "fft_z", "fft_x", "z_staging", "z_fwd_staging", "x_round", "pipeline",
+            "deposit")
 CANDIDATES = {"paint": (128, 256, 512), "read": (128, 256, 512), "spectral": (128, 256, 512),
               "fft_z": (128, 256, 512), "fft_x": (8, 16), "z_staging": (1, 2), "z_fwd_staging": (1, 2),
-              "x_round": (1, 2, 3), "pipeline": (1, 2)}
+              "x_round": (1, 2, 3), "pipeline": (1, 2), "deposit": (1, 2)}
 DEFAULT = {"paint": 256, "read": 256, "spectral": 256, "fft_z": 256, "fft_x": 8, "z_staging": 2, "z_fwd_staging": 1,
-           "x_round": 2, "pipeline": 2}
+           "x_round": 2, "pipeline": 2, "deposit": 2}
 
 
 def _pm(n_p=32, n_m=256, box=128.0, steps=3):
