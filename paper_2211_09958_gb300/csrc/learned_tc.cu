@@ -180,7 +180,7 @@ __device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
 // as two 16-byte core-matrix rows at dst and dst + M * 16.
 template <int HALF>
 __device__ __forceinline__ void feature_rows(const unsigned short *f, int64_t c, int n, unsigned short afeat,
-                                             char *dst, bf16 *xg_row) {
+                                             char *dst) {
     const int x = (int)(c / ((int64_t)n * n)), y = (int)((c / n) % n), z = (int)(c % n);
     const int xs[3] = {x == 0 ? n - 1 : x - 1, x, x == n - 1 ? 0 : x + 1};
     const int ys[3] = {y == 0 ? n - 1 : y - 1, y, y == n - 1 ? 0 : y + 1};
@@ -203,8 +203,6 @@ __device__ __forceinline__ void feature_rows(const unsigned short *f, int64_t c,
         }
         // the next 8 columns are the next K-direction core matrix, M * 16 bytes on
         *reinterpret_cast<uint4 *>(dst + chunk * M * 16) = make_uint4(w[0], w[1], w[2], w[3]);
-        if (xg_row)  // training: the features, row-major, for the first layer's weight gradient
-            *reinterpret_cast<uint4 *>(xg_row + 16 * HALF + 8 * chunk) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
@@ -217,10 +215,8 @@ __device__ __forceinline__ void mma_chain(uint32_t d_tmem, uint32_t a_base, uint
 }
 
 // 64 columns [c0, c0 + 64) of a 128-wide accumulator for this thread's row:
-// + bias, ReLU, bf16, into the A2 operand (row `row`, columns c0 ..); in
-// training also into the row-major activation row h_row (global).
-__device__ __forceinline__ void relu_to_a2(uint32_t taddr, const float *bias, int c0, int row, char *a2,
-                                           bf16 *h_row) {
+// + bias, ReLU, bf16, into the A2 operand (row `row`, columns c0 ..).
+__device__ __forceinline__ void relu_to_a2(uint32_t taddr, const float *bias, int c0, int row, char *a2) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         float v[32];
@@ -234,8 +230,21 @@ __device__ __forceinline__ void relu_to_a2(uint32_t taddr, const float *bias, in
             u.z = pack2_relu(v[8 * q + 4] + bias[c + 4], v[8 * q + 5] + bias[c + 5]);
             u.w = pack2_relu(v[8 * q + 6] + bias[c + 6], v[8 * q + 7] + bias[c + 7]);
             *reinterpret_cast<uint4 *>(a2 + 2 * nn_cm_index(row, c, M)) = u;
-            if (h_row) *reinterpret_cast<uint4 *>(h_row + c) = u;
         }
+    }
+}
+
+// The 128 rows x COLS columns of an A operand (core-matrix layout) to the
+// row-major global rows dst [128][COLS], by the PT threads of a pipeline:
+// eight lanes read one 128-byte core matrix (no bank conflict) and a warp
+// writes 64 contiguous bytes of each of 8 rows.
+template <int COLS>
+__device__ __forceinline__ void rows_out(const char *a_op, bf16 *dst, int tp) {
+    constexpr int JC = COLS / 8;
+    for (int e = tp; e < M * JC; e += PT) {
+        const int r = ((e >> 3) / JC) * 8 + (e & 7), j = (e >> 3) % JC;
+        *reinterpret_cast<uint4 *>(dst + (int64_t)r * COLS + 8 * j) =
+            *reinterpret_cast<const uint4 *>(a_op + 2 * nn_cm_index(r, 8 * j, M));
     }
 }
 
@@ -295,24 +304,25 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t til
             const int64_t c = cell0 - run * n3 + cl;
             const unsigned short *f = reinterpret_cast<const unsigned short *>(a.feat) + run * n3;
             const unsigned short afeat = __bfloat16_as_ushort(__float2bfloat16_rn(a.afeat));
-            bf16 *xrow = TRAIN ? a.xg + (cell0 + cl) * NI : nullptr;
             if (tp < M)
-                feature_rows<0>(f, c, n, afeat, abuf + 2 * nn_cm_index(cl, 0, M), xrow);
+                feature_rows<0>(f, c, n, afeat, abuf + 2 * nn_cm_index(cl, 0, M));
             else
-                feature_rows<1>(f, c, n, afeat, abuf + 2 * nn_cm_index(cl, 16, M), xrow);
+                feature_rows<1>(f, c, n, afeat, abuf + 2 * nn_cm_index(cl, 16, M));
         }
         fence_async_smem();
         fence_before();
         pipe_sync(pipe);
-        // layer 1 (A1 = features, 128 x 32)
+        // layer 1 (A1 = features, 128 x 32); in training the operand rows go out
+        // to the row-major activation arrays while the MMAs read them
         if (tp == 0) {
             fence_after();
             mma_chain(tcol, sA, sW1, NI, NH);
             mma_commit(bar);
         }
+        if (TRAIN) rows_out<NI>(abuf, a.xg + cell0 * NI, tp);
         ok = wait_all(bar, phase, tp, pipe);
         if (!ok) break;
-        relu_to_a2(lane_base, bias, 64 * colhalf, row, abuf, TRAIN ? a.h1g + (cell0 + row) * NH : nullptr);
+        relu_to_a2(lane_base, bias, 64 * colhalf, row, abuf);
         fence_async_smem();
         fence_before();
         pipe_sync(pipe);
@@ -322,9 +332,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t til
             mma_chain(tcol, sA, sW2, NH, NH);
             mma_commit(bar);
         }
+        if (TRAIN) rows_out<NH>(abuf, a.h1g + cell0 * NH, tp);
         ok = wait_all(bar, phase, tp, pipe);
         if (!ok) break;
-        relu_to_a2(lane_base, bias + NH, 64 * colhalf, row, abuf, TRAIN ? a.h2g + (cell0 + row) * NH : nullptr);
+        relu_to_a2(lane_base, bias + NH, 64 * colhalf, row, abuf);
         fence_async_smem();
         fence_before();
         pipe_sync(pipe);
@@ -334,6 +345,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_fwd_tc(NNArgs a, int64_t til
             mma_chain(tcol, sA, sW3, NH, N3);
             mma_commit(bar);
         }
+        if (TRAIN) rows_out<NH>(abuf, a.h2g + cell0 * NH, tp);
         ok = wait_all(bar, phase, tp, pipe);
         if (!ok) break;
         if (colhalf == 0) {
@@ -425,11 +437,11 @@ __device__ __forceinline__ uint32_t pack2_rn(float lo, float hi) {
 }
 
 // 64 columns [c0, c0 + 64) of this thread's accumulator row, masked by the
-// stored activation row (h > 0): bf16 into the A operand (when a_op) and the
-// global cotangent row g_row; the warp's column sums of the FP32 masked
-// values added to gsum[0..1] (lane l: columns c0 + l and c0 + 32 + l).
+// stored activation row (h > 0): bf16 into the A operand; the warp's column
+// sums of the FP32 masked values added to gsum[0..1] (lane l: columns c0 + l
+// and c0 + 32 + l).
 __device__ __forceinline__ void masked_to_a(uint32_t taddr, int c0, int row, char *a_op, const bf16 *h_row,
-                                            bf16 *g_row, float (&gsum)[2], int lane) {
+                                            float (&gsum)[2], int lane) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         float v[32];
@@ -449,8 +461,7 @@ __device__ __forceinline__ void masked_to_a(uint32_t taddr, int c0, int row, cha
             u.y = pack2_rn(v[8 * q + 2], v[8 * q + 3]);
             u.z = pack2_rn(v[8 * q + 4], v[8 * q + 5]);
             u.w = pack2_rn(v[8 * q + 6], v[8 * q + 7]);
-            if (a_op) *reinterpret_cast<uint4 *>(a_op + 2 * nn_cm_index(row, c, M)) = u;
-            *reinterpret_cast<uint4 *>(g_row + c) = u;
+            *reinterpret_cast<uint4 *>(a_op + 2 * nn_cm_index(row, c, M)) = u;
         }
         gsum[h] += column_sums32(v, lane);
     }
@@ -498,6 +509,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_bwd_tc(NNArgs a, int64_t til
     for (int64_t tile = (int64_t)blockIdx.x * PIPES + pipe; tile < tiles && ok; tile += (int64_t)gridDim.x * PIPES) {
         const int64_t cell0 = tile * M, cell = cell0 + row;
         const int64_t run = cell0 / n3;
+        // the activation rows the epilogues mask with (128 bytes each), towards L1
+        // while the MMAs run
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.h2g + cell * NH + 64 * colhalf));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.h1g + cell * NH + 64 * colhalf));
         if (colhalf == 0) {  // output cotangent of this thread's cell
             const float s_out = a.pref[run] * a.s_scale * nn_kick_coef(a, run);
             const float4 u = *reinterpret_cast<const float4 *>(a.gmesh + cell * 4);
@@ -524,7 +539,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_bwd_tc(NNArgs a, int64_t til
         }
         ok = wait_all(bar, phase, tp, pipe);
         if (!ok) break;
-        masked_to_a(lane_base, 64 * colhalf, row, abuf, a.h2g + cell * NH, a.g2g + cell * NH, gs2, lane);
+        masked_to_a(lane_base, 64 * colhalf, row, abuf, a.h2g + cell * NH, gs2, lane);
         fence_async_smem();
         fence_before();
         pipe_sync(pipe);
@@ -533,19 +548,20 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_bwd_tc(NNArgs a, int64_t til
             mma_chain(tcol, sA, sV2, NH, NH);
             mma_commit(bar);
         }
+        rows_out<NH>(abuf, a.g2g + cell0 * NH, tp);  // g2 rows out while the MMAs read them
         ok = wait_all(bar, phase, tp, pipe);
         if (!ok) break;
-        masked_to_a(lane_base, 64 * colhalf, row, a.gx ? abuf : nullptr, a.h1g + cell * NH, a.g1g + cell * NH,
-                    gs1, lane);
+        masked_to_a(lane_base, 64 * colhalf, row, abuf, a.h1g + cell * NH, gs1, lane);
+        fence_async_smem();
+        fence_before();
+        pipe_sync(pipe);
+        if (a.gx && tp == 0) {
+            fence_after();
+            mma_chain(tcol, sA, sV1, NH, NI);
+            mma_commit(bar);
+        }
+        rows_out<NH>(abuf, a.g1g + cell0 * NH, tp);
         if (a.gx) {
-            fence_async_smem();
-            fence_before();
-            pipe_sync(pipe);
-            if (tp == 0) {
-                fence_after();
-                mma_chain(tcol, sA, sV1, NH, NI);
-                mma_commit(bar);
-            }
             ok = wait_all(bar, phase, tp, pipe);
             if (!ok) break;
             float v[16];
@@ -590,11 +606,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_mlp_bwd_tc(NNArgs a, int64_t til
 //   dW2 = h1^T g2:  A = h1 [cells][128], B = g2 [cells][128], N = 128
 //   dW3 = h2^T g3:  A = h2, B = g3 [cells][8] (3 valid; zero to N = 16)
 //   dW1^T = g1^T x: A = g1, B = x [cells][32], N = 32; stored transposed
-// The [cells][units] rows arrive with coalesced 16-byte loads in a natural
-// [cell][unit] buffer, and each thread then gathers 8 cells of one unit into
-// one 16-byte row of the K-major core-matrix layout (element (i, k) at
-// nn_cm_index(i, k, 128)); two operand stages, so that one chunk is staged
-// while the MMAs of the previous one run.  At the
+// The operands are used as they lie in memory: [cells][units] rows are
+// MN-major for this product (units contiguous, the cells the K dimension),
+// so each 16-byte piece (cell k, units 8j .. 8j + 7) is copied with a
+// coalesced load straight into its MN-major core matrix: 8 cells x 8 units,
+// cell rows 16 bytes apart, unit blocks 128 bytes apart (stride byte
+// offset), cell blocks R / 8 * 128 bytes apart (leading byte offset); the
+// instruction descriptor marks A and B MN-major.  Two operand stages, so
+// that one chunk is staged while the MMAs of the previous one run.  At the
 // end each thread reads its TMEM lane (unit i) and adds its columns to the
 // FP32 gradient in global memory.  Waits are bounded as in k_mlp_fwd_tc.
 constexpr int WG_THREADS = 256;
@@ -604,34 +623,37 @@ template <int N>
 struct WgShape {
     static constexpr int A_BYTES = M * WG_K * 2, B_BYTES = N * WG_K * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int OFF_NAT = 2 * STAGE;                 // natural [cell][unit] landing buffer
-    static constexpr int OFF_BAR = OFF_NAT + M * WG_K * 2, OFF_TMEM = OFF_BAR + 16, SMEM = OFF_TMEM + 8;
+    static constexpr int OFF_BAR = 2 * STAGE, OFF_TMEM = OFF_BAR + 16, SMEM = OFF_TMEM + 8;
     static constexpr uint32_t COLS = N < 32 ? 32 : N;  // TMEM allocation: a power of two >= 32
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-// rows [c0, c0 + 128) of src ([cells][ld] bf16) -> nat [128][ld], coalesced 16-byte copies
-__device__ __forceinline__ void wg_land(const bf16 *src, int ld, int64_t c0, char *nat, int tid) {
-    const int n16 = WG_K * ld / 8;
-    const uint4 *g = reinterpret_cast<const uint4 *>(src + c0 * ld);
-    for (int e = tid; e < n16; e += WG_THREADS) reinterpret_cast<uint4 *>(nat)[e] = __ldg(g + e);
+// Instruction descriptor of the weight-gradient products: kind::f16 as
+// idesc(n), with A and B MN-major (bits 15 and 16).
+__host__ __device__ constexpr uint32_t idesc_mn(int n) { return idesc(n) | (1u << 15) | (1u << 16); }
+
+// 16-byte asynchronous copy from global to shared memory; src_bytes = 0
+// writes zeros without reading.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
 }
 
-// nat [128 cells][ld units] -> K-major core matrices of R rows (units; rows
-// >= ld are zero): thread (unit j, cells 8 kb .. 8 kb + 7) writes one 16-byte row.
+// Rows [c0, c0 + 128) of src ([cells][ld] bf16) into the MN-major core
+// matrices of R units (units >= ld zero), as asynchronous copies.
 template <int R>
-__device__ __forceinline__ void wg_transpose(const char *nat, int ld, char *dst, int tid) {
-    const unsigned short *src = reinterpret_cast<const unsigned short *>(nat);
-    for (int e = tid; e < R * (WG_K / 8); e += WG_THREADS) {
-        const int j = e % R, kb = e / R;
-        uint32_t w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t lo = j < ld ? src[(8 * kb + 2 * q) * ld + j] : 0u;
-            const uint32_t hi = j < ld ? src[(8 * kb + 2 * q + 1) * ld + j] : 0u;
-            w[q] = lo | (hi << 16);
-        }
-        *reinterpret_cast<uint4 *>(dst + 2 * nn_cm_index(j, 8 * kb, R)) = make_uint4(w[0], w[1], w[2], w[3]);
+__device__ __forceinline__ void wg_copy_mn(const bf16 *__restrict__ src, int ld, int64_t c0, char *dst, int tid) {
+    constexpr int JR = R / 8;
+    // e = ((k / 8) JR + j) 8 + k % 8: eight lanes fill one core matrix (128
+    // contiguous bytes of shared memory, no bank conflict), and a warp reads
+    // 8 cell rows of 64 bytes (R >= 32)
+    for (int e = tid; e < WG_K * JR; e += WG_THREADS) {
+        const int k = ((e >> 3) / JR) * 8 + (e & 7), j = (e >> 3) % JR;
+        const bool in = 8 * j < ld;
+        cp_async16(dst + ((k >> 3) * JR + j) * 128 + (k & 7) * 16, in ? src + (c0 + k) * ld + 8 * j : src,
+                   in ? 16 : 0);
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 template <int N>
@@ -662,25 +684,31 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     int issued[2] = {0, 0};
     bool ok = true;
     int64_t it = 0;
+    if (blockIdx.x < chunks) {  // chunk 0's copies; each iteration issues the next chunk's before waiting
+        wg_copy_mn<M>(A, M, (int64_t)blockIdx.x * WG_K, sm, tid);
+        wg_copy_mn<N>(B, ldb, (int64_t)blockIdx.x * WG_K, sm + S::A_BYTES, tid);
+    }
     for (int64_t ch = blockIdx.x; ch < chunks && ok; ch += gridDim.x, ++it) {
         const int st = (int)(it & 1);
         const uint32_t bar = bar0 + 8 * st;
-        if (issued[st]) {  // the MMAs that read this stage two chunks ago must be done
-            const int good = tid == 0 ? (int)bar_wait(bar, phase[st]) : 1;
-            ok = __syncthreads_and(good) != 0;
-            phase[st] ^= 1;
-            issued[st] = 0;
-            if (!ok) break;
+        const int64_t nx = ch + gridDim.x;
+        if (nx < chunks) {
+            const int sn = st ^ 1;
+            if (issued[sn]) {  // the MMAs that read the other stage (previous chunk) must be done
+                const int good = tid == 0 ? (int)bar_wait(bar0 + 8 * sn, phase[sn]) : 1;
+                ok = __syncthreads_and(good) != 0;
+                phase[sn] ^= 1;
+                issued[sn] = 0;
+                if (!ok) break;
+            }
+            char *na = sm + sn * S::STAGE;
+            wg_copy_mn<M>(A, M, nx * WG_K, na, tid);
+            wg_copy_mn<N>(B, ldb, nx * WG_K, na + S::A_BYTES, tid);
+            asm volatile("cp.async.wait_group 2;" ::: "memory");  // this chunk's two groups have landed
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
-        char *sa = sm + st * S::STAGE, *sb = sa + S::A_BYTES, *nat = sm + S::OFF_NAT;
-        const int64_t c0 = ch * WG_K;
-        wg_land(A, M, c0, nat, tid);
-        __syncthreads();
-        wg_transpose<M>(nat, M, sa, tid);
-        __syncthreads();
-        wg_land(B, ldb, c0, nat, tid);
-        __syncthreads();
-        wg_transpose<N>(nat, ldb, sb, tid);
+        char *sa = sm + st * S::STAGE, *sb = sa + S::A_BYTES;
         fence_async_smem();
         fence_before();
         __syncthreads();
@@ -690,11 +718,12 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
             const uint32_t a_base = smem_u32(sa), b_base = smem_u32(sb);
             for (int kk = 0; kk < WG_K / 16; ++kk)
                 mma_f16(tcol, sdesc(a_base + 2 * kk * lbo_a, lbo_a, 128), sdesc(b_base + 2 * kk * lbo_b, lbo_b, 128),
-                        idesc(N), (it > 0 || kk > 0) ? 1u : 0u);
+                        idesc_mn(N), (it > 0 || kk > 0) ? 1u : 0u);
             mma_commit(bar);
         }
         issued[st] = 1;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the loop (early exit on a time-out)
     // drain both stages
     for (int st = 0; st < 2; ++st) {
         if (!issued[st]) continue;
@@ -779,11 +808,12 @@ cudaError_t nn_tc_prepare() {
 // cotangents the backward stored (g1, g2, g3); added to a.grad.
 cudaError_t launch_nn_wgrad_tc(const NNArgs &a, int64_t cells, cudaStream_t st) {
     const int64_t chunks = cells / WG_K;
-    const unsigned grid = (unsigned)(chunks < 152 ? chunks : 152);
+    // blocks per SM as shared memory allows (128, 80 and 72 KB)
+    auto grid = [&](int per_sm) { return (unsigned)(chunks < 152 * per_sm ? chunks : 152 * per_sm); };
     float *dW1 = a.grad, *dW2 = dW1 + NI * NH + NH, *dW3 = dW2 + NH * NH + NH;
-    k_wgrad_tc<128><<<grid, WG_THREADS, WgShape<128>::SMEM, st>>>(a.h1g, a.g2g, NH, chunks, dW2, NH, NH, 0, a.err);
-    k_wgrad_tc<16><<<grid, WG_THREADS, WgShape<16>::SMEM, st>>>(a.h2g, a.g3g, 8, chunks, dW3, NO, NO, 0, a.err);
-    k_wgrad_tc<32><<<grid, WG_THREADS, WgShape<32>::SMEM, st>>>(a.g1g, a.xg, NI, chunks, dW1, NH, NI, 1, a.err);
+    k_wgrad_tc<128><<<grid(1), WG_THREADS, WgShape<128>::SMEM, st>>>(a.h1g, a.g2g, NH, chunks, dW2, NH, NH, 0, a.err);
+    k_wgrad_tc<16><<<grid(3), WG_THREADS, WgShape<16>::SMEM, st>>>(a.h2g, a.g3g, 8, chunks, dW3, NO, NO, 0, a.err);
+    k_wgrad_tc<32><<<grid(2), WG_THREADS, WgShape<32>::SMEM, st>>>(a.g1g, a.xg, NI, chunks, dW1, NH, NI, 1, a.err);
     return cudaGetLastError();
 }
 
