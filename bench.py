@@ -24,6 +24,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -200,6 +201,94 @@ def _ncu_traffic(kind, workload):
         return None
     scale = ent.get("scale_to", {}).get(workload)
     return ent["dram_bytes_per_launch"] * (scale if scale else 1.0) if (scale or ent.get("workload") == workload) else None
+
+
+TRAFFIC_WORKLOAD = "pm128_mesh256"
+TRAFFIC_COMMAND = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                   "--clock-control none --kernel-name-base demangled -k regex:<kernel> -c 3 --csv "
+                   "python bench.py --workload pm128_mesh256 --sim-steps 2 --steps 1 --warmup 1 "
+                   "--no-cpu-baseline --no-autotune [--tuning deposit=2 for the binned-deposit kernels]")
+
+
+def _kernel_kind(name, grid, n):
+    """Launch kind of a library kernel from its ncu name (template arguments
+    printed plain or with C-style casts) and grid."""
+    m = re.search(r"(k_\w+)<([^>]*)>", name)
+    if not m:
+        m = re.search(r"(k_bin_count|k_bin_scatter)\b", name)
+        return {"k_bin_count": "bin_count", "k_bin_scatter": "bin_scatter"}.get(m.group(1)) if m else None
+    k = m.group(1)
+    args = [re.sub(r"^\((int|bool)\)", "", a.strip()) for a in m.group(2).split(",")]
+    zc = ((n // 2 + 1) + 7) // 8 * 8
+    if k == "k_paint":
+        return {"0": "paint_density", "2": "paint_adj"}.get(args[0])
+    if k == "k_read":
+        return {"0": "read_force", "1": "read_kick_drift", "2": "read_half_kick", "3": "read_adj",
+                "4": "read_grad"}.get(args[0])
+    if k == "k_deposit":
+        return {"1": "deposit_density", "4": "deposit_adj"}.get(args[0])
+    if k == "k_deposit_halo":
+        return f"deposit_halo_{args[0]}"
+    if k in ("k_fft_z_fwd", "k_fft_z_inv"):
+        return f"fft_z_{k[-3:]}_{args[1]}"
+    if k == "k_fft_xpot":
+        return f"fft_x_pot_{args[1]}"
+    if k == "k_vjp_source":
+        return "vjp_source"
+    if k == "k_fft_pencil":
+        blocks = int(grid.strip("()").split(",")[0])
+        return f"fft_y_{'inv' if args[1] in ('1', 'true') else 'fwd'}_{blocks // (zc // 8 * n)}"
+    return None
+
+
+def traffic_digest(paths):
+    """profiles/traffic.json from ncu CSV captures (TRAFFIC_COMMAND, one
+    kernel per capture) on the 128^3 / 256^3 workload: mean DRAM bytes per
+    launch of each kind, with the ratio to its algorithmic bytes and the
+    factor that scales it to the other workloads."""
+    import csv
+    import collections
+    launches = collections.OrderedDict()
+    for path in paths:
+        with open(path) as fh:
+            rows = list(csv.reader(line for line in fh if line.startswith('"')))
+        if not rows:
+            continue
+        hdr = rows[0]
+        ki, mi, vi, gi, ii = (hdr.index(c) for c in ("Kernel Name", "Metric Name", "Metric Value", "Grid Size", "ID"))
+        for r in rows[1:]:
+            d = launches.setdefault((path, r[ii]), {"name": r[ki], "grid": r[gi]})
+            d[r[mi]] = float(r[vi].replace(",", ""))
+    src = WORKLOADS[TRAFFIC_WORKLOAD]
+
+    def sizes(w):
+        return (w.n_batch * w.n_p ** 3, w.n_batch * w.n_m ** 3, w.n_batch * w.n_m ** 2 * (w.n_m // 2 + 1))
+
+    per = collections.defaultdict(list)
+    for d in launches.values():
+        kd = _kernel_kind(d["name"], d["grid"], src.n_m)
+        if kd:
+            per[kd].append(d.get("dram__bytes_read.sum", 0.0) + d.get("dram__bytes_write.sum", 0.0))
+    if per.get("fft_x_pot_1") and not per.get("fft_x_pot_2"):  # two 1-field round trips per launch of its kind
+        per["fft_x_pot_2"] = [2 * v for v in per["fft_x_pot_1"]]
+    out = {"source_digest": _source_digest(), "command": TRAFFIC_COMMAND,
+           "note": "mean DRAM bytes (read + write) per launch on the 128^3 / 256^3 workload, one capture per kernel; "
+                   "scale_to multiplies by the ratio of algorithmic bytes per launch (the kernels' traffic grows in "
+                   "proportion to particles, cells and modes); at 256^3 one mesh field fits in L2, so the scaled "
+                   "figures are lower bounds for 1024^3",
+           "kernels": {}, "direct": {}}
+    for kd, vals in sorted(per.items()):
+        ab = algorithmic_bytes(kd, *sizes(src))
+        ent = {"dram_bytes_per_launch": sum(vals) / len(vals), "launches": len(vals), "workload": src.name}
+        if ab:
+            ent["algorithmic_bytes_per_launch"] = ab
+            ent["ratio"] = round(ent["dram_bytes_per_launch"] / ab, 3)
+            ent["scale_to"] = {w.name: algorithmic_bytes(kd, *sizes(w)) / ab for w in WORKLOADS.values()
+                               if w.name != src.name and not getattr(w, "learned", False)}
+        out["kernels"][kd] = ent
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    return out
 
 
 def replica_throughput(dist, world, work, steps, times_ms, device="cpu"):
@@ -690,7 +779,13 @@ def main():
     ap.add_argument("--learn-epochs", type=int, default=3)
     ap.add_argument("--paint-stress", action="store_true",
                     help="time the paint and read kernels on a clustered state instead of the bench step")
+    ap.add_argument("--traffic-from", nargs="+", metavar="CSV",
+                    help="write profiles/traffic.json from ncu DRAM-byte captures (no GPU work)")
     args = ap.parse_args()
+    if args.traffic_from:
+        d = traffic_digest(args.traffic_from)
+        print(json.dumps({k: v.get("ratio") for k, v in d["kernels"].items()}))
+        return 0
     if args.paint_stress:
         return run_paint_stress(args)
     if args.impl == "reference":

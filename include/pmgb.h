@@ -389,9 +389,11 @@ int pm_nn_train_step(pm_ctx *ctx, const float *s, const float *target, double a,
  * 16^3-cell tile of their base cell (counting sort), then one block per
  * 16 x 16 column of tiles sums its particles in shared memory and writes
  * every cell of the column once, with the faces shared between columns
- * added by a second pass.  2 is the default where it applies (own
- * transform, CIC, n_m a multiple of 16, n_batch n_p^3 < 2^31), else 1;
- * where it does not apply, 2 also runs as 1.
+ * added by a second pass.  2 applies with the own transform, CIC, n_m a
+ * multiple of 16 and n_batch n_p^3 < 2^31 (elsewhere it runs as 1); its
+ * buffers (16 B per particle, about 1/8 of a 4-field mesh) are allocated
+ * when it is first selected, PM_ENOMEM if they cannot be.  Default 1: on
+ * the benchmark's workloads the atomic scatter measured faster.
  *
  * pm_autotune     times every candidate of each family in turn (the others
  *                 held at their current best) on this context's scratch

@@ -85,8 +85,9 @@ struct pm_ctx {
     // read, spectral force/adjoint, z-pass FFT (n >= 256); x-pass pencil width
     // shape; z-inverse and z-forward staging; x round trip; force pipeline
     int tune[PM_TUNE_KINDS] = {256, 256, 256, 256, 8, 2, 1, 2, 2, 1};
-    // binned tile-owned deposit (own-FFT meshes, CIC, n_m a multiple of 16):
-    // bin keys, ranks and CSR of the particles, counters, scan scratch, halo lines
+    // binned tile-owned deposit (own-FFT meshes, CIC, n_m a multiple of 16;
+    // dep_ok: supported here): bin keys, ranks and CSR of the particles,
+    // counters, scan scratch, halo lines, allocated when it is first selected
     bool dep_ok = false;
     int *dep_key = nullptr, *dep_rank = nullptr, *dep_idx = nullptr, *dep_count = nullptr, *dep_offset = nullptr,
         *dep_chunk = nullptr;
@@ -381,7 +382,31 @@ PaintArgs paint_args(pm_ctx *ctx, const float *s, const float *mu = nullptr) {
     return a;
 }
 
-bool binned_deposit(const pm_ctx *ctx) { return ctx->dep_ok && ctx->tune[9] == 2; }
+bool binned_deposit(const pm_ctx *ctx) { return ctx->dep_ok && ctx->dep_idx && ctx->tune[9] == 2; }
+
+// The binned deposit's buffers, on its first selection (not inside a capture).
+int deposit_buffers(pm_ctx *ctx) {
+    if (!ctx->dep_ok || ctx->dep_idx) return PM_OK;
+    const size_t parts = (size_t)ctx->g.npart * ctx->P.n_batch, bins = (size_t)deposit_tiles(ctx->g) * ctx->P.n_batch;
+    if (cudaMalloc(&ctx->dep_key, sizeof(int) * parts) != cudaSuccess ||
+        cudaMalloc(&ctx->dep_rank, sizeof(int) * parts) != cudaSuccess ||
+        cudaMalloc(&ctx->dep_count, sizeof(int) * bins) != cudaSuccess ||
+        cudaMalloc(&ctx->dep_offset, sizeof(int) * (bins + 1)) != cudaSuccess ||
+        cudaMalloc(&ctx->dep_chunk, sizeof(int) * deposit_scan_chunks(ctx->g)) != cudaSuccess ||
+        cudaMalloc(&ctx->dep_halo, sizeof(float) * deposit_halo_floats(ctx->g)) != cudaSuccess ||
+        cudaMemset(ctx->dep_count, 0, sizeof(int) * bins) != cudaSuccess || deposit_prepare() != cudaSuccess ||
+        cudaMalloc(&ctx->dep_idx, sizeof(int) * parts) != cudaSuccess) {  // dep_idx last: it marks completion
+        cudaGetLastError();
+        for (int **p : {&ctx->dep_key, &ctx->dep_rank, &ctx->dep_count, &ctx->dep_offset, &ctx->dep_chunk, &ctx->dep_idx}) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+        if (ctx->dep_halo) cudaFree(ctx->dep_halo);
+        ctx->dep_halo = nullptr;
+        return fail(ctx, PM_ENOMEM, "cannot allocate the binned-deposit buffers");
+    }
+    return PM_OK;
+}
 
 // Paint into a plain mesh that this call fills completely, every cell
 // starting from `base`: the binned tile-owned deposit (no zeroing), or
@@ -834,6 +859,7 @@ static int set_tuning(pm_ctx *ctx, const int *t) {
             return fail(ctx, PM_EINVAL,
                         "block sizes must be 128, 256 or 512, the x-pass width 8 or 16, the z stagings 1 or 2, "
                         "the x round trip 1, 2 or 3, the force pipeline 1 or 2, the deposit 1 or 2");
+    if (t[9] == 2) PM_TRY(deposit_buffers(ctx));
     for (int k = 0; k < PM_TUNE_KINDS; ++k) ctx->tune[k] = t[k];
     ctx->fg.zthreads = ctx->tune[3];
     ctx->fg.xwidth = ctx->tune[4];
@@ -1135,23 +1161,7 @@ int pm_create(const pm_config *cfg, pm_ctx **out) {
         ctx->tune[7] = ctx->P.n_m >= 512 ? 3 : 2;  // the fused adjoint spills on lines of 512+ points
         // the potential pipeline needs the 4-point difference gradient
         ctx->tune[8] = (c.solver & PM_SOLVER_SPECTRAL_GRADIENT) ? 1 : 2;
-        if (deposit_supported(ctx->g, n)) {
-            const size_t parts = (size_t)npart * B, bins = (size_t)deposit_tiles(ctx->g) * B;
-            if (cudaMalloc(&ctx->dep_key, sizeof(int) * parts) != cudaSuccess ||
-                cudaMalloc(&ctx->dep_rank, sizeof(int) * parts) != cudaSuccess ||
-                cudaMalloc(&ctx->dep_idx, sizeof(int) * parts) != cudaSuccess ||
-                cudaMalloc(&ctx->dep_count, sizeof(int) * bins) != cudaSuccess ||
-                cudaMalloc(&ctx->dep_offset, sizeof(int) * (bins + 1)) != cudaSuccess ||
-                cudaMalloc(&ctx->dep_chunk, sizeof(int) * deposit_scan_chunks(ctx->g)) != cudaSuccess ||
-                cudaMalloc(&ctx->dep_halo, sizeof(float) * deposit_halo_floats(ctx->g)) != cudaSuccess ||
-                cudaMemset(ctx->dep_count, 0, sizeof(int) * bins) != cudaSuccess || deposit_prepare() != cudaSuccess) {
-                cudaGetLastError();
-                fail(ctx, PM_ENOMEM, "cannot allocate the binned-deposit buffers");
-                return bail(PM_ENOMEM);
-            }
-            ctx->dep_ok = true;
-            ctx->tune[9] = 2;
-        }
+        ctx->dep_ok = deposit_supported(ctx->g, n);  // buffers on first selection (tuning family [9])
     } else if (cudaMalloc(&ctx->mesh, sizeof(float) * (size_t)ctx->mesh_pad * B * kMeshFields) != cudaSuccess) {
         cudaGetLastError();
         fail(ctx, PM_ENOMEM, "cannot allocate the FFT meshes");

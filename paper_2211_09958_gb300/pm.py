@@ -47,7 +47,7 @@ class ParticleMesh:
         tuning = self.get_tuning()
         self._x_round_default = tuning["x_round"]          # 2, or 3 on meshes of 512 and more
         self._pipeline_default = tuning["pipeline"]        # 2, or 1 with the spectral-gradient flag
-        self._deposit_default = tuning["deposit"]          # 2 where the binned deposit applies, else 1
+        self._deposit_default = tuning["deposit"]          # 1: the atomic scatter
 
     # ------------------------------------------------------------ helpers --
     @property

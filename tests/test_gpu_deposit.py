@@ -1,6 +1,7 @@
-"""Binned, tile-owned CIC deposit (tuning family "deposit" = 2, the default
-on own-transform meshes whose side is a multiple of 16) against the FP64
-oracle's density and against the atomic scatter (deposit = 1).
+"""Binned, tile-owned CIC deposit (tuning family "deposit" = 2, for
+own-transform meshes whose side is a multiple of 16; the default is the
+atomic scatter, deposit = 1) against the FP64 oracle's density and against
+the atomic scatter.
 
   * density (pm_density, delta = alpha sum W - 1) of seeded states that
     cross tile faces and the periodic box edges (random displacements of up
@@ -56,7 +57,7 @@ def _states(n_p, box):
 @pytest.mark.parametrize("n_p,n_m,box", [(8, 16, 32.0), (32, 64, 96.0), (64, 128, 128.0), (8, 8, 40.0)])
 def test_binned_density_against_oracle(n_p, n_m, box):
     pm = _pm(n_p, n_m, box, B=3)
-    assert pm.get_tuning()["deposit"] == (2 if n_m % 16 == 0 else 1)
+    assert pm.get_tuning()["deposit"] == 1                           # the atomic scatter by default
     pm.set_tuning(deposit=2)
     states = _states(n_p, box)
     d = _host(pm.density(_cuda(np.stack(states))))

@@ -16,7 +16,7 @@ CANDIDATES = {"paint": (128, 256, 512), "read": (128, 256, 512), "spectral": (12
               "fft_z": (128, 256, 512), "fft_x": (8, 16), "z_staging": (1, 2), "z_fwd_staging": (1, 2),
               "x_round": (1, 2, 3), "pipeline": (1, 2), "deposit": (1, 2)}
 DEFAULT = {"paint": 256, "read": 256, "spectral": 256, "fft_z": 256, "fft_x": 8, "z_staging": 2, "z_fwd_staging": 1,
-           "x_round": 2, "pipeline": 2, "deposit": 2}
+           "x_round": 2, "pipeline": 2, "deposit": 1}
 
 
 def _pm(n_p=32, n_m=256, box=128.0, steps=3):
