@@ -545,12 +545,106 @@ __global__ void __launch_bounds__(kThreads) k_vjp_source(const float4 *__restric
     }
 }
 
+// The same source for meshes of 64 and more per side, marching along x: a
+// block owns an 8 (y) x 32 (z) patch of cells, one thread a (y, z) column
+// (warp = y row, lane = z), and walks XC planes x0 .. x0 + XC - 1 with two
+// planes of halo on either side, so u_x of a cell is loaded once per block
+// instead of once per tile and its four x neighbours flow through a
+// five-register window.  Per plane: the cell's float4 (next plane's loads
+// issued while this one is processed), u_y of the 8 rows plus the two halo
+// rows each side through a double-buffered shared-memory plane (one barrier
+// per plane), u_z of the z neighbours by warp shuffles (lanes 0..3 fetch the
+// four halo nodes).  S_y u_y + S_z u_z of plane x waits two planes, until
+// u_x of plane x + 2 has arrived.
+template <int XC>
+__global__ void __launch_bounds__(kThreads) k_vjp_source_x(const float4 *__restrict__ in, float2 *__restrict__ out,
+                                                           int lgn, float inv12h) {
+    constexpr int TY = kThreads / 32;
+    __shared__ float uys[2][TY + 4][32];
+    const int n = 1 << lgn, m = n - 1;
+    const int64_t n3 = (int64_t)1 << (3 * lgn);
+    const int b = blockIdx.y;
+    const float4 *src = in + (int64_t)b * n3;
+    const float *srcf = reinterpret_cast<const float *>(src);
+    float2 *dst = out + (int64_t)b * n3;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nz = n / 32, ny = n / TY;
+    const int t = blockIdx.x;
+    const int z0 = (t % nz) * 32, y0 = ((t / nz) % ny) * TY, x0 = (t / nz / ny) * XC;
+    const int y = y0 + w, z = z0 + lane;
+    auto cell = [&](int xx, int yy, int zz) -> int64_t {
+        return (((int64_t)(xx & m) << lgn) | (yy & m)) << lgn | (zz & m);
+    };
+    // halo fetches of plane xx: warps 0..3 the u_y rows y0 - 2, y0 - 1, y0 + TY, y0 + TY + 1;
+    // lanes 0..3 the u_z nodes z0 - 2, z0 - 1, z0 + 32, z0 + 33 of their row
+    const int hy = w < 2 ? y0 - 2 + w : y0 + TY + w - 2;
+    const int hz = lane < 2 ? z0 - 2 + lane : z0 + 30 + lane;
+    float ux[5] = {0.f, 0.f, 0.f, 0.f, 0.f};                  // u_x at planes p - 4 .. p of this column
+    float vq[3] = {0.f, 0.f, 0.f}, rq[3] = {0.f, 0.f, 0.f};  // S_y u_y + S_z u_z and rho of planes p - 2 .. p
+    float4 cur = make_float4(0.f, 0.f, 0.f, 0.f);
+    float cur_hy = 0.f, cur_hz = 0.f;
+    auto fetch = [&](int p, float4 &c, float &fy, float &fz) {
+        const bool inner = p >= x0 && p < x0 + XC;
+        if (inner) {
+            c = __ldg(src + cell(p, y, z));
+            if (w < 4) fy = __ldg(srcf + 4 * cell(p, hy, z) + 2);
+            if (lane < 4) fz = __ldg(srcf + 4 * cell(p, y, hz) + 3);
+        } else {
+            c.y = __ldg(srcf + 4 * cell(p, y, z) + 1);  // u_x alone in the x halo
+        }
+    };
+    fetch(x0 - 2, cur, cur_hy, cur_hz);
+    for (int p = x0 - 2; p < x0 + XC + 2; ++p) {
+        float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
+        float nxt_hy = 0.f, nxt_hz = 0.f;
+        if (p + 1 < x0 + XC + 2) fetch(p + 1, nxt, nxt_hy, nxt_hz);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ux[k] = ux[k + 1];
+        ux[4] = cur.y;
+        vq[0] = vq[1];
+        vq[1] = vq[2];
+        rq[0] = rq[1];
+        rq[1] = rq[2];
+        if (p >= x0 && p < x0 + XC) {  // uniform across the block
+            float(*plane)[32] = uys[p & 1];
+            plane[w + 2][lane] = cur.z;
+            if (w < 4) plane[w < 2 ? w : TY + w][lane] = cur_hy;
+            __syncthreads();
+            const float sy = 8.f * (plane[w + 3][lane] - plane[w + 1][lane]) - (plane[w + 4][lane] - plane[w][lane]);
+            const float hm2 = __shfl_sync(0xffffffffu, cur_hz, 0), hm1 = __shfl_sync(0xffffffffu, cur_hz, 1);
+            const float hp1 = __shfl_sync(0xffffffffu, cur_hz, 2), hp2 = __shfl_sync(0xffffffffu, cur_hz, 3);
+            float zm1 = __shfl_up_sync(0xffffffffu, cur.w, 1), zm2 = __shfl_up_sync(0xffffffffu, cur.w, 2);
+            float zp1 = __shfl_down_sync(0xffffffffu, cur.w, 1), zp2 = __shfl_down_sync(0xffffffffu, cur.w, 2);
+            if (lane == 0) zm1 = hm1;
+            if (lane < 2) zm2 = lane == 0 ? hm2 : hm1;
+            if (lane == 31) zp1 = hp1;
+            if (lane > 29) zp2 = lane == 31 ? hp2 : hp1;
+            vq[2] = sy + (8.f * (zp1 - zm1) - (zp2 - zm2));
+            rq[2] = cur.x;
+        }
+        const int q = p - 2;  // ux[0 .. 4] = u_x at q - 2 .. q + 2
+        if (q >= x0 && q < x0 + XC) {
+            const float sx = 8.f * (ux[3] - ux[1]) - (ux[4] - ux[0]);
+            dst[cell(q, y, z)] = make_float2(rq[0], inv12h * (sx + vq[0]));
+        }
+        cur = nxt;
+        cur_hy = nxt_hy;
+        cur_hz = nxt_hz;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_vjp_source(const float4 *in, float2 *out, int n, int nb, float inv12h, cudaStream_t st) {
     int lgn = 0;
     while ((1 << lgn) < n) ++lgn;
     if ((1 << lgn) != n || n < 16) return cudaErrorInvalidValue;
+    if (n >= 64) {  // x-marching blocks of 8 x 32 columns over 64 planes
+        constexpr int XC = 64, TY = kThreads / 32;
+        k_vjp_source_x<XC><<<dim3((unsigned)((n / 32) * (n / TY) * (n / XC)), nb), kThreads, 0, st>>>(in, out, lgn,
+                                                                                                    inv12h);
+        return cudaGetLastError();
+    }
     const int tz = n < 32 ? n : 32;
     const dim3 grid((unsigned)((n / 4) * (n / 8) * (n / tz)), nb);
     if (tz == 16)
