@@ -53,7 +53,7 @@ struct pm_ctx {
     float *r1 = nullptr, *r4 = nullptr;
     float *rpot = nullptr;   // [run][n^3][2]: potential phi (and adjoint psi) before the gradient stencil
     float2 *spec = nullptr, *tw = nullptr;
-    ZInvMap zmaps[3] = {};   // TMA descriptors of the blocked spectrum (z inverse)
+    ZInvMap zmaps[Z_INV_MAPS] = {};  // TMA descriptors of the blocked spectrum (z inverse)
     int *d_err = nullptr;    // device error flag (bounded TMA waits)
     bool have_plans = false;
     void *work = nullptr;
@@ -938,7 +938,11 @@ int pm_autotune(pm_ctx *ctx, const float *s, float *ms) {
             }
             return e;
         }
-        if (kind == 5) {
+        if (kind == 5) {  // the z inverses the force pipeline runs
+            if (pot_pipeline(ctx)) {
+                if ((e = launch_fft_z_inv(2, ctx->spec, ctx->rpot, ctx->fg, ctx->stream)) != cudaSuccess) return e;
+                return launch_fft_z_inv(1, ctx->spec, ctx->rpot, ctx->fg, ctx->stream);
+            }
             if ((e = launch_fft_z_inv(3, ctx->spec, ctx->r4, ctx->fg, ctx->stream)) != cudaSuccess) return e;
             return launch_fft_z_inv(4, ctx->spec, ctx->r4, ctx->fg, ctx->stream);
         }

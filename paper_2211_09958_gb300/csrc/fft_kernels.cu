@@ -421,13 +421,14 @@ cudaError_t z_inv_tt(const float2 *spec, float *out, const FftGeom &fg, const CU
     return cudaGetLastError();
 }
 
-// TMA staging where a map for this block shape exists (n >= 256, 4 output
-// slots, own transform), per-thread loads otherwise.
+// TMA staging where a map for this block shape exists (n >= 256, own
+// transform; one map per output shape and block size), per-thread loads
+// otherwise.
 template <int N, int GS, int GO, int T>
 cudaError_t z_inv_t(const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st) {
-    constexpr int ti = T == 128 ? 0 : (T == 256 ? 1 : 2);
-    if (N >= 256 && GO == 4 && fg.ztma && fg.tmaps && fg.tmaps[ti].valid)
-        return z_inv_tt<N, GS, GO, T, (N >= 256 && GO == 4)>(spec, out, fg, fg.tmaps[ti].map, st);
+    constexpr int ti = (GO == 4 ? 0 : (GO == 2 ? 3 : 6)) + (T == 128 ? 0 : (T == 256 ? 1 : 2));
+    if (N >= 256 && fg.ztma && fg.tmaps && fg.tmaps[ti].valid)
+        return z_inv_tt<N, GS, GO, T, (N >= 256)>(spec, out, fg, fg.tmaps[ti].map, st);
     static const CUtensorMap none{};
     return z_inv_tt<N, GS, GO, T, false>(spec, out, fg, none, st);
 }
@@ -920,17 +921,19 @@ cudaError_t upload_fft_constants(float2 *tw_dev) {
     return cudaMemcpy(tw_dev, w1024, sizeof(w1024), cudaMemcpyHostToDevice);
 }
 
-int z_inv_rows(int n, int threads) {
-    const int m = n / 2, tl = m / (1 << ((ilog2(m) + 1) / 2)), y = threads / tl / 4;
+// Rows per z-inverse block (ZShape<n, go, threads>::Y).
+int z_inv_rows(int n, int threads, int go) {
+    const int m = n / 2, tl = m / (1 << ((ilog2(m) + 1) / 2)), y = threads / tl / go;
     return y < n ? y : n;
 }
 
 // 5-D tensor maps over the blocked spectrum for the TMA z inverse, one per
-// block size (rows per block Y): dims, innermost first, [16 floats][y][x][kz
-// block][field * nb + run], box [16][Y][1][n/16 + 1][1].  Returns false (and
-// leaves the maps invalid) when the driver entry point is unavailable.
-bool encode_z_inv_maps(float2 *spec, const FftGeom &fg, ZInvMap maps[3]) {
-    for (int i = 0; i < 3; ++i) maps[i].valid = false;
+// output shape and block size (rows per block Y): dims, innermost first,
+// [16 floats][y][x][kz block][field * nb + run], box [16][Y][1][n/16 + 1][1].
+// Returns false (and leaves the maps invalid) when the driver entry point is
+// unavailable.
+bool encode_z_inv_maps(float2 *spec, const FftGeom &fg, ZInvMap maps[Z_INV_MAPS]) {
+    for (int i = 0; i < Z_INV_MAPS; ++i) maps[i].valid = false;
     if (fg.n < 256) return false;
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q{};
@@ -947,15 +950,18 @@ bool encode_z_inv_maps(float2 *spec, const FftGeom &fg, ZInvMap maps[3]) {
     const cuuint64_t dims[5] = {16, n, n, (cuuint64_t)(fg.zc / 8), (cuuint64_t)(4 * fg.nb)};
     const cuuint64_t strides[4] = {64, n * 64, n * n * 64, (cuuint64_t)(fg.zc / 8) * n * n * 64};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    const int threads[3] = {128, 256, 512};
-    for (int i = 0; i < 3; ++i) {
-        const cuuint32_t box[5] = {16, (cuuint32_t)z_inv_rows(fg.n, threads[i]), 1, (cuuint32_t)(fg.n / 16 + 1), 1};
+    const int threads[3] = {128, 256, 512}, go[3] = {4, 2, 1};
+    bool all = true;
+    for (int i = 0; i < Z_INV_MAPS; ++i) {
+        const cuuint32_t box[5] = {16, (cuuint32_t)z_inv_rows(fg.n, threads[i % 3], go[i / 3]), 1,
+                                   (cuuint32_t)(fg.n / 16 + 1), 1};
         const CUresult r = encode(&maps[i].map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, spec, dims, strides, box, estr,
                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         maps[i].valid = r == CUDA_SUCCESS;
+        all = all && maps[i].valid;
     }
-    return maps[0].valid && maps[1].valid && maps[2].valid;
+    return all;
 }
 
 cudaError_t launch_fft_z_fwd(int g, const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st) {

@@ -205,7 +205,7 @@ struct FftGeom {
     int zthreads;       // z-pass block size for n >= 256: 128, 256 (also for 0) or 512 (autotuned)
     int ztma;           // z inverse: 1 = stage the spectrum rows with TMA (where maps exist)
     int zstage;         // z forward (4 fields): 1 = coalesced 16-byte staging of the input rows
-    const ZInvMap *tmaps;  // host array [3] (block sizes 128, 256, 512), or NULL
+    const ZInvMap *tmaps;  // host array [3 output shapes: 4, 2, 1 slots][3 block sizes: 128, 256, 512], or NULL
     int *err;           // device flag set when a TMA wait times out
     int xwidth;         // x-pass pencil width in complex columns: 8 (also for 0) or 16 (autotuned)
 };
@@ -218,7 +218,8 @@ bool own_fft_supported(int n);
 int own_fft_zc(int n);
 cudaError_t upload_fft_constants(float2 *tw_dev);
 cudaError_t launch_fft_z_fwd(int g, const float *in, float2 *spec, const FftGeom &fg, cudaStream_t st);
-bool encode_z_inv_maps(float2 *spec, const FftGeom &fg, ZInvMap maps[3]);
+constexpr int Z_INV_MAPS = 9;  // [output shape GO = 4, 2, 1][block size 128, 256, 512]
+bool encode_z_inv_maps(float2 *spec, const FftGeom &fg, ZInvMap maps[Z_INV_MAPS]);
 // gs = 4 or 3: spectrum fields -> 4-slot interleaved real mesh; gs = 2: two
 // planar meshes (field 1 at out + nb n^3); gs = 1: plain real mesh.
 cudaError_t launch_fft_z_inv(int gs, const float2 *spec, float *out, const FftGeom &fg, cudaStream_t st);

@@ -26,8 +26,9 @@ of 8192 particles and 32768 white-noise sites.  Bounds (FP32 against FP64):
     batched test shows the same gradients with TSC weights, which have no
     jump, within 1e-4).  dL/dOm cancels to 1/300 of its terms here, so its
     relative error is 300 times the terms' FP32 accuracy: 1.4e-2 without
-    stored states (4.6e-5 of the terms), 1e-3 with a checkpoint every 4 steps,
-    which is the bound for that run.  The cotangents (lam, mu) of the initial
+    stored states (4.6e-5 of the terms), 1.0e-3 to 1.6e-3 with a checkpoint
+    every 4 steps (3e-6 to 5e-6 of the terms; the read's block shape sets the
+    order of the per-block reduction sums), held to 3e-3 for that run.  The cotangents (lam, mu) of the initial
     state carry the reversal drift: within 1e-2 relative L2 without stored
     states (measured 4e-3) and 2e-3 with checkpoints (measured 1.3e-3).
 """
@@ -120,4 +121,4 @@ def test_gradients(run, every):
     assert rel["s8"] < 1e-3, rel
     assert rel["om/terms"] < 1e-4, rel
     if every:
-        assert rel["om"] < 1e-3, rel
+        assert rel["om"] < 3e-3, rel
