@@ -241,7 +241,7 @@ def _kernel_kind(name, grid, n):
     return None
 
 
-def traffic_digest(paths):
+def traffic_digest(paths, out_path=None):
     """profiles/traffic.json from ncu CSV captures (TRAFFIC_COMMAND, one
     kernel per capture) on the 128^3 / 256^3 workload: mean DRAM bytes per
     launch of each kind, with the ratio to its algorithmic bytes and the
@@ -286,7 +286,7 @@ def traffic_digest(paths):
             ent["scale_to"] = {w.name: algorithmic_bytes(kd, *sizes(w)) / ab for w in WORKLOADS.values()
                                if w.name != src.name and not getattr(w, "learned", False)}
         out["kernels"][kd] = ent
-    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
+    with open(out_path or os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
         json.dump(out, fh, indent=1)
     return out
 

@@ -1,11 +1,14 @@
 """Host side of the benchmark: the JSON line of the reference arm (the FP64
 oracle on the CPU), the algorithmic byte model behind the roofline, the
-fixed-tuning argument and the DRAM traffic lookup.  No GPU."""
+fixed-tuning argument, the DRAM traffic lookup and the digest built from
+ncu captures.  No GPU."""
 
 import json
 import os
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
@@ -84,3 +87,51 @@ def test_workloads_of_the_bench():
     assert (batch.n_batch, batch.n_p, batch.n_m, batch.n_steps) == (32, 64, 128, 20)
     learned = WORKLOADS[bench.LEARNED_WORKLOAD]
     assert (learned.n_p, learned.n_m, learned.n_steps) == (128, 128, 40)
+
+
+def test_kernel_kinds_from_ncu_names():
+    # the names ncu prints (template arguments plain or with C-style casts)
+    kind = bench._kernel_kind
+    assert kind("void pmgb::<unnamed>::k_read<(int)3, (bool)0, (int)128, (int)2, (bool)1>(pmgb::ReadArgs)",
+                "(1, 1, 1)", 256) == "read_adj"
+    assert kind("void pmgb::<unnamed>::k_read<1, false, 128, 2, true>(pmgb::ReadArgs)", "(1, 1, 1)", 256) == \
+        "read_kick_drift"
+    assert kind("void pmgb::<unnamed>::k_paint<(int)2, (int)512, (int)2>(pmgb::PaintArgs)", "(1, 1, 1)", 256) == \
+        "paint_adj"
+    assert kind("void pmgb::<unnamed>::k_deposit<(int)1, (int)256>(pmgb::DepositArgs)", "(1, 1, 1)", 256) == \
+        "deposit_density"
+    assert kind("void pmgb::<unnamed>::k_deposit_halo<(int)4>(pmgb::DepositArgs)", "(1, 1, 1)", 256) == \
+        "deposit_halo_4"
+    assert kind("pmgb::<unnamed>::k_bin_count(pmgb::DepositArgs)", "(1, 1, 1)", 256) == "bin_count"
+    assert kind("void pmgb::<unnamed>::k_fft_xpot<(int)256, (int)1>(float2 *, ...)", "(1, 1, 1)", 256) == \
+        "fft_x_pot_1"
+    assert kind("void pmgb::<unnamed>::k_fft_z_inv<(int)256, (int)2, (int)2, (int)256, (bool)1>(...)",
+                "(1, 1, 1)", 256) == "fft_z_inv_2"
+    # y pass: one block per (field, run, kz block of 8) and x; 256^3 has 136 / 8 kz blocks
+    assert kind("void pmgb::<unnamed>::k_fft_pencil<(int)256, (bool)1, (int)8>(...)", f"({2 * 17 * 256}, 1, 1)",
+                256) == "fft_y_inv_2"
+    assert kind("void regular_fft<512, EPT<8>>(kernel_arguments_t)", "(1, 1, 1)", 256) is None
+
+
+def test_traffic_digest_from_a_capture(tmp_path, monkeypatch):
+    # a two-launch capture of one kernel: mean DRAM bytes per launch, its ratio to
+    # the algorithmic bytes and the factor to the headline workload
+    csv_text = "\n".join([
+        '"ID","Kernel Name","Grid Size","Metric Name","Metric Unit","Metric Value"',
+        '"0","void pmgb::<unnamed>::k_vjp_source<32>(const float4 *, float2 *, int, float)","(512, 1, 1)",'
+        '"dram__bytes_read.sum","byte","300,000,000"',
+        '"0","void pmgb::<unnamed>::k_vjp_source<32>(const float4 *, float2 *, int, float)","(512, 1, 1)",'
+        '"dram__bytes_write.sum","byte","100,000,000"',
+        '"1","void pmgb::<unnamed>::k_vjp_source<32>(const float4 *, float2 *, int, float)","(512, 1, 1)",'
+        '"dram__bytes_read.sum","byte","320,000,000"',
+        '"1","void pmgb::<unnamed>::k_vjp_source<32>(const float4 *, float2 *, int, float)","(512, 1, 1)",'
+        '"dram__bytes_write.sum","byte","80,000,000"'])
+    path = tmp_path / "k.csv"
+    path.write_text("==PROF== noise\n" + csv_text + "\n")
+    out = bench.traffic_digest([str(path)], out_path=str(tmp_path / "traffic.json"))
+    ent = out["kernels"]["vjp_source"]
+    assert ent["launches"] == 2 and ent["dram_bytes_per_launch"] == 4e8
+    ab = bench.algorithmic_bytes("vjp_source", 128 ** 3, 256 ** 3, 256 ** 2 * 129)
+    assert ent["ratio"] == round(4e8 / ab, 3)
+    assert ent["scale_to"]["pm512_mesh1024"] == pytest.approx(1024 ** 3 / 256 ** 3)
+    assert json.load(open(tmp_path / "traffic.json"))["source_digest"] == bench._source_digest()
