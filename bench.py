@@ -233,7 +233,7 @@ def _kernel_kind(name, grid, n):
         return f"fft_z_{k[-3:]}_{args[1]}"
     if k == "k_fft_xpot":
         return f"fft_x_pot_{args[1]}"
-    if k == "k_vjp_source":
+    if k in ("k_vjp_source", "k_vjp_source_x"):
         return "vjp_source"
     if k == "k_fft_pencil":
         blocks = int(grid.strip("()").split(",")[0])
