@@ -89,6 +89,10 @@ struct pm_ctx {
     // dep_ok: supported here): bin keys, ranks and CSR of the particles,
     // counters, scan scratch, halo lines, allocated when it is first selected
     bool dep_ok = false;
+    // r1 / r4 known to hold zeros (cleared by the previous read of the same
+    // integration call), so that the next paint can skip its zeroing pass;
+    // false outside the integration loops
+    bool r1_zero = false, r4_zero = false;
     int *dep_key = nullptr, *dep_rank = nullptr, *dep_idx = nullptr, *dep_count = nullptr, *dep_offset = nullptr,
         *dep_chunk = nullptr;
     float *dep_halo = nullptr;
@@ -435,13 +439,20 @@ int paint_own(pm_ctx *ctx, int mode, const PaintArgs &pa, float base = 0.f) {
         PM_LAUNCH(ctx, "bin_scatter", launch_bin_scatter(da, ctx->stream));
         PM_LAUNCH(ctx, (adj ? "deposit_adj" : "deposit_density"), launch_deposit(nf, da, ctx->stream));
         PM_LAUNCH(ctx, (adj ? "deposit_halo_4" : "deposit_halo_1"), launch_deposit_halo(nf, da, ctx->stream));
+        if (pa.mesh.ptr == ctx->r1) ctx->r1_zero = false;
+        if (pa.mesh.ptr == ctx->r4) ctx->r4_zero = false;
         return PM_OK;
     }
     const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
-    if (base == 0.f)
+    const bool zeroed = base == 0.f && ((pa.mesh.ptr == ctx->r1 && ctx->r1_zero) || (pa.mesh.ptr == ctx->r4 && ctx->r4_zero));
+    if (zeroed)
+        ;  // cleared by the previous step's read
+    else if (base == 0.f)
         PM_MEMSET(ctx, cudaMemsetAsync(pa.mesh.ptr, 0, sizeof(float) * n3 * nf * ctx->P.n_batch, ctx->stream));
     else
         PM_LAUNCH(ctx, "fill", launch_fill(pa.mesh.ptr, n3 * nf * ctx->P.n_batch, base, ctx->stream));
+    if (pa.mesh.ptr == ctx->r1) ctx->r1_zero = false;
+    if (pa.mesh.ptr == ctx->r4) ctx->r4_zero = false;
     PM_LAUNCH(ctx, paint_kind(mode), launch_paint(mode, pa, ctx->stream));
     return PM_OK;
 }
@@ -595,6 +606,15 @@ int force_meshes(pm_ctx *ctx, const float *s, const float *mu, double a = -1.0, 
     PM_LAUNCH(ctx, (adj ? "spectral_adj" : "spectral_force"), launch_spectral(adj ? SPEC_ADJ : SPEC_FORCE, mesh_spec(ctx), ctx->d_pref, ctx->stream));
     PM_TRY(mesh_c2r(ctx, 0, adj ? 4 : 3));
     return PM_OK;
+}
+
+// The next paint's mesh the read may clear (own transform, potential read:
+// the read does not touch r1 or r4; atomic paints, which add into zeros).
+float4 *zero_target(pm_ctx *ctx, bool adj, int64_t *n4) {
+    if (!ctx->own || !pot_read(ctx) || binned_deposit(ctx)) return nullptr;
+    const int64_t n3 = (int64_t)ctx->P.n_m * ctx->P.n_m * ctx->P.n_m;
+    *n4 = adj ? n3 : n3 / 4;
+    return reinterpret_cast<float4 *>(adj ? ctx->r4 : ctx->r1);
 }
 
 // Interpolate from the force meshes (particles in lattice order).
@@ -1385,6 +1405,7 @@ int pm_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, fl
         ReadArgs ra = force_read_args(ctx, s);
         ra.p = p;
         ra.f = f;
+        ctx->r1_zero = false;
         for (int n = step_begin; n < step_end; ++n) {
             PM_TRY(force_meshes(ctx, s, nullptr, a_of(ctx, n)));
             const int ck = ck_slot(ctx, n);
@@ -1392,13 +1413,17 @@ int pm_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, float *s, fl
             ra.kick_step = n;
             ra.kick_sel = n == step_begin ? KICK_A : KICK_MERGED;
             ra.drift_step = n;
+            ra.zero = zero_target(ctx, false, &ra.zero4);  // the density mesh, for the next step's paint
             PM_TRY(read_forces(ctx, READ_KICK_DRIFT, ra));
+            ctx->r1_zero = ra.zero != nullptr;
             if (ck >= 0) PM_TRY(ck_copy(ctx, ck_ptr(ctx, ck, 1), p));  // p_{n+1/2}
         }
         PM_TRY(force_meshes(ctx, s, nullptr, a_of(ctx, step_end)));
         ra.kick_step = step_end - 1;
         ra.kick_sel = KICK_B;
         ra.drift_step = -1;
+        ra.zero = nullptr;
+        ctx->r1_zero = false;
         return read_forces(ctx, READ_HALF_KICK, ra);
     });
 }
@@ -1421,6 +1446,7 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
     const int N = ctx->P.n_steps, B = ctx->P.n_batch;
     const int last = step_end - 1;
     PM_TRY(run_graphed(ctx, 2, step_begin, step_end, s, p, f, lam, mu, flags, [&]() -> int {
+        ctx->r4_zero = false;
         PM_MEMSET(ctx, cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * B * 2 * (N + 1), ctx->stream));
         if (ctx->nn_on)  // parameter gradient of this adjoint run
             PM_MEMSET(ctx, cudaMemsetAsync(ctx->nn_grad, 0, sizeof(float) * nn_param_count(), ctx->stream));
@@ -1445,7 +1471,9 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
             ra.drift_step = last;
             ra.red = ctx->d_red + 2 * N;
             ra.red2_offset = (2 * last + 1) - 2 * N;
+            ra.zero = zero_target(ctx, true, &ra.zero4);  // the 4-field mesh, for the next step's paint
             PM_TRY(read_forces(ctx, READ_ADJ, ra));
+            ctx->r4_zero = ra.zero != nullptr;
         }
         for (int n = last; n >= step_begin; --n) {
             const int ck = ck_slot(ctx, n);
@@ -1465,8 +1493,11 @@ int pm_adjoint_integrate(pm_ctx *ctx, int32_t step_begin, int32_t step_end, floa
                 ra.drift_step = n - 1;
                 ra.red2_offset = (2 * (n - 1) + 1) - 2 * n;
             }
+            ra.zero = n > step_begin ? zero_target(ctx, true, &ra.zero4) : nullptr;
             PM_TRY(read_forces(ctx, READ_ADJ, ra));
+            ctx->r4_zero = ra.zero != nullptr;
         }
+        ctx->r4_zero = false;
         return PM_OK;
     }));
     if (domega) {

@@ -247,6 +247,12 @@ __global__ void __launch_bounds__(T) k_read(ReadArgs a) {
         float s3[3] = {sx, sy, sz};
         finish_read<MODE>(a, b, gi, s3, F, G, mu, red);
     }
+    if (a.zero) {  // streaming stores of zeros into the next paint's mesh, grid-strided over the run
+        const int64_t stride = (int64_t)gridDim.x * T;
+        float4 *z = a.zero + (int64_t)b * a.zero4;
+        for (int64_t j = (int64_t)blockIdx.x * T + threadIdx.x; j < a.zero4; j += stride)
+            z[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     if (MODE == READ_ADJ) block_sum_to<T, 2>(red, a.red + (int64_t)b * a.red_bstride, a.red2_offset);
 }
 

@@ -135,6 +135,11 @@ struct ReadArgs {
     const float *pot;
     int lgn;              // log2 n_m
     float inv12h;         // 1 / (12 h)
+    // when zero != NULL the read also clears zero4 float4 per run at
+    // zero + b zero4 (the paint target of the next step, which the read no
+    // longer needs), so that the next paint needs no separate zeroing pass
+    float4 *zero;
+    int64_t zero4;
 };
 
 cudaError_t launch_paint(int mode, const PaintArgs &a, cudaStream_t st);
