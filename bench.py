@@ -170,8 +170,9 @@ def algorithmic_bytes(kind, npart, ncell, nmodes, pot_read=False):
 
 def _source_digest():
     """Digest of the library sources that hold device code (kernels and the
-    headers they include): a DRAM traffic capture stays valid while these
-    are unchanged.  Host-only orchestration files do not enter."""
+    headers they include), comments and blank lines left out: a DRAM traffic
+    capture stays valid while the code in them is unchanged.  Host-only
+    orchestration files do not enter."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2211_09958_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
@@ -179,7 +180,9 @@ def _source_digest():
             with open(os.path.join(csrc, f), "rb") as fh:
                 text = fh.read()
             if b"__global__" in text or b"__device__" in text:
-                h.update(text)
+                code = re.sub(rb"/\*.*?\*/", b"", text, flags=re.S)
+                code = re.sub(rb"//[^\n]*", b"", code)
+                h.update(b"\n".join(line.rstrip() for line in code.splitlines() if line.strip()))
     return h.hexdigest()[:16]
 
 

@@ -1,9 +1,11 @@
-// Learned-correction inference on the 5th-generation tensor cores: the same
-// per-cell MLP as learned.cu (features asinh(rho - 1) of the 27 periodic
-// neighbours and a; 32 -> 128 -> 128 -> 3, ReLU; BF16 operands, FP32
-// accumulation; output times 3/2 Om h added to the force meshes), with each
-// layer one M = 128 tcgen05.mma chain whose accumulator lives in tensor
-// memory.
+// The learned correction's network on the 5th-generation tensor cores:
+// inference and the training forward (k_mlp_fwd_tc), the backward to the
+// activation and feature cotangents (k_mlp_bwd_tc) and the weight gradients
+// (k_wgrad_tc), for the per-cell MLP described in learned.cu (features
+// asinh(rho - 1) of the 27 periodic neighbours and a; 32 -> 128 -> 128 -> 3,
+// ReLU; BF16 operands, FP32 accumulation; output times 3/2 Om h added to the
+// force meshes).  Each layer is one M = 128 tcgen05.mma chain whose
+// accumulator lives in tensor memory.
 //
 // Per 128-cell tile (one row of A per cell, one TMEM lane per row):
 //   features -> smem A1 (128 x 32, bf16)             all threads, gathered
